@@ -1,0 +1,198 @@
+"""CPU oracle for the CMIF: the paper's direct histogram method (Sec. 2.2).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library ``paper_2106_14699_gb300``
+and neither imports the other; the only common module is ``synth`` (input
+generators, which hold none of the method's arithmetic).
+
+Functions and the passages they follow:
+
+* ``cmif``        -- the full CMIF map by the direct method (Sec. 2.2), entropies
+                     per Eq. margentropy / Eq. jointentropy on relative frequencies
+                     (Eq. finalentropy), MI by Eq. mientropy; 0/0 = 0, 0 log 0 = 0
+                     (Sec. 3.2).  Pinned by tests/test_oracle.py.
+* ``cmif_at``     -- the same at a list of displacements.  Pinned (same code path).
+* ``warp_nn``     -- nearest-neighbour rotation of B (Sec. 3.6); the paper leaves
+                     centre, canvas and sign open, the reading is documented in
+                     cmif_direct.c.  Pinned by quarter-turn / identity cases.
+* ``gamma_argmax``, ``align`` -- the per-transform gamma-gated argmax and the
+                     strict-greater update over transforms of Alg. 1.  Pinned by
+                     hand-built cases.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIBPATH = os.path.join(_LIBDIR, "liboracle_cmif.so")
+_SRC = os.path.join(_HERE, "cmif_direct.c")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_LABEL_RANGE, ERR_INTERNAL = 0, 1, 2, 3
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (plain C + OpenMP)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIBPATH) or os.path.getmtime(_LIBPATH) < os.path.getmtime(_SRC):
+        tmp = _LIBPATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIBPATH)
+    return _LIBPATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIBPATH)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            lib.oracle_cmif.argtypes = [P, P, I, I, P, P, I, I, I, I, P, P, P, P, P, P, I]
+            lib.oracle_cmif.restype = I
+            lib.oracle_cmif_at.argtypes = [P, P, I, I, P, P, I, I, I, I, I, P, P, P, P, P, P, I]
+            lib.oracle_cmif_at.restype = I
+            lib.oracle_warp_nn.argtypes = [P, P, I, I, ctypes.c_double, P, P]
+            lib.oracle_warp_nn.restype = I
+            lib.oracle_max_threads.argtypes = []
+            lib.oracle_max_threads.restype = I
+            _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prep(A, M_A, B, M_B):
+    A = np.ascontiguousarray(A, np.int32)
+    B = np.ascontiguousarray(B, np.int32)
+    M_A = None if M_A is None else np.ascontiguousarray(M_A, np.uint8)
+    M_B = None if M_B is None else np.ascontiguousarray(M_B, np.uint8)
+    if A.ndim != 2 or B.ndim != 2:
+        raise ValueError("A and B must be 2-D label images")
+    if M_A is not None and M_A.shape != A.shape or M_B is not None and M_B.shape != B.shape:
+        raise ValueError("mask shape mismatch")
+    return A, M_A, B, M_B
+
+
+def _check(st):
+    if st == ERR_LABEL_RANGE:
+        raise OracleError("label outside [0, K) under mask")
+    if st != OK:
+        raise OracleError(f"oracle status {st}")
+
+
+def cmif(A, M_A, B, M_B, K_A, K_B, *, counts=False, marginals=False, entropies=False, nthreads=0):
+    """Full CMIF map over the linear shift range (direct method, Sec. 2.2).
+
+    Returns dict with ``mi`` (R x C float64 bits), ``n`` (R x C int64) and,
+    on request, ``joint`` (K_A*K_B x R x C int32), ``marg_a``, ``marg_b``,
+    ``ent`` (3 x R x C: H_A, H_B, H_AB).  Row r <-> dy = r - (H_A-1),
+    column c <-> dx = c - (W_A-1).
+    """
+    A, M_A, B, M_B = _prep(A, M_A, B, M_B)
+    HA, WA = A.shape
+    HB, WB = B.shape
+    R, C = HA + HB - 1, WA + WB - 1
+    mi = np.empty((R, C), np.float64)
+    n = np.empty((R, C), np.int64)
+    joint = np.empty((K_A * K_B, R, C), np.int32) if counts else None
+    ma = np.empty((K_A, R, C), np.int32) if marginals else None
+    mb = np.empty((K_B, R, C), np.int32) if marginals else None
+    ent = np.empty((3, R, C), np.float64) if entropies else None
+    st = _load().oracle_cmif(_ptr(A), _ptr(M_A), HA, WA, _ptr(B), _ptr(M_B), HB, WB, K_A, K_B,
+                             _ptr(mi), _ptr(n), _ptr(joint), _ptr(ma), _ptr(mb), _ptr(ent), nthreads)
+    _check(st)
+    out = dict(mi=mi, n=n)
+    if counts:
+        out["joint"] = joint
+    if marginals:
+        out["marg_a"], out["marg_b"] = ma, mb
+    if entropies:
+        out["ent"] = ent
+    return out
+
+
+def cmif_at(A, M_A, B, M_B, K_A, K_B, dys, dxs, *, counts=False, entropies=False, nthreads=0):
+    """CMIF, N (and optionally joint counts, entropies) at the displacements (dys[i], dxs[i])."""
+    A, M_A, B, M_B = _prep(A, M_A, B, M_B)
+    HA, WA = A.shape
+    HB, WB = B.shape
+    dys = np.ascontiguousarray(dys, np.int32)
+    dxs = np.ascontiguousarray(dxs, np.int32)
+    m = len(dys)
+    mi = np.empty(m, np.float64)
+    n = np.empty(m, np.int64)
+    joint = np.empty((m, K_A * K_B), np.int32) if counts else None
+    ent = np.empty((m, 3), np.float64) if entropies else None
+    st = _load().oracle_cmif_at(_ptr(A), _ptr(M_A), HA, WA, _ptr(B), _ptr(M_B), HB, WB, K_A, K_B,
+                                m, _ptr(dys), _ptr(dxs), _ptr(mi), _ptr(n), _ptr(joint), _ptr(ent), nthreads)
+    _check(st)
+    out = dict(mi=mi, n=n)
+    if counts:
+        out["joint"] = joint
+    if entropies:
+        out["ent"] = ent
+    return out
+
+
+def warp_nn(B, M_B, theta):
+    """Nearest-neighbour rotation of (B, M_B) by theta radians (reading in cmif_direct.c)."""
+    B = np.ascontiguousarray(B, np.int32)
+    M_B = None if M_B is None else np.ascontiguousarray(M_B, np.uint8)
+    H, W = B.shape
+    oB = np.empty_like(B)
+    oM = np.empty((H, W), np.uint8)
+    _check(_load().oracle_warp_nn(_ptr(B), _ptr(M_B), H, W, float(theta), _ptr(oB), _ptr(oM)))
+    return oB, oM
+
+
+def gamma_argmax(mi, n, gamma):
+    """One transform of Alg. 1: Ncal = gamma * max_chi N; the chi maximising CMIF
+    among shifts with N >= Ncal.  Ties go to the lowest row-major map index.
+    Returns (flat index, MI there, N there)."""
+    mi = np.asarray(mi, np.float64).ravel()
+    n = np.asarray(n).ravel()
+    thr = float(gamma) * float(n.max()) if n.size else 0.0
+    ok = n.astype(np.float64) >= thr
+    masked = np.where(ok, mi, -np.inf)
+    idx = int(np.argmax(masked))
+    return idx, float(mi[idx]), int(n[idx])
+
+
+def align(per_angle, gamma, top_k=1):
+    """Alg. 1 over a set of transforms.  ``per_angle`` is a list of (mi_map, n_map).
+
+    I starts at 0 and T-hat at the identity (no transform chosen, angle index -1);
+    a transform replaces the best only when its I_T is strictly greater.  Also
+    returns the top_k per-transform bests, by MI descending, earlier transform
+    first among equals.
+    """
+    best = (-1, -1, 0.0, 0)   # (angle index, flat shift index, I, N)
+    recs = []
+    for t, (mi, n) in enumerate(per_angle):
+        idx, i_t, n_t = gamma_argmax(mi, n, gamma)
+        recs.append((t, idx, i_t, n_t))
+        if i_t > best[2]:
+            best = (t, idx, i_t, n_t)
+    order = sorted(range(len(recs)), key=lambda k: (-recs[k][2], recs[k][0]))
+    return best, [recs[k] for k in order[:top_k]]
