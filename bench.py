@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""CMIF benchmark: shift*angle evaluations per second at 1024^2, K = 16.
+
+One step = one full CMIF map of the 1024 x 1024, K_A = K_B = 16 workload
+(synthetic Voronoi labels, all-ones masks, planted shift; the paper's image
+datasets are not available): the level-set transforms of A and B, the 256
+pair correlations, the rounding + entropy epilogue and the gamma-gated peak of
+Alg. 1.  One evaluation = the MI at one displacement of the full linear range
+(2047 x 2047 = 4,190,209 per map, one angle).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one replica per GPU (the path has no exchange step;
+each rank computes its own map) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CMIF shift·angle evaluations/sec at 1024², K=16 (1 GB300); % HBM roofline"
+UNIT = "shift·angle evals/s"
+CONFIG_ID = 3
+GAMMA = 0.5
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+# DRAM bytes per launch of the dominant kernels from one ncu capture of this
+# workload (profiles/); None until captured for the current kernel version.
+NCU_TRAFFIC = {}
+
+
+def algorithmic_bytes(name, g):
+    """Bytes one launch of a kernel must move at minimum (its inputs once, its outputs once)."""
+    HA, WA, HB, WB, KA, KB = g
+    R, C = HA + HB - 1, WA + WB - 1
+    P = 1 << max(4, math.ceil(math.log2(R)))
+    Q = 1 << max(4, math.ceil(math.log2(C)))
+    Qh = Q // 2 + 1
+    cs = 8  # FP32 complex
+    y = KA * KB * R * Qh * cs                 # column-inverted products, output rows only
+    spectra = (KA + KB) * Qh * P * cs
+    if name.startswith("pair_rows"):
+        return y + R * C * (8 + 4)            # Y in, MI (f64) + N (i32) out
+    if name.startswith("pair_cols"):
+        return spectra + y                    # spectra in, Y out
+    if name.startswith("fwd_cols_A"):
+        return KA * HA * Qh * cs + KA * Qh * P * cs
+    if name.startswith("fwd_cols_B"):
+        return KB * HB * Qh * cs + KB * Qh * P * cs
+    if name.startswith("fwd_rows_A"):
+        return HA * WA * 5 + KA * HA * Qh * cs
+    if name.startswith("fwd_rows_B"):
+        return HB * WB * 5 + KB * HB * Qh * cs
+    return 0
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(cfg, budget_s, rng_seed=7):
+    """Direct-method oracle on a bounded random sample of shifts of the same map.
+    Returns (shifts per second, shifts, seconds, threads)."""
+    import oracle
+    A, B = cfg["A"], cfg["B"]
+    HA, WA = A.shape
+    HB, WB = B.shape
+    rng = np.random.default_rng(rng_seed)
+
+    def sample(n):
+        return (rng.integers(-(HA - 1), HB, n).astype(np.int32), rng.integers(-(WA - 1), WB, n).astype(np.int32))
+
+    threads = oracle.max_threads()
+    n = max(8, threads)
+    while True:  # calibrate on growing samples until one takes >= 1 s (or a tenth of the budget)
+        dy, dx = sample(n)
+        t0 = time.perf_counter()
+        oracle.cmif_at(A, cfg["M_A"], B, cfg["M_B"], cfg["K_A"], cfg["K_B"], dy, dx)
+        el = time.perf_counter() - t0
+        if el >= min(1.0, budget_s / 10) or n > 10_000_000:
+            break
+        n *= 4
+    n = max(threads, int(n * budget_s / max(el, 1e-9)))
+    dy, dx = sample(n)
+    t0 = time.perf_counter()
+    oracle.cmif_at(A, cfg["M_A"], B, cfg["M_B"], cfg["K_A"], cfg["K_B"], dy, dx)
+    secs = time.perf_counter() - t0
+    return n / secs, n, secs, threads
+
+
+def run_reference(args, rank, world):
+    """The oracle (the direct method of Sec. 2.2) as the reference arm, on the host cores."""
+    if rank != 0:
+        return
+    import synth
+    cfg = synth.make_config(CONFIG_ID)
+    per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    n_tot, s_tot, thr = 0, 0.0, 1
+    for i in range(args.warmup + args.steps):
+        rate, n, secs, thr = cpu_oracle_rate(cfg, per_step, rng_seed=100 + i)
+        if i >= args.warmup:
+            rates.append(rate)
+            n_tot += n
+            s_tot += secs
+    value = n_tot / s_tot
+    shifts = (2 * 1024 - 1) ** 2
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * shifts / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "single-1024x1024-K16 (config 3)", "shifts_per_map": shifts},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": f"{n_tot} random shifts of the 1024^2 K=16 map over {args.steps} steps "
+                                   f"(direct method, FP64 entropies)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_profile_shape(args):
+    """Device step loop only, on a smaller planted pair (inputs and workspace of a few GB at most)."""
+    import torch
+    import paper_2106_14699_gb300 as cm
+    import synth
+    H, W = (int(v) for v in args.profile_shape.lower().split("x"))
+    rng = np.random.default_rng(5)
+    A_np, B_np = synth.planted_pair(rng, H, W, max(40, H * W // 500), 16, 16, (3, -5), 0.1, same_labels=True)
+    dev = torch.device("cuda", 0)
+    A, B = torch.from_numpy(A_np).to(dev), torch.from_numpy(B_np).to(dev)
+    R, C = 2 * H - 1, 2 * W - 1
+    mi = torch.empty((R, C), dtype=torch.float64, device=dev)
+    n = torch.empty((R, C), dtype=torch.int32, device=dev)
+    peak = torch.empty(24, dtype=torch.uint8, device=dev)
+    plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32)
+    for _ in range(args.warmup + args.steps):
+        plan.compute(A, None, B, None, mi, n, None, GAMMA, peak)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_shape": [H, W], "status": plan.status(),
+                      "workspace_gb": plan.workspace_bytes() / 1e9}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-shape", default=None,
+                    help="HxW: run only the device step loop on a planted pair of this size (for ncu captures)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.profile_shape:
+        run_profile_shape(args)
+        return
+
+    import torch
+    import paper_2106_14699_gb300 as cm
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    cfg = synth.make_config(CONFIG_ID)
+    A_np, B_np, MA_np, MB_np = cfg["A"], cfg["B"], cfg["M_A"], cfg["M_B"]
+    HA, WA = A_np.shape
+    HB, WB = B_np.shape
+    KA, KB = cfg["K_A"], cfg["K_B"]
+    R, C = HA + HB - 1, WA + WB - 1
+    shifts = R * C
+
+    A = torch.from_numpy(A_np).to(dev)
+    B = torch.from_numpy(B_np).to(dev)
+    MA = torch.from_numpy(MA_np).to(dev)
+    MB = torch.from_numpy(MB_np).to(dev)
+    mi = torch.empty((R, C), dtype=torch.float64, device=dev)
+    n = torch.empty((R, C), dtype=torch.int32, device=dev)
+    peak = torch.empty(24, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    plan = cm.Plan(HA, WA, HB, WB, KA, KB, cm.FP32)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.compute(A, MA, B, MB, mi, n, None, GAMMA, peak, stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    st = plan.status()
+    if st[0] != "OK":
+        raise SystemExit(f"device status after warm-up: {st}")
+
+    plan.set_profiling(True)
+    clk = ClockSampler(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = {}
+    launches = 0
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the step's events)
+        ev0[i].record(stream)
+        step()
+        ev1[i].record(stream)
+        for name, ms in plan.stage_times():  # synchronises; between steps
+            stage.setdefault(name, []).append(ms)
+            launches += 2 if name == "peak" else 1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    plan.set_profiling(False)
+    ms_steps = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    ms_per_step = sum(ms_steps) / len(ms_steps)
+    if dist:
+        t = torch.tensor([ms_per_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    st = plan.status()
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(A_np).pin_memory()
+        hB = torch.from_numpy(B_np).pin_memory()
+        hMA = torch.from_numpy(MA_np).pin_memory()
+        hMB = torch.from_numpy(MB_np).pin_memory()
+        hmi = torch.empty((R, C), dtype=torch.float64).pin_memory()
+        hpk = cm.Peak()
+        for _ in range(2):
+            plan.compute_host(hA, hMA, hB, hMB, hmi, None, GAMMA, hpk, stream)
+        if dist:
+            dist.barrier()
+        ts = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.compute_host(hA, hMA, hB, hMB, hmi, None, GAMMA, hpk, stream)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = sum(ts) / len(ts)
+        if dist:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = A_np.nbytes + B_np.nbytes + MA_np.nbytes + MB_np.nbytes
+        d2h = R * C * 8 + 24
+        e2e = {"value": shifts * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (largest mean launch time)
+    g = (HA, WA, HB, WB, KA, KB)
+    mean_ms = {k: sum(v) / len(v) for k, v in stage.items()}
+    dom = max(mean_ms, key=mean_ms.get)
+    peak_gbs, peak_kind = measured_peak_gbs()
+    alg = algorithmic_bytes(dom, g)
+    achieved = alg / (mean_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                "frac": achieved / peak_gbs, "traffic": NCU_TRAFFIC.get(dom), "kernel": dom,
+                "kernel_ms": mean_ms[dom], "algorithmic_bytes": alg, "peak_source": peak_kind}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, n_s, secs, thr = cpu_oracle_rate(cfg, 15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{n_s} random shifts of the 1024^2 K=16 map ({secs:.1f} s, direct method, FP64)"}
+
+    line = {
+        "metric": METRIC, "value": shifts * world / (ms_per_step * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "single-1024x1024-K16 (config 3)", "H": HA, "W": WA, "K_A": KA, "K_B": KB,
+                   "shifts_per_map": shifts, "angles": 1, "precision": "FP32 transforms, fixed-point entropy",
+                   "gamma": GAMMA, "l2": "flushed between steps (256 MB write), per-step CUDA events",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "stage_ms": {k: round(v, 4) for k, v in mean_ms.items()},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "device_status": {"status": st[0], "max_residual": st[1], "escalations": st[2]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * cmif.h -- C ABI of the GB300 CMIF library (libcmif.so).
+ *
+ * The cross-mutual information function (Eq. cmif) of two label images A
+ * and B with region-of-interest masks M_A, M_B (Sec. 3.1):
+ *
+ *     CMIF(chi; A, B) = I(A, T_chi[B]),   T_chi[B](x) = B(x + chi),
+ *
+ * the mutual information (Eq. mi / Eq. mientropy) of the label pairs
+ * (A(x), B(x + chi)) over the pixels where both masks are 1, for every
+ * integer displacement chi of the full linear range
+ *
+ *     chi = (dy, dx),  dy in [-(H_A-1), H_B-1],  dx in [-(W_A-1), W_B-1].
+ *
+ * It is computed by the frequency-domain method of Sec. 3.2: the joint
+ * counts C_AB^{a,b}(chi) are the cross-correlations (Eq. cc) of the level
+ * sets L_a[A] and L_b[B] (Eq. correlationjointhisto), computed with FFTs
+ * and rounded to integers, which makes them identical to the direct
+ * method's histogram counts (Sec. 3.4).  The marginal counts and N
+ * (Eq. correlationmarghisto, Eq. number) are the exact integer sums of the
+ * joint counts, and the entropies of Eq. finalentropy are reduced per shift
+ * in fixed point.  MI is in bits; 0/0 = 0 and 0 log 0 = 0, so MI = 0 where
+ * N = 0.
+ *
+ * Map layout (all maps): row-major, R = H_A + H_B - 1 rows by
+ * C = W_A + W_B - 1 columns; element (r, c) is chi = (r - (H_A-1), c - (W_A-1)).
+ *
+ * Images: A is int32 H_A x W_A row-major, M_A is uint8 H_A x W_A (nonzero = 1)
+ * or NULL for all ones; likewise B, M_B.  Where a mask is 1 the label must
+ * lie in [0, K); where it is 0 the label is ignored.
+ *
+ * Memory: every array argument of cmif_compute / cmif_align_rotations is a
+ * DEVICE pointer owned by the caller, on the plan's device.  The plan owns
+ * its workspace (allocated by cmif_plan_create*, freed by
+ * cmif_plan_destroy); compute calls allocate nothing.  Calls are
+ * asynchronous and stream-ordered on the given stream (a cudaStream_t; NULL
+ * is the legacy default stream).  A plan must not be used by two calls that
+ * may overlap in time (different streams, different threads).
+ *
+ * Errors: the return value reports argument and launch errors found on the
+ * host, synchronously.  Problems found on the device (a label out of range,
+ * a rounding residual the chosen precision could not bring under the guard)
+ * are recorded in the plan's device status word and read with
+ * cmif_get_status(), which synchronises.
+ */
+#ifndef CMIF_H
+#define CMIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cmif_plan_s* cmif_plan;
+
+typedef enum {
+    CMIF_OK = 0,
+    CMIF_ERR_INVALID_ARG = 1,      /* bad size, K, pointer, gamma, precision or flag          */
+    CMIF_ERR_LABEL_RANGE = 2,      /* device: a label under mask 1 lies outside [0, K)        */
+    CMIF_ERR_OOM = 3,              /* workspace allocation failed                             */
+    CMIF_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed                    */
+    CMIF_ERR_PRECISION = 5,        /* device: rounding residual >= 0.25 in the final precision */
+    CMIF_ERR_TIMEOUT = 6,          /* device: a bounded wait gave up                          */
+    CMIF_ERR_NOT_IMPLEMENTED = 7,  /* precision or mode not built                             */
+    CMIF_ERR_UNSUPPORTED = 8       /* size beyond the supported transform lengths             */
+} cmif_status;
+
+/* Arithmetic of the FFT correlations.  Counts are exact when every pre-rounding
+ * residual |c - round(c)| stays below 0.25 (checked on every call).
+ *   CMIF_FP32   : FP32 transforms (fast; exact for balanced labels up to ~1024^2)
+ *   CMIF_SPLIT32: two-term FP32 transforms (not built yet: CMIF_ERR_NOT_IMPLEMENTED)
+ *   CMIF_FP64   : FP64 transforms (exact everywhere in range; slow on GB300)
+ *   CMIF_AUTO   : FP32, re-run in FP64 on the device when the FP32 residual
+ *                 breaches the guard (no host round trip). */
+typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } cmif_precision;
+
+/* Plan flags. */
+#define CMIF_FLAG_DEBUG_COUNTS 1u /* allow a non-NULL counts output in cmif_compute */
+
+/* One argmax record of Alg. 1: the displacement chi = (dy, dx) maximising
+ * CMIF among shifts with N(chi) >= gamma * max N, for transform angle_idx
+ * (-1: identity / none).  24 bytes, naturally aligned. */
+typedef struct {
+    int32_t angle_idx;
+    int32_t dy;
+    int32_t dx;
+    int32_t n;
+    double mi;
+} cmif_peak;
+
+/* Create a plan for equal-sized images H x W with K_A, K_B labels.
+ * Same as cmif_plan_create_ex(out, H, W, H, W, K_A, K_B, prec, 0). */
+cmif_status cmif_plan_create(cmif_plan* out, int H, int W, int K_A, int K_B, cmif_precision prec);
+
+/* Create a plan (Sec. 3.1: domains X_A, X_B rectangular, any sizes).
+ *   H_A, W_A, H_B, W_B >= 1, H*W <= 2^22 per image; 1 <= K_A, K_B <= 64;
+ *   the transform sizes P >= H_A+H_B-1 and Q >= W_A+W_B-1 (powers of two)
+ *   must not exceed 4096 (else CMIF_ERR_UNSUPPORTED).
+ *   prec: see cmif_precision.  flags: CMIF_FLAG_*.
+ * Allocates the workspace on the current CUDA device, which becomes the
+ * plan's device.  On error *out is NULL. */
+cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B,
+                                cmif_precision prec, unsigned flags);
+
+/* Free the plan and its workspace (synchronises the plan's device). NULL is ignored. */
+cmif_status cmif_plan_destroy(cmif_plan plan);
+
+/* Bytes of device workspace the plan holds. */
+cmif_status cmif_plan_workspace_bytes(cmif_plan plan, size_t* bytes);
+
+/* The CMIF map of (A, M_A) and (B, M_B) over the full linear shift range
+ * (Eq. cmif, computed per Sec. 3.2), plus optionally N and the peak.
+ *   A, M_A, B, M_B : device images as described above (masks may be NULL)
+ *   mi_map  : device double[R*C] (required): MI in bits
+ *   n_map   : device int32[R*C] or NULL: N(chi) (Eq. number)
+ *   counts  : device int32[(K_A*K_B + K_A + K_B) * R*C] or NULL; only with
+ *             CMIF_FLAG_DEBUG_COUNTS.  Maps in order: joint C_AB^{a,b} for
+ *             a-major pairs (a*K_B + b), then C_A^a, then C_B^b.
+ *   gamma   : overlap fraction in [0, 1] of Alg. 1 for the peak
+ *   peak_dev: device cmif_peak* or NULL: the gamma-gated argmax of Alg. 1
+ *             (ties: lowest map index), angle_idx = 0
+ *   stream  : cudaStream_t
+ * Returns CMIF_ERR_INVALID_ARG for NULL A/B/mi_map, a counts pointer
+ * without the debug flag, or gamma outside [0, 1]. */
+cmif_status cmif_compute(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
+                         const uint8_t* M_B, double* mi_map, int32_t* n_map, int32_t* counts, double gamma,
+                         cmif_peak* peak_dev, void* stream);
+
+/* cmif_compute with HOST buffers: copies the images in, computes, copies
+ * mi_map (and n_map, peak when non-NULL) out, and synchronises the stream.
+ * Host pointers; the device staging buffers belong to the plan. */
+cmif_status cmif_compute_host(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
+                              const uint8_t* M_B, double* mi_map, int32_t* n_map, double gamma,
+                              cmif_peak* peak_host, void* stream);
+
+/* Device status of the last call on this plan (synchronises the plan's
+ * last stream).  device_side: CMIF_OK, or the first device problem in the
+ * order LABEL_RANGE, PRECISION, TIMEOUT.  max_residual: the largest
+ * pre-rounding residual of the authoritative precision.  escalations: FP64
+ * re-runs done by CMIF_AUTO.  Any output pointer may be NULL. */
+cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* max_residual, int* escalations);
+
+/* Launch timing (instrumentation, off by default).  When enabled, each
+ * compute call records a CUDA event pair on its stream around every kernel
+ * launch it makes; cmif_plan_stage_times (which synchronises) returns the
+ * last call's launches in order: *n = count, ms[i] = duration, names[i] =
+ * static kernel name, for i < max_n (ms, names may be NULL). */
+cmif_status cmif_plan_set_profiling(cmif_plan plan, int enable);
+cmif_status cmif_plan_stage_times(cmif_plan plan, int max_n, int* n, double* ms, const char** names);
+
+/* Static string for a status code. */
+const char* cmif_status_string(cmif_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMIF_H */

@@ -1,0 +1,188 @@
+"""Python binding of the GB300 CMIF library (``include/cmif.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libcmif.so``.  There is no CPU fallback; if the library is not
+built, every call raises.  PyTorch is used for device memory and streams.
+
+The names follow the C ABI: ``Plan`` wraps ``cmif_plan_create_ex`` /
+``cmif_compute`` / ``cmif_compute_host`` / ``cmif_get_status`` /
+``cmif_plan_destroy``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["FP32", "SPLIT32", "FP64", "AUTO", "Plan", "Peak", "CmifError", "lib", "STATUS_NAMES", "cmif"]
+
+FP32, SPLIT32, FP64, AUTO = 0, 1, 2, 3
+FLAG_DEBUG_COUNTS = 1
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "LABEL_RANGE", 3: "OOM", 4: "CUDA", 5: "PRECISION",
+                6: "TIMEOUT", 7: "NOT_IMPLEMENTED", 8: "UNSUPPORTED"}
+
+
+class CmifError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)}" if what else STATUS_NAMES.get(code, str(code)))
+
+
+class Peak(ctypes.Structure):
+    _fields_ = [("angle_idx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dx", ctypes.c_int32),
+                ("n", ctypes.c_int32), ("mi", ctypes.c_double)]
+
+
+EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_destroy", "cmif_plan_workspace_bytes",
+           "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
+           "cmif_plan_stage_times", "cmif_status_string"]
+
+_lib = None
+
+
+def lib():
+    """Load libcmif.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.LIBPATH
+        if not os.path.exists(path):
+            raise CmifError(4, f"{path} is not built (run __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(path)
+        P, I, D, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint
+        L.cmif_plan_create.argtypes = [ctypes.POINTER(P), I, I, I, I, I]
+        L.cmif_plan_create_ex.argtypes = [ctypes.POINTER(P), I, I, I, I, I, I, I, U]
+        L.cmif_plan_destroy.argtypes = [P]
+        L.cmif_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.cmif_compute.argtypes = [P, P, P, P, P, P, P, P, D, P, P]
+        L.cmif_compute_host.argtypes = [P, P, P, P, P, P, P, D, P, P]
+        L.cmif_get_status.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
+        L.cmif_plan_set_profiling.argtypes = [P, I]
+        L.cmif_plan_stage_times.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_char_p)]
+        L.cmif_status_string.argtypes = [I]
+        L.cmif_status_string.restype = ctypes.c_char_p
+        for name in EXPORTS[:-1]:
+            getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(code, what):
+    if code != 0:
+        raise CmifError(code, what)
+
+
+class Plan:
+    """A CMIF plan for images H_A x W_A and H_B x W_B with K_A, K_B labels."""
+
+    def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False):
+        self._h = ctypes.c_void_p()
+        flags = FLAG_DEBUG_COUNTS if debug_counts else 0
+        _check(lib().cmif_plan_create_ex(ctypes.byref(self._h), H_A, W_A, H_B, W_B, K_A, K_B, precision, flags),
+               "cmif_plan_create_ex")
+        self.H_A, self.W_A, self.H_B, self.W_B, self.K_A, self.K_B = H_A, W_A, H_B, W_B, K_A, K_B
+        self.precision = precision
+        self.R, self.C = H_A + H_B - 1, W_A + W_B - 1
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def workspace_bytes(self):
+        n = ctypes.c_size_t()
+        _check(lib().cmif_plan_workspace_bytes(self._h, ctypes.byref(n)), "cmif_plan_workspace_bytes")
+        return n.value
+
+    def compute(self, A, M_A, B, M_B, mi_map, n_map=None, counts=None, gamma=0.0, peak=None, stream=None):
+        """Device-pointer call (torch CUDA tensors or raw addresses); asynchronous."""
+        _check(lib().cmif_compute(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), _ptr(mi_map), _ptr(n_map),
+                                  _ptr(counts), float(gamma), _ptr(peak), _stream(stream)), "cmif_compute")
+
+    def compute_host(self, A, M_A, B, M_B, mi_map, n_map=None, gamma=0.0, peak=None, stream=None):
+        """Host-buffer call (numpy, ideally pinned); copies in and out, synchronises."""
+        pk = ctypes.byref(peak) if peak is not None else None
+        _check(lib().cmif_compute_host(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), _ptr(mi_map), _ptr(n_map),
+                                       float(gamma), pk, _stream(stream)), "cmif_compute_host")
+
+    def status(self):
+        """(device status name, max residual, escalations) of the last call; synchronises."""
+        ds, res, esc = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(lib().cmif_get_status(self._h, ctypes.byref(ds), ctypes.byref(res), ctypes.byref(esc)), "cmif_get_status")
+        return STATUS_NAMES.get(ds.value, ds.value), res.value, esc.value
+
+    def set_profiling(self, enable=True):
+        _check(lib().cmif_plan_set_profiling(self._h, 1 if enable else 0), "cmif_plan_set_profiling")
+
+    def stage_times(self, max_n=64):
+        """[(kernel name, ms)] of the last call's launches (profiling on); synchronises."""
+        n = ctypes.c_int()
+        ms = (ctypes.c_double * max_n)()
+        names = (ctypes.c_char_p * max_n)()
+        _check(lib().cmif_plan_stage_times(self._h, max_n, ctypes.byref(n), ms, names), "cmif_plan_stage_times")
+        return [(names[i].decode(), ms[i]) for i in range(min(n.value, max_n))]
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().cmif_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def cmif(A, M_A, B, M_B, K_A, K_B, precision=FP32, gamma=0.0, with_counts=False, plan=None, stream=None):
+    """Convenience: CMIF map of torch CUDA tensors.  Returns dict(mi, n, peak[, counts], status)."""
+    import torch
+    H_A, W_A = A.shape
+    H_B, W_B = B.shape
+    own = plan is None
+    if own:
+        plan = Plan(H_A, W_A, H_B, W_B, K_A, K_B, precision, debug_counts=with_counts)
+    dev = A.device
+    mi = torch.empty((plan.R, plan.C), dtype=torch.float64, device=dev)
+    n = torch.empty((plan.R, plan.C), dtype=torch.int32, device=dev)
+    counts = None
+    if with_counts:
+        counts = torch.empty((K_A * K_B + K_A + K_B, plan.R, plan.C), dtype=torch.int32, device=dev)
+    peak = torch.empty(24, dtype=torch.uint8, device=dev)
+    plan.compute(A, M_A, B, M_B, mi, n, counts, gamma, peak, stream)
+    st = plan.status()
+    pk = Peak.from_buffer_copy(peak.cpu().numpy().tobytes())
+    out = dict(mi=mi, n=n, peak=(pk.angle_idx, pk.dy, pk.dx, pk.n, pk.mi), status=st)
+    if with_counts:
+        out["counts"] = counts
+    if own:
+        plan.close()
+    return out

@@ -1,0 +1,35 @@
+// Shared host/device definitions of the CMIF library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+
+namespace cmif {
+
+// Device-side status word, one per plan; read back by cmif_get_status().
+struct DevStatus {
+    unsigned flags;        // STATUS_* bits below
+    unsigned res_bits[2];  // max |c - round(c)| seen, as float bits: [0] FP32 pass, [1] FP64 pass
+    int max_n;             // max_chi N(chi) of the last map (for the gamma gate of Alg. 1)
+    int escalations;       // number of FP32 -> FP64 re-runs
+    int pad[3];
+};
+enum : unsigned {
+    STATUS_LABEL_RANGE = 1u,  // a label under mask 1 lies outside [0, K)
+    STATUS_PRECISION = 2u,    // residual guard breached in the final precision
+    STATUS_TIMEOUT = 4u,      // a bounded device wait gave up
+    STATUS_ESCALATE = 8u,     // AUTO: FP32 residual breached, FP64 pass is authoritative
+};
+
+// Problem geometry of one CMIF map.
+struct Geom {
+    int HA, WA, HB, WB;  // image sizes
+    int KA, KB;          // label counts
+    int R, C;            // output map rows / cols: H_A+H_B-1, W_A+W_B-1
+    int P, Q;            // transform sizes (powers of two >= R, C)
+    int Qh;              // Q/2 + 1 half-spectrum columns
+    int Qs;              // padded row stride (complex elements) of row-major spectra
+};
+
+constexpr float kResidualGuard = 0.25f;  // a count whose pre-rounding residual reaches this is not trusted
+constexpr int kFixBits = 22;             // fixed-point scale of sum c*log2(c): units of 2^-22
+
+}  // namespace cmif

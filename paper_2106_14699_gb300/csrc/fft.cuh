@@ -1,0 +1,212 @@
+// Register / shared-memory FFT building blocks for the CMIF transforms.
+//
+// The paper computes every cross-correlation of Eq. correlationjointhisto
+// in the frequency domain with FFTs (Sec. 3.5, Eq. maincomplexity).  These
+// are the transforms, written for sm_103a:
+//
+//  * dft_reg<M>     : an M-point DFT (M = 2..32) held in one thread's
+//                     registers, radix-2 decimation in frequency, twiddles
+//                     folded to compile-time constants.  Output in
+//                     bit-reversed register order.
+//  * team_fft<M,R>  : a length N = R*M*M DFT done by a "team" of R groups of
+//                     M lanes (M points per lane).  The four-step split
+//                     N' = M*M needs a single shared-memory transpose (XOR
+//                     swizzled, conflict-free); R > 1 adds a radix-R
+//                     decimation-in-frequency pre-step fused into the loads,
+//                     so group r produces the outputs k = r (mod R).
+//
+// Sign convention: DIR = -1 is the forward transform X[k] = sum x[n] e^{-2 pi i kn/N},
+// DIR = +1 the unnormalised inverse.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cmif {
+
+template <typename T>
+struct cpx {
+    T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+// multiply by e^{DIR * i * theta} given (cos theta, sin theta)
+template <int DIR, typename T>
+__device__ __forceinline__ cpx<T> rot(cpx<T> a, T c, T s) {
+    if (DIR < 0) return {a.x * c + a.y * s, a.y * c - a.x * s};
+    return {a.x * c - a.y * s, a.y * c + a.x * s};
+}
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+__host__ __device__ constexpr int brev(int k, int M) {
+    int r = 0;
+    for (int b = 1, t = M >> 1; b < M; b <<= 1, t >>= 1)
+        if (k & b) r |= t;
+    return r;
+}
+
+// cos / sin of 2*pi*k/32 from first-octant constants, so that the symmetric
+// entries are exact mirror images.
+__host__ __device__ constexpr double c16(int r) {
+    return r == 0 ? 1.0 : r == 1 ? 0.98078528040323044913 : r == 2 ? 0.92387953251128675613
+         : r == 3 ? 0.83146961230254523708 : 0.70710678118654752440;
+}
+__host__ __device__ constexpr double s16(int r) {
+    return r == 0 ? 0.0 : r == 1 ? 0.19509032201612826785 : r == 2 ? 0.38268343236508977173
+         : r == 3 ? 0.55557023301960222474 : 0.70710678118654752440;
+}
+__host__ __device__ constexpr double cos32q(int k) { return k <= 4 ? c16(k) : s16(8 - k); }   // k in [0, 8]
+__host__ __device__ constexpr double sin32q(int k) { return k <= 4 ? s16(k) : c16(8 - k); }
+__host__ __device__ constexpr double cos32(int k) {
+    return k < 8 ? cos32q(k) : k < 16 ? -sin32q(k - 8) : k < 24 ? -cos32q(k - 16) : sin32q(k - 24);
+}
+__host__ __device__ constexpr double sin32(int k) {
+    return k < 8 ? sin32q(k) : k < 16 ? cos32q(k - 8) : k < 24 ? -sin32q(k - 16) : -cos32q(k - 24);
+}
+
+// d * e^{DIR * 2 pi i k / M}, with the trivial angles special-cased.
+template <int M, int DIR, typename T>
+__device__ __forceinline__ cpx<T> twc(cpx<T> d, int k) {
+    const int k32 = k * (32 / M);
+    if (k32 == 0) return d;
+    if (k32 == 8) return DIR < 0 ? cpx<T>{d.y, -d.x} : cpx<T>{-d.y, d.x};
+    if (k32 == 16) return {-d.x, -d.y};
+    if (k32 == 24) return DIR < 0 ? cpx<T>{-d.y, d.x} : cpx<T>{d.y, -d.x};
+    return rot<DIR>(d, (T)cos32(k32), (T)sin32(k32));
+}
+
+// In-register M-point DFT, natural order in, bit-reversed order out:
+// after the call v[brev(k, M)] = sum_n v_in[n] e^{DIR 2 pi i n k / M}.
+template <int M, int DIR, typename T>
+__device__ __forceinline__ void dft_reg(cpx<T> (&v)[M]) {
+#pragma unroll
+    for (int span = M / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int start = 0; start < M; start += 2 * span) {
+#pragma unroll
+            for (int j = 0; j < span; ++j) {
+                cpx<T> a = v[start + j], b = v[start + j + span];
+                v[start + j] = a + b;
+                v[start + j + span] = twc<M, DIR>(a - b, j * (M / (2 * span)));
+            }
+        }
+    }
+}
+
+}  // namespace cmif
+
+namespace cmif {
+
+// Lanes per group for a team transform: the largest power of two M with
+// M*M <= N, capped so that M complex values fit in registers (32 for FP32,
+// 16 for FP64).
+__host__ __device__ constexpr int team_m(int N, int mmax) {
+    int M = mmax;
+    while (M > 1 && M * M > N) M >>= 1;
+    return M;
+}
+template <typename T>
+__host__ __device__ constexpr int max_m() { return sizeof(T) == 4 ? 32 : 16; }
+
+// Twiddle tables in device memory, filled once per device from FP64 values.
+//   n[l][k]         = e^{-2 pi i k / 2^l},           k < 2^l
+//   sq[l][k1*M + j] = e^{-2 pi i j k1 / (M*M)},       M = 2^l, j, k1 < M
+template <typename T>
+struct Tw {
+    const cpx<T>* n[14];
+    const cpx<T>* sq[6];
+};
+
+template <int DIR, typename T>
+__device__ __forceinline__ cpx<T> twl(const cpx<T>* __restrict__ t, int k) {
+    cpx<T> w = t[k];
+    if (DIR > 0) w.y = -w.y;
+    return w;
+}
+
+// Shared-memory scratch of one group of M lanes.  FP32 transposes go through
+// shared memory in two halves (real parts, then imaginary parts), so a group
+// needs M*M floats; groups narrower than a warp get M floats of padding so
+// that the groups of one warp hit disjoint banks.  FP64 transposes complex
+// values directly.
+template <int M>
+__host__ __device__ constexpr int grp_pad() { return M < 32 ? M : 0; }
+template <typename T, int M>
+__host__ __device__ constexpr int grp_scratch_bytes() {
+    return sizeof(T) == 4 ? (M * M + grp_pad<M>()) * 4 : M * M * (int)sizeof(cpx<T>);
+}
+
+// Length N = R*M*M transform by a team of R groups x M lanes.
+//   load(n)  : x[n] for n in [0, N)
+//   r, j     : this lane's group and lane-in-group
+//   sm       : this group's scratch (grp_scratch_bytes<T, M>() bytes of shared memory)
+//   twq      : Tw::sq for this M;  twn : Tw::n for N (used when R > 1)
+// Result: v[brev(k2, M)] = X[R*(j + M*k2) + r], k2 in [0, M).
+// Every lane of every warp taking part must call this (it uses __syncwarp).
+template <int M, int R, int DIR, typename T, typename Load>
+__device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
+                                         const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
+    constexpr int NQ = M * M;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const int m = j + M * i;
+        if constexpr (R == 1) {
+            v[i] = load(m);
+        } else {
+            // radix-R decimation in frequency: y_r[m] = w_N^{m r} sum_s x[m + s NQ] w_R^{s r}
+            cpx<T> acc = load(m);
+#pragma unroll
+            for (int s = 1; s < R; ++s) {
+                cpx<T> x = load(m + s * NQ);
+                if constexpr (R == 2) {
+                    acc = (r & 1) ? acc - x : acc + x;
+                } else {
+                    acc = acc + cmul(x, twl<DIR>(twn, ((s * r) % R) * NQ));
+                }
+            }
+            v[i] = (r == 0) ? acc : cmul(acc, twl<DIR>(twn, m * r));
+        }
+    }
+    dft_reg<M, DIR>(v);  // v[brev(k1)] = A[j][k1]
+#pragma unroll
+    for (int k1 = 1; k1 < M; ++k1) v[brev(k1, M)] = cmul(v[brev(k1, M)], twl<DIR>(twq, k1 * M + j));
+    if constexpr (sizeof(T) == 4) {
+        float* sf = reinterpret_cast<float*>(sm);
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) sf[k1 * M + (j ^ k1)] = v[brev(k1, M)].x;
+        __syncwarp();
+#pragma unroll
+        for (int n2 = 0; n2 < M; ++n2) v[n2].x = sf[j * M + (n2 ^ j)];
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) sf[k1 * M + (j ^ k1)] = v[brev(k1, M)].y;
+        __syncwarp();
+#pragma unroll
+        for (int n2 = 0; n2 < M; ++n2) v[n2].y = sf[j * M + (n2 ^ j)];
+        __syncwarp();
+    } else {
+        cpx<T>* sc = reinterpret_cast<cpx<T>*>(sm);
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) sc[k1 * M + (j ^ k1)] = v[brev(k1, M)];
+        __syncwarp();
+#pragma unroll
+        for (int n2 = 0; n2 < M; ++n2) v[n2] = sc[j * M + (n2 ^ j)];
+        __syncwarp();
+    }
+    dft_reg<M, DIR>(v);  // v[brev(k2)] = X_r[j + M k2]
+}
+
+}  // namespace cmif

@@ -1,0 +1,431 @@
+// CMIF kernels: the frequency-domain method of Sec. 3.2.
+//
+//   fwd_rows   : level sets L_a[X] of one label image (Sec. 3.1), two planes
+//                packed per complex row FFT of length Q, unpacked into the
+//                half spectra of both planes.  Also checks labels in range.
+//   fwd_cols   : column FFT of length P -> 2-D half spectra F[plane][kx][ky].
+//   pair_cols  : for every label pair (a, b): conj(F[L_a A]) * F[L_b B] (the
+//                correlation theorem for Eq. cc), inverse column FFT -> Y.
+//   pair_rows  : inverse row FFT (complex-to-real, length Q) of every pair's
+//                Y row, rounded to integer joint counts C_AB^{a,b}(chi)
+//                (Eq. correlationjointhisto; rounding per Sec. 3.2), fused
+//                with the per-shift entropy reduction: the marginals
+//                C_A^a = sum_b C_AB^{a,b}, C_B^b = sum_a C_AB^{a,b} and
+//                N = sum_a C_A^a (Eq. number), and
+//                MI = log2 N + (sum c log2 c (joint) - sum (marginals)) / N,
+//                which is Eq. finalentropy + Eq. mientropy rearranged.  The
+//                K_A*K_B count maps never reach global memory.
+//   peak       : the gamma-gated argmax of Alg. 1 for one map.
+#pragma once
+#include <cstdint>
+#include "common.h"
+#include "fft.cuh"
+
+namespace cmif {
+
+// ---------------------------------------------------------------------------
+// c * log2(c) for an exact non-negative integer c < 2^23 held in a float,
+// in fixed point (units of 2^-kFixBits) so that per-shift sums are exact,
+// order independent and cheap (integer adds).  log2 of the mantissa comes
+// from the MUFU lg2 approximation.
+__device__ __forceinline__ long long clog2c_fixed(float c) {
+    if (c < 1.5f) return 0;  // 0 log 0 = 0 (Sec. 3.2) and 1 log 1 = 0
+    const int ci = __float_as_int(c + 8388608.0f) - 0x4B000000;
+    const int bits = __float_as_int(c);
+    const int e = (bits >> 23) - 127;
+    const float m = __int_as_float((bits & 0x7FFFFF) | 0x3F800000);
+    const float lm = __log2f(m);
+    const int lmi = __float_as_int(fmaf(lm, (float)(1 << kFixBits), 12582912.0f)) - 0x4B400000;
+    const int L = (e << kFixBits) + lmi;
+    return (long long)ci * (long long)L;
+}
+
+// MI(chi) = (S + N log2 N) / N, where S = sum_joint c log2 c - sum_A - sum_B and
+// every c log2 c term (N log2 N included) comes from clog2c_fixed, so that MI is
+// exactly 0 whenever the entropies cancel exactly (e.g. a single label).
+__device__ __forceinline__ double mi_finish(long long S, int N) {
+    if (N <= 0) return 0.0;  // 0/0 = 0: no overlap, no information (Sec. 3.2)
+    const long long Sp = S + clog2c_fixed((float)N);
+    const float sh = (float)Sp;
+    const long long rem = Sp - (long long)sh;
+    const float sl = (float)rem;
+    const float fN = (float)N;
+    const float inv = 1.0f / fN;
+    const float q1 = sh * inv;
+    const float r1 = fmaf(-q1, fN, sh) + sl;
+    const float q2 = r1 * inv;
+    return ((double)q1 + (double)q2) * (1.0 / (double)(1 << kFixBits));
+}
+
+__device__ __forceinline__ void atomic_max_float_pos(unsigned* addr, float v) {
+    atomicMax(addr, __float_as_uint(v));  // v >= 0: float order = unsigned order
+}
+
+template <typename T>
+__device__ __forceinline__ T rint_t(T v);
+template <>
+__device__ __forceinline__ float rint_t<float>(float v) { return rintf(v); }
+template <>
+__device__ __forceinline__ double rint_t<double>(double v) { return rint(v); }
+
+// Map a circular shift index (0..n-1) to the output map index, or -1 when the
+// shift lies in the zero-padding gap (cannot happen for in-range shifts).
+__device__ __forceinline__ int circ_to_out(int s, int n, int lo_count /*H_A or W_A*/, int hi_max /*H_B-1*/) {
+    if (s <= hi_max) return s + lo_count - 1;
+    if (s >= n - (lo_count - 1)) return s - n + lo_count - 1;
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Team geometry for a transform of length N in precision T.
+template <typename T, int N>
+struct TeamGeom {
+    static constexpr int M = team_m(N, max_m<T>());
+    static constexpr int R = N / (M * M);
+    static constexpr int TEAM = R * M;                                        // lanes
+    static constexpr int SCRATCH = R * grp_scratch_bytes<T, M>();            // bytes of FFT scratch
+};
+
+// ---------------------------------------------------------------------------
+// Forward row transforms.  Item = (row y, plane pair pp): planes 2pp, 2pp+1.
+template <typename T, int Q>
+struct FwdRowsCfg {
+    using G = TeamGeom<T, Q>;
+    static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
+    static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
+    static constexpr int THREADS = TPB * TEAM;
+    static constexpr int REGION = (int)(Q * sizeof(cpx<T>)) > G::SCRATCH ? (int)(Q * sizeof(cpx<T>)) : G::SCRATCH;
+    static constexpr size_t SMEM = (size_t)TPB * REGION;
+};
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(FwdRowsCfg<T, Q>::THREADS)
+k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, int H, int W, int K, int Qs,
+           cpx<T>* __restrict__ T1, Tw<T> tw, DevStatus* __restrict__ st, int conditional) {
+    using C = FwdRowsCfg<T, Q>;
+    if (conditional && !(st->flags & STATUS_ESCALATE)) return;
+    constexpr int M = C::M, R = C::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
+    const int npp = (K + 1) / 2;
+    const long long item = (long long)blockIdx.x * C::TPB + team;
+    const bool active = item < (long long)H * npp;
+    const int y = active ? (int)(item / npp) : 0, pp = active ? (int)(item % npp) : 0;
+    const int la = 2 * pp, lb = 2 * pp + 1;
+    unsigned char* region = smem_raw + (size_t)team * C::REGION;
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(region);
+    const int32_t* xr = X + (size_t)y * W;
+    const uint8_t* mr = MX ? MX + (size_t)y * W : nullptr;
+    bool bad = false;
+    auto load = [&](int x) -> cpx<T> {
+        if (!active || x >= W) return {T(0), T(0)};
+        const int lab = xr[x];
+        const bool m = mr ? (mr[x] != 0) : true;
+        if (m && (lab < 0 || lab >= K)) bad = true;
+        return {(m && lab == la) ? T(1) : T(0), (m && lab == lb) ? T(1) : T(0)};
+    };
+    cpx<T> v[M];
+    team_fft<M, R, -1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)], tw.n[ilog2c(Q)]);
+    if (bad && pp == 0) atomicOr(&st->flags, STATUS_LABEL_RANGE);
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) sm[R * (j + M * k2) + r] = v[brev(k2, M)];
+    __syncthreads();
+    if (!active) return;
+    const T h = T(0.5);
+    for (int k = lt; k <= Q / 2; k += C::TEAM) {
+        const cpx<T> a = sm[k], b = sm[(Q - k) & (Q - 1)];
+        // F_la = (X[k] + conj X[-k]) / 2,  F_lb = (X[k] - conj X[-k]) / (2i)
+        T1[((size_t)la * H + y) * Qs + k] = {h * (a.x + b.x), h * (a.y - b.y)};
+        if (lb < K) T1[((size_t)lb * H + y) * Qs + k] = {h * (a.y + b.y), h * (b.x - a.x)};
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward column transforms.  Item = (plane, kx).
+template <typename T, int P>
+struct ColCfg {
+    using G = TeamGeom<T, P>;
+    static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
+    static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
+    static constexpr int THREADS = TPB * TEAM;
+    static constexpr size_t SMEM = (size_t)TPB * G::SCRATCH;
+};
+
+template <typename T, int P>
+__global__ void __launch_bounds__(ColCfg<T, P>::THREADS)
+k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cpx<T>* __restrict__ F, Tw<T> tw,
+           const DevStatus* __restrict__ st, int conditional) {
+    using C = ColCfg<T, P>;
+    if (conditional && !(st->flags & STATUS_ESCALATE)) return;
+    constexpr int M = C::M, R = C::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
+    const int kx = blockIdx.x * C::TPB + team, plane = blockIdx.y;
+    const bool active = kx < Qh;
+    const cpx<T>* col = T1 + (size_t)plane * H * Qs + kx;
+    auto load = [&](int y) -> cpx<T> {
+        if (!active || y >= H) return {T(0), T(0)};
+        return col[(size_t)y * Qs];
+    };
+    cpx<T> v[M];
+    team_fft<M, R, -1>(v, r, j, load, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(),
+                       tw.sq[ilog2c(M)], tw.n[ilog2c(P)]);
+    if (!active) return;
+    cpx<T>* out = F + ((size_t)plane * Qh + kx) * P;
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) out[R * (j + M * k2) + r] = v[brev(k2, M)];
+}
+
+// ---------------------------------------------------------------------------
+// Pair product + inverse column transform.  Block = (pair, kx block): pairs
+// vary fastest so that the blocks resident at one time read the same few
+// spectrum columns (L2 reuse).  The transformed columns are transposed
+// through shared memory in two halves of rows and written as row chunks of
+// TPB adjacent kx (full 32-byte sectors).
+template <typename T, int P>
+struct PairColsCfg {
+    using G = TeamGeom<T, P>;
+    static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
+    static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
+    static constexpr int THREADS = TPB * TEAM;
+    static constexpr int TS = TPB + 1;  // tile row stride (complex), padded
+    static constexpr size_t TILE = (size_t)(P / 2) * TS * sizeof(cpx<T>);
+    static constexpr size_t FFT = (size_t)TPB * G::SCRATCH;
+    static constexpr size_t SMEM = TILE > FFT ? TILE : FFT;
+    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;
+};
+
+template <typename T, int P>
+__global__ void __launch_bounds__(PairColsCfg<T, P>::THREADS, PairColsCfg<T, P>::MIN_BLOCKS)
+k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KB, int Qh, int HA, int HB,
+            T scale, int Rout, int Qs, cpx<T>* __restrict__ Y, Tw<T> tw,
+            const DevStatus* __restrict__ st, int conditional) {
+    using C = PairColsCfg<T, P>;
+    if (conditional && !(st->flags & STATUS_ESCALATE)) return;
+    constexpr int M = C::M, R = C::R, TPB = C::TPB, TS = C::TS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* tile = reinterpret_cast<cpx<T>*>(smem_raw);
+    const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
+    const int pair = blockIdx.x, kx0 = blockIdx.y * TPB, kx = kx0 + team;
+    const int a = pair / KB, b = pair % KB;
+    const bool active = kx < Qh;
+    const cpx<T>* fa = FA + ((size_t)a * Qh + (active ? kx : 0)) * P;
+    const cpx<T>* fb = FB + ((size_t)b * Qh + (active ? kx : 0)) * P;
+    auto load = [&](int ky) -> cpx<T> {
+        if (!active) return {T(0), T(0)};
+        const cpx<T> z = cmulc(fb[ky], fa[ky]);  // conj(F_a) F_b
+        return {z.x * scale, z.y * scale};
+    };
+    cpx<T> v[M];
+    team_fft<M, R, +1>(v, r, j, load, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(),
+                       tw.sq[ilog2c(M)], tw.n[ilog2c(P)]);
+    cpx<T>* yp = Y + (size_t)pair * Rout * Qs;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        __syncthreads();
+#pragma unroll
+        for (int k2 = h * (M / 2); k2 < (h + 1) * (M / 2); ++k2)
+            tile[(size_t)(R * (j + M * k2) + r - h * (P / 2)) * TS + team] = v[brev(k2, M)];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < (P / 2) * TPB; idx += C::THREADS) {
+            const int rl = idx / TPB, t = idx - rl * TPB, k = kx0 + t;
+            if (k >= Qh) continue;
+            const int orow = circ_to_out(rl + h * (P / 2), P, HA, HB - 1);
+            if (orow < 0) continue;
+            yp[(size_t)orow * Qs + k] = tile[(size_t)rl * TS + t];
+        }
+    }
+}
+
+template <typename T, int P>
+constexpr size_t pair_cols_smem() {
+    return PairColsCfg<T, P>::SMEM;
+}
+
+// ---------------------------------------------------------------------------
+// Inverse row transform (complex-to-real, length Q) + fused entropy epilogue.
+// One block per output row (grid-stride).  Per round, NT teams transform NT
+// pairs (a-major order); each thread then owns fixed shift positions p and
+// accumulates, pair by pair, the joint term T(c), the running A-marginal of
+// the current label a, and the B-marginal C_B^b(p) (shared or global memory).
+// The rounded counts reach the owners through the teams' scratch, in HALVES
+// passes (two for FP32, whose scratch holds half a row).
+template <typename T, int Q>
+struct RowCfg {
+    static constexpr int L = Q / 2;
+    using G = TeamGeom<T, L>;
+    static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
+    static constexpr int BT_TARGET = sizeof(T) == 4 ? 512 : 256;
+    static constexpr int NT = TEAM >= BT_TARGET ? 1 : BT_TARGET / TEAM;
+    static constexpr int THREADS = NT * TEAM;
+    static constexpr int HALVES = sizeof(T) == 4 ? 2 : 1;
+    static constexpr int QH = Q / HALVES;                      // positions per pass
+    static constexpr int UH = (QH + THREADS - 1) / THREADS;    // positions per thread per pass
+    static constexpr int U = HALVES * UH;
+    static constexpr int REGION = G::SCRATCH;                  // >= QH floats
+    static constexpr size_t TEAM_SMEM = (size_t)NT * REGION;
+    static_assert(REGION >= QH * 4, "team scratch must hold one pass of rounded counts");
+};
+
+template <typename T, int Q, bool CB_SMEM>
+__global__ void __launch_bounds__(RowCfg<T, Q>::THREADS, 1)
+k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ cb_global,
+            double* __restrict__ mi_map, int32_t* __restrict__ n_map, int32_t* __restrict__ counts,
+            DevStatus* __restrict__ st, int prec_slot, int conditional) {
+    using C = RowCfg<T, Q>;
+    constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, BT = C::THREADS;
+    constexpr int HALVES = C::HALVES, QH = C::QH;
+    if (conditional && !(st->flags & STATUS_ESCALATE)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* cb = CB_SMEM ? reinterpret_cast<float*>(smem_raw + C::TEAM_SMEM)
+                        : cb_global + (size_t)blockIdx.x * g.KB * Q;
+    const int tid = threadIdx.x, team = tid / C::TEAM, lt = tid % C::TEAM, r = lt / M, j = lt % M;
+    unsigned char* region = smem_raw + (size_t)team * C::REGION;
+    const int KA = g.KA, KB = g.KB, npairs = KA * KB, Rout = g.R, Cout = g.C, Qs = g.Qs;
+    const size_t RC = (size_t)Rout * Cout;
+    const cpx<T>* twq_c2r = tw.n[ilog2c(Q)];
+    float res_max = 0.f;
+    int row_max_n = 0;
+
+    for (int row = blockIdx.x; row < Rout; row += gridDim.x) {
+        long long S[U];
+        float CA[U];
+        int N[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) { S[u] = 0; CA[u] = 0.f; N[u] = 0; }
+        for (int b = 0; b < KB; ++b)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int pl = tid + BT * (u % UH), p = (u / UH) * QH + pl;
+                if (pl < QH) cb[(size_t)b * Q + p] = 0.f;
+            }
+        int cur_a[HALVES];
+#pragma unroll
+        for (int hf = 0; hf < HALVES; ++hf) cur_a[hf] = 0;
+        for (int base = 0; base < npairs; base += NT) {
+            const int pair = base + team;
+            const bool act = pair < npairs;
+            const cpx<T>* yr = Y + ((size_t)(act ? pair : 0) * Rout + row) * Qs;
+            // Hermitian split: z = IDFT_L(E + iO), z[m] = x[2m] + i x[2m+1]
+            auto load = [&](int k) -> cpx<T> {
+                if (!act) return {T(0), T(0)};
+                const cpx<T> yk = yr[k], ym = yr[L - k];
+                const cpx<T> e = {yk.x + ym.x, yk.y - ym.y};
+                const cpx<T> d = {yk.x - ym.x, yk.y + ym.y};
+                const cpx<T> o = cmul(d, twl<+1>(twq_c2r, k));
+                return {e.x - o.y, e.y + o.x};
+            };
+            cpx<T> v[M];
+            team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)],
+                               tw.n[ilog2c(L)]);
+            // round to the nearest integer; track the worst residual (the exactness guard)
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const T cr = rint_t<T>(v[k].x), ci = rint_t<T>(v[k].y);
+                res_max = fmaxf(res_max, fmaxf((float)fabs(v[k].x - cr), (float)fabs(v[k].y - ci)));
+                v[k].x = cr;
+                v[k].y = ci;
+            }
+            const int nt = min(NT, npairs - base);
+            const int a0 = base / KB, b0 = base - a0 * KB;
+#pragma unroll
+            for (int hf = 0; hf < HALVES; ++hf) {
+                __syncthreads();  // all scratch reads (FFT or previous pass) done
+                float2* ob = reinterpret_cast<float2*>(region);
+#pragma unroll
+                for (int k2 = hf * (M / HALVES); k2 < (hf + 1) * (M / HALVES); ++k2) {
+                    const int m = R * (j + M * k2) + r - hf * (L / HALVES);
+                    const cpx<T> z = v[brev(k2, M)];
+                    ob[m] = make_float2((float)z.x, (float)z.y);
+                }
+                __syncthreads();
+                int a = a0, b = b0;
+                for (int t = 0; t < nt; ++t) {
+                    if (a != cur_a[hf]) {  // uniform: the A-marginal of label cur_a is complete
+#pragma unroll
+                        for (int uh = 0; uh < UH; ++uh) {
+                            const int u = hf * UH + uh, pl = tid + BT * uh;
+                            if (pl >= QH) continue;
+                            S[u] -= clog2c_fixed(CA[u]);
+                            N[u] += (int)CA[u];
+                            if (counts) {
+                                const int c = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
+                                if (c >= 0) counts[((size_t)npairs + cur_a[hf]) * RC + (size_t)row * Cout + c] = (int)CA[u];
+                            }
+                            CA[u] = 0.f;
+                        }
+                        cur_a[hf] = a;
+                    }
+                    const float* obt = reinterpret_cast<const float*>(smem_raw + (size_t)t * C::REGION);
+                    float* cbb = cb + (size_t)b * Q + hf * QH;
+#pragma unroll
+                    for (int uh = 0; uh < UH; ++uh) {
+                        const int u = hf * UH + uh, pl = tid + BT * uh;
+                        if (pl >= QH) continue;
+                        const float c = obt[pl];
+                        S[u] += clog2c_fixed(c);
+                        CA[u] += c;
+                        cbb[pl] += c;
+                        if (counts) {
+                            const int cc = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
+                            if (cc >= 0) counts[(size_t)(base + t) * RC + (size_t)row * Cout + cc] = (int)c;
+                        }
+                    }
+                    if (++b == KB) { b = 0; ++a; }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int pl = tid + BT * (u % UH), p = (u / UH) * QH + pl;
+            if (pl >= QH) continue;
+            const int cidx = circ_to_out(p, Q, g.WA, g.WB - 1);
+            S[u] -= clog2c_fixed(CA[u]);
+            N[u] += (int)CA[u];
+            if (counts && cidx >= 0) counts[((size_t)npairs + cur_a[u / UH]) * RC + (size_t)row * Cout + cidx] = (int)CA[u];
+            for (int b = 0; b < KB; ++b) {
+                const float cbv = cb[(size_t)b * Q + p];
+                S[u] -= clog2c_fixed(cbv);
+                if (counts && cidx >= 0) counts[((size_t)npairs + KA + b) * RC + (size_t)row * Cout + cidx] = (int)cbv;
+            }
+            if (cidx < 0) continue;
+            const size_t o = (size_t)row * Cout + cidx;
+            mi_map[o] = mi_finish(S[u], N[u]);
+            if (n_map) n_map[o] = N[u];
+            row_max_n = max(row_max_n, N[u]);
+        }
+        __syncthreads();
+    }
+    // block reductions of the residual and max N
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        res_max = fmaxf(res_max, __shfl_xor_sync(0xffffffffu, res_max, off));
+        row_max_n = max(row_max_n, __shfl_xor_sync(0xffffffffu, row_max_n, off));
+    }
+    if ((tid & 31) == 0) {
+        atomic_max_float_pos(&st->res_bits[prec_slot], res_max);
+        atomicMax(&st->max_n, row_max_n);
+    }
+}
+
+template <typename T, int Q>
+constexpr size_t pair_rows_smem(int KB, bool cb_smem) {
+    return RowCfg<T, Q>::TEAM_SMEM + (cb_smem ? (size_t)KB * Q * sizeof(float) : 0);
+}
+
+// ---------------------------------------------------------------------------
+// gamma-gated argmax of Alg. 1 over one map: N_cal = gamma * max N; best MI
+// among shifts with N >= N_cal; ties to the lowest map index.
+struct PeakPart {
+    double mi;
+    long long idx;
+};
+
+__global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __restrict__ n, long long RC,
+                               const DevStatus* __restrict__ st, double gamma, PeakPart* __restrict__ parts);
+__global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, const double* __restrict__ mi,
+                             const int32_t* __restrict__ n, int HA, int WA, int Cout, int angle_idx,
+                             void* __restrict__ peak_out);
+
+}  // namespace cmif

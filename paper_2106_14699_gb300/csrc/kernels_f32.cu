@@ -1,0 +1,5 @@
+// FP32-transform instantiation of the CMIF launch sequence.
+#include "pipeline_impl.cuh"
+namespace cmif {
+CMIF_INSTANTIATE(float)
+}

@@ -1,0 +1,219 @@
+// Peak search (Alg. 1), status bookkeeping and twiddle tables.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "kernels.cuh"
+#include "misc.h"
+
+namespace cmif {
+
+// ---------------------------------------------------------------------------
+// gamma-gated argmax (Alg. 1): N_cal = gamma * max_chi N; chi* maximises MI
+// among shifts with N >= N_cal; ties go to the lowest map index.
+__device__ __forceinline__ bool better(double m1, long long i1, double m2, long long i2) {
+    return m1 > m2 || (m1 == m2 && i1 < i2);
+}
+
+__global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __restrict__ n, long long RC,
+                               const DevStatus* __restrict__ st, double gamma, PeakPart* __restrict__ parts) {
+    const double thr = gamma * (double)st->max_n;
+    double bm = -INFINITY;
+    long long bi = -1;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < RC; i += (long long)gridDim.x * blockDim.x) {
+        if ((double)n[i] >= thr) {
+            const double m = mi[i];
+            if (bi < 0 || better(m, i, bm, bi)) { bm = m; bi = i; }
+        }
+    }
+    __shared__ double sm_m[32];
+    __shared__ long long sm_i[32];
+    for (int off = 16; off > 0; off >>= 1) {
+        const double om = __shfl_xor_sync(0xffffffffu, bm, off);
+        const long long oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (oi >= 0 && (bi < 0 || better(om, oi, bm, bi))) { bm = om; bi = oi; }
+    }
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) { sm_m[w] = bm; sm_i[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k)
+            if (sm_i[k] >= 0 && (bi < 0 || better(sm_m[k], sm_i[k], bm, bi))) { bm = sm_m[k]; bi = sm_i[k]; }
+        parts[blockIdx.x] = {bm, bi};
+    }
+}
+
+__global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, const double* __restrict__ mi,
+                             const int32_t* __restrict__ n, int HA, int WA, int Cout, int angle_idx,
+                             void* __restrict__ peak_out) {
+    double bm = -INFINITY;
+    long long bi = -1;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x)
+        if (parts[k].idx >= 0 && (bi < 0 || better(parts[k].mi, parts[k].idx, bm, bi))) { bm = parts[k].mi; bi = parts[k].idx; }
+    __shared__ double sm_m[32];
+    __shared__ long long sm_i[32];
+    for (int off = 16; off > 0; off >>= 1) {
+        const double om = __shfl_xor_sync(0xffffffffu, bm, off);
+        const long long oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (oi >= 0 && (bi < 0 || better(om, oi, bm, bi))) { bm = om; bi = oi; }
+    }
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) { sm_m[w] = bm; sm_i[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int k = 1; k < nw; ++k)
+        if (sm_i[k] >= 0 && (bi < 0 || better(sm_m[k], sm_i[k], bm, bi))) { bm = sm_m[k]; bi = sm_i[k]; }
+    PeakRec* p = reinterpret_cast<PeakRec*>(peak_out);
+    if (bi < 0) { *p = {-1, 0, 0, 0, 0.0}; return; }
+    p->angle_idx = angle_idx;
+    p->dy = (int)(bi / Cout) - (HA - 1);
+    p->dx = (int)(bi % Cout) - (WA - 1);
+    p->n = n[bi];
+    p->mi = bm;
+}
+
+// AUTO: escalate to the FP64 pass when the FP32 residual reached the guard.
+__global__ void k_check_escalate(DevStatus* st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (__uint_as_float(st->res_bits[0]) >= kResidualGuard) {
+            st->flags |= STATUS_ESCALATE;
+            st->escalations += 1;
+        }
+    }
+}
+
+// Final verdict on the authoritative precision's residual.
+__global__ void k_finalize(DevStatus* st, int slot_if_escalated, int slot_default) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int slot = (st->flags & STATUS_ESCALATE) ? slot_if_escalated : slot_default;
+        if (__uint_as_float(st->res_bits[slot]) >= kResidualGuard) st->flags |= STATUS_PRECISION;
+    }
+}
+
+cudaError_t launch_peak(const double* mi, const int32_t* n, long long RC, const DevStatus* st, double gamma,
+                        PeakPart* parts, int nparts, int HA, int WA, int Cout, int angle_idx, void* peak_out,
+                        cudaStream_t s) {
+    k_peak_partial<<<nparts, 256, 0, s>>>(mi, n, RC, st, gamma, parts);
+    k_peak_final<<<1, 256, 0, s>>>(parts, nparts, mi, n, HA, WA, Cout, angle_idx, peak_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_escalate(DevStatus* st, cudaStream_t s) {
+    k_check_escalate<<<1, 32, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s) {
+    k_finalize<<<1, 32, 0, s>>>(st, slot_if_escalated, slot_default);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Twiddle tables: e^{-2 pi i k / N} evaluated in FP64 with octant symmetry
+// (so mirrored entries are exact negatives / swaps), then rounded to the
+// table precision.
+static void host_twiddle(long long k, long long N, double* c, double* s) {
+    k %= N;
+    if (N <= 2) {
+        *c = (k == 0) ? 1.0 : -1.0;
+        *s = 0.0;
+        return;
+    }
+    const long long q4 = N / 4;  // N is a power of two >= 4
+    const long long qd = k / q4, r = k - qd * q4;
+    double cu, su;
+    if (2 * r <= q4) {
+        const double t = 2.0 * M_PI * (double)r / (double)N;
+        cu = std::cos(t);
+        su = std::sin(t);
+    } else {
+        const double t = 2.0 * M_PI * (double)(q4 - r) / (double)N;
+        cu = std::sin(t);
+        su = std::cos(t);
+    }
+    double cc, ss;  // cos, sin of 2 pi k / N
+    switch (qd) {
+        case 0: cc = cu; ss = su; break;
+        case 1: cc = -su; ss = cu; break;
+        case 2: cc = -cu; ss = -su; break;
+        default: cc = su; ss = -cu; break;
+    }
+    *c = cc;
+    *s = -ss;  // e^{-i t}
+}
+
+struct DevTables {
+    void* buf = nullptr;
+    Tw<float> tf{};
+    Tw<double> td{};
+};
+
+static std::mutex g_tw_mu;
+static DevTables g_tw[64];
+
+cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    DevTables& t = g_tw[device];
+    if (!t.buf) {
+        // layout: for l = 0..13 the N = 2^l tables, then for l = 0..5 the (2^l)^2 square tables;
+        // first all FP64, then all FP32.
+        std::vector<double> re, im;
+        std::vector<size_t> off_n(14), off_sq(6);
+        for (int l = 0; l < 14; ++l) {
+            off_n[l] = re.size();
+            const long long N = 1LL << l;
+            for (long long k = 0; k < N; ++k) {
+                double c, s;
+                host_twiddle(k, N, &c, &s);
+                re.push_back(c);
+                im.push_back(s);
+            }
+        }
+        for (int l = 0; l < 6; ++l) {
+            off_sq[l] = re.size();
+            const long long M = 1LL << l;
+            for (long long k1 = 0; k1 < M; ++k1)
+                for (long long j = 0; j < M; ++j) {
+                    double c, s;
+                    host_twiddle(j * k1, M * M, &c, &s);
+                    re.push_back(c);
+                    im.push_back(s);
+                }
+        }
+        const size_t n = re.size();
+        std::vector<double> hd(2 * n);
+        std::vector<float> hf(2 * n);
+        for (size_t i = 0; i < n; ++i) {
+            hd[2 * i] = re[i];
+            hd[2 * i + 1] = im[i];
+            hf[2 * i] = (float)re[i];
+            hf[2 * i + 1] = (float)im[i];
+        }
+        const size_t bytes_d = 2 * n * sizeof(double), bytes_f = 2 * n * sizeof(float);
+        int prev = -1;
+        cudaGetDevice(&prev);
+        cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) return e;
+        void* buf = nullptr;
+        e = cudaMalloc(&buf, bytes_d + bytes_f);
+        if (e == cudaSuccess) e = cudaMemcpy(buf, hd.data(), bytes_d, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy((char*)buf + bytes_d, hf.data(), bytes_f, cudaMemcpyHostToDevice);
+        if (prev >= 0) cudaSetDevice(prev);
+        if (e != cudaSuccess) {
+            if (buf) cudaFree(buf);
+            return e;
+        }
+        t.buf = buf;
+        const cpx<double>* bd = reinterpret_cast<const cpx<double>*>(buf);
+        const cpx<float>* bf = reinterpret_cast<const cpx<float>*>((char*)buf + bytes_d);
+        for (int l = 0; l < 14; ++l) { t.td.n[l] = bd + off_n[l]; t.tf.n[l] = bf + off_n[l]; }
+        for (int l = 0; l < 6; ++l) { t.td.sq[l] = bd + off_sq[l]; t.tf.sq[l] = bf + off_sq[l]; }
+    }
+    if (tf) *tf = t.tf;
+    if (td) *td = t.td;
+    return cudaSuccess;
+}
+
+}  // namespace cmif

@@ -1,0 +1,24 @@
+// Host-side launchers of the small kernels in misc.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.h"
+#include "fft.cuh"
+
+namespace cmif {
+
+struct PeakPart;
+
+// Device image of cmif_peak (include/cmif.h): same 24-byte layout.
+struct PeakRec {
+    int32_t angle_idx, dy, dx, n;
+    double mi;
+};
+
+cudaError_t launch_peak(const double* mi, const int32_t* n, long long RC, const DevStatus* st, double gamma,
+                        PeakPart* parts, int nparts, int HA, int WA, int Cout, int angle_idx, void* peak_out,
+                        cudaStream_t s);
+cudaError_t launch_check_escalate(DevStatus* st, cudaStream_t s);
+cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s);
+cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td);
+
+}  // namespace cmif

@@ -1,0 +1,44 @@
+// Launch sequence of one CMIF map for one precision (FP32 or FP64 transforms).
+#pragma once
+#include <cuda_runtime.h>
+#include "kernels.cuh"
+#include "profiler.h"
+
+namespace cmif {
+
+template <typename T>
+struct PipeArgs {
+    const int32_t* A;
+    const uint8_t* MA;
+    const int32_t* B;
+    const uint8_t* MB;
+    cpx<T>* T1A;  // [K_A][H_A][Qs]  row spectra of A's level sets
+    cpx<T>* T1B;  // [K_B][H_B][Qs]
+    cpx<T>* FA;   // [K_A][Qh][P]    2-D half spectra, column-contiguous
+    cpx<T>* FB;   // [K_B][Qh][P]
+    cpx<T>* Y;    // [K_A*K_B][R][Qs] column-inverted products, output rows only
+    float* cb_global;  // [rows_grid][K_B][Q] when !cb_smem
+    Tw<T> tw;
+    double* mi;
+    int32_t* n;
+    int32_t* counts;
+    DevStatus* st;
+    int prec_slot;    // 0: FP32 residual slot, 1: FP64
+    int conditional;  // run only when STATUS_ESCALATE is set (AUTO re-run)
+    int rows_grid;    // persistent grid of the row/epilogue kernel
+    bool cb_smem;     // B-marginal accumulators in shared memory
+    Profiler* prof;   // optional launch timing (nullptr = off)
+};
+
+template <typename T>
+cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);
+
+// Per-precision facts the host needs at plan time.
+template <typename T>
+size_t rows_smem_bytes(int Q, int KB, bool cb_smem);
+template <typename T>
+int rows_threads(int Q);
+template <typename T>
+cudaError_t rows_max_blocks_per_sm(int Q, int KB, bool cb_smem, int* out);
+
+}  // namespace cmif

@@ -1,0 +1,169 @@
+// Template bodies of the launch sequence; included by kernels_f32.cu and
+// kernels_f64.cu, which instantiate them for one precision each.
+#pragma once
+#include "pipeline.cuh"
+
+namespace cmif {
+
+template <typename K>
+static cudaError_t ensure_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define CMIF_SIZE_SWITCH(N, ...)              \
+    switch (N) {                               \
+        case 16: { constexpr int SZ = 16; __VA_ARGS__; } break;     \
+        case 32: { constexpr int SZ = 32; __VA_ARGS__; } break;     \
+        case 64: { constexpr int SZ = 64; __VA_ARGS__; } break;     \
+        case 128: { constexpr int SZ = 128; __VA_ARGS__; } break;   \
+        case 256: { constexpr int SZ = 256; __VA_ARGS__; } break;   \
+        case 512: { constexpr int SZ = 512; __VA_ARGS__; } break;   \
+        case 1024: { constexpr int SZ = 1024; __VA_ARGS__; } break; \
+        case 2048: { constexpr int SZ = 2048; __VA_ARGS__; } break; \
+        case 4096: { constexpr int SZ = 4096; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;               \
+    }
+
+template <typename T, int Q>
+static cudaError_t launch_fwd_rows(const int32_t* X, const uint8_t* MX, int H, int W, int K, int Qs, cpx<T>* T1,
+                                   const Tw<T>& tw, DevStatus* st, int conditional, cudaStream_t s) {
+    using C = FwdRowsCfg<T, Q>;
+    auto kern = k_fwd_rows<T, Q>;
+    cudaError_t e = ensure_smem(kern, C::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long items = (long long)H * ((K + 1) / 2);
+    const unsigned blocks = (unsigned)((items + C::TPB - 1) / C::TPB);
+    kern<<<blocks, C::THREADS, C::SMEM, s>>>(X, MX, H, W, K, Qs, T1, tw, st, conditional);
+    return cudaGetLastError();
+}
+
+template <typename T, int P>
+static cudaError_t launch_fwd_cols(const cpx<T>* T1, int H, int K, int Qh, int Qs, cpx<T>* F, const Tw<T>& tw,
+                                   const DevStatus* st, int conditional, cudaStream_t s) {
+    using C = ColCfg<T, P>;
+    auto kern = k_fwd_cols<T, P>;
+    cudaError_t e = ensure_smem(kern, C::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((Qh + C::TPB - 1) / C::TPB, K);
+    kern<<<grid, C::THREADS, C::SMEM, s>>>(T1, H, K, Qh, Qs, F, tw, st, conditional);
+    return cudaGetLastError();
+}
+
+template <typename T, int P>
+static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
+    using C = PairColsCfg<T, P>;
+    auto kern = k_pair_cols<T, P>;
+    const size_t smem = pair_cols_smem<T, P>();
+    cudaError_t e = ensure_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(g.KA * g.KB, (g.Qh + C::TPB - 1) / C::TPB);
+    const T scale = T(1) / (T(g.P) * T(g.Q));  // exact: P*Q is a power of two
+    kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KB, g.Qh, g.HA, g.HB, scale, g.R, g.Qs, a.Y, a.tw, a.st,
+                                        a.conditional);
+    return cudaGetLastError();
+}
+
+template <typename T, int Q>
+static cudaError_t launch_pair_rows(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
+    using C = RowCfg<T, Q>;
+    const size_t smem = pair_rows_smem<T, Q>(g.KB, a.cb_smem);
+    if (a.cb_smem) {
+        auto kern = k_pair_rows<T, Q, true>;
+        cudaError_t e = ensure_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<a.rows_grid, C::THREADS, smem, s>>>(a.Y, g, a.tw, a.cb_global, a.mi, a.n, a.counts, a.st,
+                                                   a.prec_slot, a.conditional);
+    } else {
+        auto kern = k_pair_rows<T, Q, false>;
+        cudaError_t e = ensure_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<a.rows_grid, C::THREADS, smem, s>>>(a.Y, g, a.tw, a.cb_global, a.mi, a.n, a.counts, a.st,
+                                                   a.prec_slot, a.conditional);
+    }
+    return cudaGetLastError();
+}
+
+struct ProfScope {
+    Profiler* p;
+    cudaStream_t s;
+    ProfScope(Profiler* p_, const char* name, cudaStream_t s_) : p(p_), s(s_) { if (p) p->begin(name, s); }
+    ~ProfScope() { if (p) p->end(s); }
+};
+
+template <typename T>
+cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
+    cudaError_t e;
+    constexpr bool f32 = sizeof(T) == 4;
+    CMIF_SIZE_SWITCH(g.Q, {
+        ProfScope ps(a.prof, f32 ? "fwd_rows_A_f32" : "fwd_rows_A_f64", s);
+        e = (launch_fwd_rows<T, SZ>(a.A, a.MA, g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st, a.conditional, s));
+    } if (e != cudaSuccess) return e; {
+        ProfScope ps(a.prof, f32 ? "fwd_rows_B_f32" : "fwd_rows_B_f64", s);
+        e = (launch_fwd_rows<T, SZ>(a.B, a.MB, g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st, a.conditional, s));
+    } if (e != cudaSuccess) return e);
+    CMIF_SIZE_SWITCH(g.P, {
+        ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : "fwd_cols_A_f64", s);
+        e = (launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional, s));
+    } if (e != cudaSuccess) return e; {
+        ProfScope ps(a.prof, f32 ? "fwd_cols_B_f32" : "fwd_cols_B_f64", s);
+        e = (launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional, s));
+    } if (e != cudaSuccess) return e; {
+        ProfScope ps(a.prof, f32 ? "pair_cols_f32" : "pair_cols_f64", s);
+        e = (launch_pair_cols<T, SZ>(g, a, s));
+    } if (e != cudaSuccess) return e);
+    CMIF_SIZE_SWITCH(g.Q, {
+        ProfScope ps(a.prof, f32 ? "pair_rows_f32" : "pair_rows_f64", s);
+        e = (launch_pair_rows<T, SZ>(g, a, s));
+    } if (e != cudaSuccess) return e);
+    return cudaSuccess;
+}
+
+template <typename T>
+size_t rows_smem_bytes(int Q, int KB, bool cb_smem) {
+    size_t out = 0;
+    auto f = [&]() -> cudaError_t {
+        CMIF_SIZE_SWITCH(Q, out = pair_rows_smem<T, SZ>(KB, cb_smem));
+        return cudaSuccess;
+    };
+    f();
+    return out;
+}
+
+template <typename T>
+int rows_threads(int Q) {
+    int out = 0;
+    auto f = [&]() -> cudaError_t {
+        CMIF_SIZE_SWITCH(Q, out = RowCfg<T, SZ>::THREADS);
+        return cudaSuccess;
+    };
+    f();
+    return out;
+}
+
+template <typename T>
+cudaError_t rows_max_blocks_per_sm(int Q, int KB, bool cb_smem, int* out) {
+    const size_t smem = rows_smem_bytes<T>(Q, KB, cb_smem);
+    CMIF_SIZE_SWITCH(Q, {
+        if (cb_smem) {
+            auto kern = k_pair_rows<T, SZ, true>;
+            cudaError_t e = ensure_smem(kern, smem);
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, RowCfg<T, SZ>::THREADS, smem);
+        } else {
+            auto kern = k_pair_rows<T, SZ, false>;
+            cudaError_t e = ensure_smem(kern, smem);
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, RowCfg<T, SZ>::THREADS, smem);
+        }
+    });
+    return cudaSuccess;
+}
+
+#define CMIF_INSTANTIATE(T)                                                             \
+    template cudaError_t run_pipeline<T>(const Geom&, const PipeArgs<T>&, cudaStream_t); \
+    template size_t rows_smem_bytes<T>(int, int, bool);                                  \
+    template int rows_threads<T>(int);                                                   \
+    template cudaError_t rows_max_blocks_per_sm<T>(int, int, bool, int*);
+
+}  // namespace cmif

@@ -1,0 +1,55 @@
+"""CPU checks of the C ABI boundary: the library builds, loads, exports every
+function declared in include/cmif.h, and rejects bad arguments on the host
+before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2106_14699_gb300 as cm
+from paper_2106_14699_gb300 import build as cmbuild
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "cmif.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cmif_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libcmif():
+    cmbuild.build()
+    return cm.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_destroy", "cmif_compute",
+                     "cmif_get_status", "cmif_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libcmif):
+    for name in _declared():
+        assert hasattr(libcmif, name), f"{name} declared in cmif.h but not exported"
+    assert set(_declared()) == set(cm.EXPORTS)
+
+
+def test_host_side_argument_errors(libcmif):
+    h = ctypes.c_void_p()
+    P = ctypes.byref(h)
+    assert libcmif.cmif_plan_create_ex(P, 0, 4, 4, 4, 2, 2, cm.FP32, 0) == 1     # H_A < 1
+    assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 0, 2, cm.FP32, 0) == 1     # K_A < 1
+    assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 65, 2, cm.FP32, 0) == 1    # K_A > 64
+    assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 2, 2, 9, 0) == 1           # bad precision
+    assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 2, 2, cm.FP32, 0x80) == 1  # unknown flag
+    assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 2, 2, cm.SPLIT32, 0) == 7  # not built
+    assert libcmif.cmif_plan_create_ex(P, 4096, 1025, 8, 8, 2, 2, cm.FP32, 0) == 1  # H*W > 2^22
+    assert libcmif.cmif_plan_create_ex(P, 2049, 2, 2049, 2, 2, 2, cm.FP32, 0) == 8  # P > 4096
+    assert libcmif.cmif_plan_create_ex(None, 4, 4, 4, 4, 2, 2, cm.FP32, 0) == 1
+    assert libcmif.cmif_compute(None, None, None, None, None, None, None, None, 0.0, None, None) == 1
+    assert libcmif.cmif_plan_destroy(None) == 0
+    assert libcmif.cmif_status_string(2) == b"label outside [0, K) under mask"

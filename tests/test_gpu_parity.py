@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Counts (joint C_AB^{a,b}, marginals C_A^a, C_B^b and N) must be bit-exact;
+MI must be within 1e-6 bits of the oracle's FP64 value (the epilogue reduces
+c log2 c in fixed point, an FP64-grade reduction); the rounding residual of
+every count must stay under the 0.25 guard.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MI_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def cm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_14699_gb300 as cm
+    from paper_2106_14699_gb300 import build
+    build.build()
+    cm.lib()
+    return cm
+
+
+def _to(x):
+    return None if x is None else torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def run_gpu(cm, A, MA, B, MB, KA, KB, prec, counts=True, gamma=0.0):
+    out = cm.cmif(_to(A), _to(MA), _to(B), _to(MB), KA, KB, precision=prec, gamma=gamma, with_counts=counts)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+
+
+def check_exact(cm, A, MA, B, MB, KA, KB, prec, gamma=0.0):
+    g = run_gpu(cm, A, MA, B, MB, KA, KB, prec, counts=True, gamma=gamma)
+    ref = oracle.cmif(A, MA, B, MB, KA, KB, counts=True, marginals=True)
+    assert g["status"][0] == "OK", g["status"]
+    assert g["status"][1] < 0.25
+    np.testing.assert_array_equal(g["n"], ref["n"])
+    kk = KA * KB
+    np.testing.assert_array_equal(g["counts"][:kk], ref["joint"])
+    np.testing.assert_array_equal(g["counts"][kk:kk + KA], ref["marg_a"])
+    np.testing.assert_array_equal(g["counts"][kk + KA:], ref["marg_b"])
+    err = float(np.abs(g["mi"] - ref["mi"]).max())
+    print(f"[mi-error] {A.shape}x{B.shape} K={KA},{KB} prec={prec} max|dMI|={err:.3e} residual={g['status'][1]:.3e}")
+    assert err <= MI_TOL, err
+    # gamma-gated peak of Alg. 1: identical, or a near-tie within the MI tolerance
+    idx, best, _ = oracle.gamma_argmax(ref["mi"], ref["n"], gamma)
+    _, dy, dx, n, mi = g["peak"]
+    r, c = dy + A.shape[0] - 1, dx + A.shape[1] - 1
+    assert (r * ref["mi"].shape[1] + c == idx) or abs(ref["mi"][r, c] - best) <= MI_TOL
+    assert ref["n"][r, c] >= gamma * ref["n"].max()
+    return g, ref
+
+
+def _rand(rng, HA, WA, HB, WB, KA, KB, p0=0.2):
+    A = rng.integers(0, KA, (HA, WA)).astype(np.int32)
+    B = rng.integers(0, KB, (HB, WB)).astype(np.int32)
+    MA = (rng.random((HA, WA)) >= p0).astype(np.uint8)
+    MB = (rng.random((HB, WB)) >= p0).astype(np.uint8)
+    A[MA == 0] = 999   # ignored under mask 0
+    B[MB == 0] = -7
+    return A, MA, B, MB
+
+
+RAGGED = [(1, 1, 1, 1, 1, 1), (1, 5, 3, 1, 2, 3), (7, 9, 5, 6, 5, 4), (17, 33, 20, 11, 3, 7),
+          (64, 70, 31, 45, 13, 24), (70, 70, 70, 70, 8, 8), (5, 130, 9, 120, 4, 4)]
+
+
+@pytest.mark.parametrize("prec_name", ["FP32", "FP64"])
+@pytest.mark.parametrize("shape", RAGGED, ids=lambda s: "x".join(map(str, s)))
+def test_ragged_random(cm, prec_name, shape):
+    rng = np.random.default_rng(hash(shape) % 2**32)
+    A, MA, B, MB = _rand(rng, *shape)
+    check_exact(cm, A, MA, B, MB, shape[4], shape[5], getattr(cm, prec_name), gamma=0.3)
+
+
+def test_null_masks_and_voronoi(cm):
+    rng = np.random.default_rng(11)
+    A = synth.make_field(rng, 48, 40, 30, 6).image(48, 40)
+    B = synth.make_field(rng, 33, 52, 30, 5).image(33, 52)
+    check_exact(cm, A, None, B, None, 6, 5, cm.FP32, gamma=0.5)
+
+
+def test_empty_mask_gives_zero(cm):
+    rng = np.random.default_rng(12)
+    A, MA, B, MB = _rand(rng, 20, 20, 20, 20, 4, 4)
+    MB[:] = 0
+    g = run_gpu(cm, A, MA, B, MB, 4, 4, cm.FP32)
+    assert np.all(g["n"] == 0) and np.all(g["mi"] == 0.0)
+    assert np.all(g["counts"] == 0)
+
+
+def test_single_label_is_zero(cm):
+    rng = np.random.default_rng(13)
+    A = np.zeros((30, 25), np.int32)
+    B = np.zeros((22, 31), np.int32)
+    MB = (rng.random((22, 31)) > 0.5).astype(np.uint8)
+    g, ref = check_exact(cm, A, None, B, MB, 1, 1, cm.FP32)
+    assert np.all(g["mi"] == 0.0)
+
+
+def test_label_range_reported(cm):
+    A = np.zeros((16, 16), np.int32)
+    A[3, 4] = 5
+    B = np.zeros((16, 16), np.int32)
+    g = run_gpu(cm, A, None, B, None, 4, 4, cm.FP32, counts=False)
+    assert g["status"][0] == "LABEL_RANGE"
+    MA = np.ones((16, 16), np.uint8)
+    MA[3, 4] = 0
+    g = run_gpu(cm, A, MA, B, None, 4, 4, cm.FP32, counts=False)
+    assert g["status"][0] == "OK"
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP32"])
+def test_config1_full(cm, prec_name):
+    cfg = synth.make_config(1)
+    g, ref = check_exact(cm, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 8, 8, getattr(cm, prec_name), gamma=0.5)
+    _, dy, dx, _, _ = g["peak"]
+    assert (dy, dx) == tuple(cfg["shift"])
+
+
+def test_config2_full(cm):
+    cfg = synth.make_config(2)
+    g, ref = check_exact(cm, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 16, 16, cm.FP32, gamma=0.5)
+    _, dy, dx, _, _ = g["peak"]
+    assert (dy, dx) == tuple(cfg["shift"])
+
+
+def _sample_shifts(rng, HA, WA, HB, WB, n, extra=()):
+    dys = list(rng.integers(-(HA - 1), HB, n))
+    dxs = list(rng.integers(-(WA - 1), WB, n))
+    for dy, dx in [(0, 0), (-(HA - 1), -(WA - 1)), (HB - 1, WB - 1), (-(HA - 1), WB - 1), (HB - 1, -(WA - 1)),
+                   (1, -1), (-2, 3), *extra]:
+        dys.append(dy)
+        dxs.append(dx)
+    return np.array(dys, np.int32), np.array(dxs, np.int32)
+
+
+def test_config3_full_size_sampled(cm):
+    """1024^2, K=16, FP32 path at the benchmark size: N exact on the whole map
+    (closed form for all-ones masks), MI on sampled shifts vs the oracle,
+    residual under the guard, planted shift found."""
+    cfg = synth.make_config(3)
+    A, B = cfg["A"], cfg["B"]
+    g = run_gpu(cm, A, cfg["M_A"], B, cfg["M_B"], 16, 16, cm.FP32, counts=False, gamma=0.5)
+    assert g["status"][0] == "OK" and g["status"][1] < 0.25, g["status"]
+    H = 1024
+    d = np.arange(2 * H - 1) - (H - 1)
+    np.testing.assert_array_equal(g["n"], np.outer(H - np.abs(d), H - np.abs(d)))
+    rng = np.random.default_rng(3)
+    dys, dxs = _sample_shifts(rng, H, H, H, H, 160, extra=[tuple(cfg["shift"])])
+    ref = oracle.cmif_at(A, cfg["M_A"], B, cfg["M_B"], 16, 16, dys, dxs)
+    got = g["mi"][dys + H - 1, dxs + H - 1]
+    np.testing.assert_array_equal(g["n"][dys + H - 1, dxs + H - 1], ref["n"])
+    err = float(np.abs(got - ref["mi"]).max())
+    print(f"[mi-error] config3 sampled max|dMI|={err:.3e} residual={g['status'][1]:.3e}")
+    assert err <= MI_TOL, err
+    _, dy, dx, _, _ = g["peak"]
+    assert (dy, dx) == tuple(cfg["shift"])
+
+
+def test_auto_escalates_unbalanced_labels(cm):
+    """A dominant label makes FP32 correlations of ~10^6 counts inexact; AUTO
+    must detect it on the device and re-run in FP64 (exact)."""
+    rng = np.random.default_rng(21)
+    H = 1024
+    A = (rng.random((H, H)) < 0.02).astype(np.int32)
+    B = (rng.random((H, H)) < 0.02).astype(np.int32)
+    g32 = run_gpu(cm, A, None, B, None, 2, 2, cm.FP32, counts=False)
+    ga = run_gpu(cm, A, None, B, None, 2, 2, cm.AUTO, counts=False)
+    plan_status = ga["status"]
+    dys, dxs = _sample_shifts(rng, H, H, H, H, 64)
+    ref = oracle.cmif_at(A, None, B, None, 2, 2, dys, dxs)
+    got = ga["mi"][dys + H - 1, dxs + H - 1]
+    if g32["status"][1] >= 0.25:
+        assert g32["status"][0] == "PRECISION"
+        assert plan_status[2] == 1 and plan_status[0] == "OK" and plan_status[1] < 0.25
+    assert float(np.abs(got - ref["mi"]).max()) <= MI_TOL
+    np.testing.assert_array_equal(ga["n"][dys + H - 1, dxs + H - 1], ref["n"])
+
+
+def test_host_buffer_entry_point(cm):
+    cfg = synth.make_config(1)
+    A, B = cfg["A"], cfg["B"]
+    plan = cm.Plan(64, 64, 64, 64, 8, 8, cm.FP32)
+    mi = np.empty((127, 127), np.float64)
+    n = np.empty((127, 127), np.int32)
+    pk = cm.Peak()
+    plan.compute_host(A, cfg["M_A"], B, cfg["M_B"], mi, n, 0.5, pk)
+    ref = oracle.cmif(A, cfg["M_A"], B, cfg["M_B"], 8, 8)
+    np.testing.assert_array_equal(n, ref["n"])
+    assert float(np.abs(mi - ref["mi"]).max()) <= MI_TOL
+    assert (pk.dy, pk.dx) == tuple(cfg["shift"])
+    plan.close()
