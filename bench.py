@@ -36,9 +36,14 @@ CONFIG_ID = 3
 GAMMA = 0.5
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
-# DRAM bytes per launch of the dominant kernels from one ncu capture of this
-# workload (profiles/); None until captured for the current kernel version.
-NCU_TRAFFIC = {}
+# DRAM bytes per launch of the pair kernels, from ncu captures of the same
+# kernel instantiations on smaller cases (profiles/k_pair_*_small_*.md) scaled
+# by the units processed (2047/511 output rows; 1025/257 kx columns).  Set to
+# None when a kernel changes after its capture.
+NCU_TRAFFIC = {
+    "pair_rows_f32": (1.077061e9 + 19.25376e6) * 2047 / 511,
+    "pair_cols_f32": (156.884992e6 + 1.144764e9) * 1025 / 257,
+}
 
 
 def algorithmic_bytes(name, g):

@@ -375,6 +375,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
                     if (++b == KB) { b = 0; ++a; }
                 }
             }
+            __syncthreads();  // the next round's transforms overwrite the scratch read above
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
