@@ -150,6 +150,30 @@ cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* ma
 cmif_status cmif_plan_set_profiling(cmif_plan plan, int enable);
 cmif_status cmif_plan_stage_times(cmif_plan plan, int max_n, int* n, double* ms, const char** names);
 
+/* No-allocation variant of cmif_compute.  The paper has no counterpart: this
+ * is for callers that may not allocate device memory at all -- for instance a
+ * host framework that owns every device allocation and forbids cudaMalloc in
+ * its plug-ins, or a loop that must not synchronise the device (cudaMalloc and
+ * cudaFree can synchronise implicitly).  No plan is needed and nothing is
+ * allocated: the transform workspace, twiddle tables, status word and peak
+ * partials live in one fixed device array of 64 MiB inside the library, which
+ * every GPU that loads it holds until the process exits.
+ *   Arguments as in cmif_compute, plus the sizes (as in cmif_plan_create_ex)
+ *   and status_dev: device int32 or NULL, receives the device-side
+ *   cmif_status of this map (CMIF_OK, CMIF_ERR_LABEL_RANGE, CMIF_ERR_PRECISION).
+ *   FP32 transforms only; no debug counts.
+ * Returns CMIF_ERR_UNSUPPORTED when the workspace would exceed the 64 MiB array
+ * (e.g. 64 x 64 with K = 8 needs 6 MB; 128 x 128 with K = 12 about 48 MB) or
+ * the B-marginals would not fit in shared memory; CMIF_ERR_INVALID_ARG as
+ * cmif_compute.  The first call on a device resolves the array's address and
+ * uploads the twiddle tables with a synchronous copy: make that first call
+ * before any stream capture.  All calls share the one array: calls that may
+ * overlap on the GPU (different streams, threads) race and must not be issued. */
+cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, int K_A, int K_B, const int32_t* A,
+                                 const uint8_t* M_A, const int32_t* B, const uint8_t* M_B, double* mi_map,
+                                 int32_t* n_map, double gamma, cmif_peak* peak_dev, int32_t* status_dev,
+                                 void* stream);
+
 /* Static string for a status code. */
 const char* cmif_status_string(cmif_status status);
 

@@ -38,7 +38,7 @@ class Peak(ctypes.Structure):
 
 EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_destroy", "cmif_plan_workspace_bytes",
            "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
-           "cmif_plan_stage_times", "cmif_status_string"]
+           "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_status_string"]
 
 _lib = None
 
@@ -61,6 +61,7 @@ def lib():
         L.cmif_get_status.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
         L.cmif_plan_set_profiling.argtypes = [P, I]
         L.cmif_plan_stage_times.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_char_p)]
+        L.cmif_compute_noalloc.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, D, P, P, P]
         L.cmif_status_string.argtypes = [I]
         L.cmif_status_string.restype = ctypes.c_char_p
         for name in EXPORTS[:-1]:
@@ -160,6 +161,16 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def compute_noalloc(A, M_A, B, M_B, K_A, K_B, mi_map, n_map=None, gamma=0.0, peak=None, status=None,
+                    stream=None):
+    """cmif_compute_noalloc on torch CUDA tensors (no plan, no device allocation in the library)."""
+    H_A, W_A = A.shape
+    H_B, W_B = B.shape
+    _check(lib().cmif_compute_noalloc(H_A, W_A, H_B, W_B, K_A, K_B, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B),
+                                      _ptr(mi_map), _ptr(n_map), float(gamma), _ptr(peak), _ptr(status),
+                                      _stream(stream)), "cmif_compute_noalloc")
 
 
 def cmif(A, M_A, B, M_B, K_A, K_B, precision=FP32, gamma=0.0, with_counts=False, plan=None, stream=None):

@@ -143,6 +143,32 @@ static void host_twiddle(long long k, long long N, double* c, double* s) {
     *s = -ss;  // e^{-i t}
 }
 
+void twiddle_table_f32(std::vector<float>& out, size_t off_n[14], size_t off_sq[6]) {
+    out.clear();
+    size_t n = 0;
+    for (int l = 0; l < 14; ++l) {
+        off_n[l] = n;
+        const long long N = 1LL << l;
+        for (long long k = 0; k < N; ++k, ++n) {
+            double c, s;
+            host_twiddle(k, N, &c, &s);
+            out.push_back((float)c);
+            out.push_back((float)s);
+        }
+    }
+    for (int l = 0; l < 6; ++l) {
+        off_sq[l] = n;
+        const long long M = 1LL << l;
+        for (long long k1 = 0; k1 < M; ++k1)
+            for (long long j = 0; j < M; ++j, ++n) {
+                double c, s;
+                host_twiddle(j * k1, M * M, &c, &s);
+                out.push_back((float)c);
+                out.push_back((float)s);
+            }
+    }
+}
+
 struct DevTables {
     void* buf = nullptr;
     Tw<float> tf{};

@@ -1,6 +1,7 @@
 // Host-side launchers of the small kernels in misc.cu.
 #pragma once
 #include <cuda_runtime.h>
+#include <vector>
 #include "common.h"
 #include "fft.cuh"
 
@@ -20,5 +21,8 @@ cudaError_t launch_peak(const double* mi, const int32_t* n, long long RC, const 
 cudaError_t launch_check_escalate(DevStatus* st, cudaStream_t s);
 cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s);
 cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td);
+// Host copy of the FP32 twiddle tables (interleaved re, im) and the entry offsets
+// of each table, in the same layout get_twiddles() uploads.
+void twiddle_table_f32(std::vector<float>& out, size_t off_n[14], size_t off_sq[6]);
 
 }  // namespace cmif
