@@ -135,6 +135,37 @@ cmif_status cmif_compute_host(cmif_plan plan, const int32_t* A, const uint8_t* M
                               const uint8_t* M_B, double* mi_map, int32_t* n_map, double gamma,
                               cmif_peak* peak_host, void* stream);
 
+/* Nearest-neighbour rotation of the floating image for Alg. 1's rotation grid
+ * (Sec. 3.6: NN interpolation, the labels being categorical).  The paper
+ * leaves centre, canvas and sign open; here: centre ((H-1)/2, (W-1)/2) in
+ * (row, col), canvas = B's own H x W, and output pixel (i, j) takes the source
+ *   col = c_col + u cos(theta) - v sin(theta),  row = c_row + u sin(theta) + v cos(theta)
+ * with u = j - c_col, v = i - c_row, each rounded half away from zero (the
+ * content turns counter-clockwise on screen, rows pointing down).  M_out is 1
+ * iff the source lies in B and M_B(source) = 1 (M_B NULL: all ones); elsewhere
+ * B_out and M_out are 0.  Device pointers: B, B_out int32 H x W; M_B, M_out
+ * uint8 H x W.  Coordinates in FP64. */
+cmif_status cmif_rotate_nn(const int32_t* B, const uint8_t* M_B, int H, int W, double theta, int32_t* B_out,
+                           uint8_t* M_out, void* stream);
+
+/* Alg. 1 over a set of rotations Omega = {R_theta_i}: for every angle, B and
+ * M_B are rotated (cmif_rotate_nn, into the plan's buffers), the CMIF map of
+ * A against the rotated B is computed (as cmif_compute; A's transforms are
+ * computed once), and its gamma-gated argmax taken (N_cal = gamma * max N,
+ * ties to the lowest map index).  The per-angle bests are then ordered by MI,
+ * descending, earlier angle first among equals, and the first top_k written to
+ * topk_dev; topk_dev[0] is Alg. 1's T-hat (strict > against I = 0) when its MI
+ * is > 0.  cmif_peak.angle_idx indexes angles_rad_host.
+ *   angles_rad_host: host double[n_angles], radians; 1 <= n_angles <= 4096
+ *   top_k          : 1 <= top_k <= n_angles
+ *   topk_dev       : device cmif_peak[top_k]
+ *   mi_maps        : device double[n_angles * R * C] or NULL (per-angle maps,
+ *                    angle-major; NULL keeps only the peaks)
+ * The plan's sizes are those of A and of B (the rotation keeps B's canvas). */
+cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
+                                 const uint8_t* M_B, const double* angles_rad_host, int n_angles, double gamma,
+                                 int top_k, cmif_peak* topk_dev, double* mi_maps, void* stream);
+
 /* Device status of the last call on this plan (synchronises the plan's
  * last stream).  device_side: CMIF_OK, or the first device problem in the
  * order LABEL_RANGE, PRECISION, TIMEOUT.  max_residual: the largest

@@ -38,7 +38,8 @@ class Peak(ctypes.Structure):
 
 EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_destroy", "cmif_plan_workspace_bytes",
            "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
-           "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_status_string"]
+           "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_rotate_nn", "cmif_align_rotations",
+           "cmif_status_string"]
 
 _lib = None
 
@@ -62,6 +63,8 @@ def lib():
         L.cmif_plan_set_profiling.argtypes = [P, I]
         L.cmif_plan_stage_times.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_char_p)]
         L.cmif_compute_noalloc.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, D, P, P, P]
+        L.cmif_rotate_nn.argtypes = [P, P, I, I, D, P, P, P]
+        L.cmif_align_rotations.argtypes = [P, P, P, P, P, P, I, D, I, P, P, P]
         L.cmif_status_string.argtypes = [I]
         L.cmif_status_string.restype = ctypes.c_char_p
         for name in EXPORTS[:-1]:
@@ -128,6 +131,13 @@ class Plan:
         _check(lib().cmif_compute_host(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), _ptr(mi_map), _ptr(n_map),
                                        float(gamma), pk, _stream(stream)), "cmif_compute_host")
 
+    def align_rotations(self, A, M_A, B, M_B, angles_rad, gamma, top_k, topk_dev, mi_maps=None, stream=None):
+        """Alg. 1 over rotations (device tensors; angles: host sequence of radians); asynchronous."""
+        ang = np.ascontiguousarray(np.asarray(angles_rad, dtype=np.float64))
+        _check(lib().cmif_align_rotations(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), ang.ctypes.data,
+                                          len(ang), float(gamma), int(top_k), _ptr(topk_dev), _ptr(mi_maps),
+                                          _stream(stream)), "cmif_align_rotations")
+
     def status(self):
         """(device status name, max residual, escalations) of the last call; synchronises."""
         ds, res, esc = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
@@ -161,6 +171,23 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def rotate_nn(B, M_B, theta, B_out, M_out, stream=None):
+    """cmif_rotate_nn on torch CUDA tensors."""
+    H, W = B.shape
+    _check(lib().cmif_rotate_nn(_ptr(B), _ptr(M_B), H, W, float(theta), _ptr(B_out), _ptr(M_out), _stream(stream)),
+           "cmif_rotate_nn")
+
+
+def peaks_from_bytes(buf, count):
+    """Decode `count` cmif_peak records from a uint8 tensor / bytes."""
+    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+    out = []
+    for i in range(count):
+        pk = Peak.from_buffer_copy(raw[24 * i:24 * (i + 1)])
+        out.append((pk.angle_idx, pk.dy, pk.dx, pk.n, pk.mi))
+    return out
 
 
 def compute_noalloc(A, M_A, B, M_B, K_A, K_B, mi_map, n_map=None, gamma=0.0, peak=None, status=None,

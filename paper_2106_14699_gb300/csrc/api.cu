@@ -1,5 +1,7 @@
 // C ABI of the CMIF library: plans, workspace, launch order, status.
 #include <cstdio>
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -23,6 +25,7 @@ struct Workspace {
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr int kMaxAngles = 4096;
 
 int pow2_at_least(int v, int lo) {
     int p = lo;
@@ -41,11 +44,16 @@ struct cmif_plan_s {
     Workspace<float> w32;
     Workspace<double> w64;
     bool has32 = false, has64 = false;
-    DevStatus* st = nullptr;
+    DevStatus* st = nullptr;      // status of the map being computed (reset per map)
+    DevStatus* st_total = nullptr;  // status of the whole call (what cmif_get_status reports)
     PeakPart* parts = nullptr;
     int nparts = 0;
     void* small = nullptr;  // st + parts + internal N map in one allocation
     int32_t* nbuf = nullptr;  // N map used when the caller passes no n_map
+    double* mibuf = nullptr;  // MI map used by cmif_align_rotations when the caller keeps no maps
+    int32_t* wB = nullptr;    // rotated floating image (cmif_align_rotations)
+    uint8_t* wM = nullptr;    // its rotated-support mask
+    void* peaks = nullptr;    // per-transform peaks, kMaxAngles records
     // host-buffer path staging (allocated lazily by cmif_compute_host)
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -68,12 +76,28 @@ cmif_status alloc_workspace(cmif_plan p, Workspace<T>& w) {
     const size_t sT1A = (size_t)g.KA * g.HA * g.Qs * cs, sT1B = (size_t)g.KB * g.HB * g.Qs * cs;
     const size_t sFA = (size_t)g.KA * g.Qh * g.P * cs, sFB = (size_t)g.KB * g.Qh * g.P * cs;
     const size_t sY = (size_t)g.KA * g.KB * g.R * g.Qs * cs;
-    // B-marginal accumulators: shared memory when they fit beside the team buffers
-    const size_t smem_cb = rows_smem_bytes<T>(g.Q, g.KB, true);
-    w.cb_smem = smem_cb <= 200 * 1024;
+    // Row kernel: the TMEM / TMA variant where it applies (FP32, Q = 1024 or 2048),
+    // else B-marginal accumulators in shared memory when they fit, else in global memory.
     int bps = 0;
-    cudaError_t e = rows_max_blocks_per_sm<T>(g.Q, g.KB, w.cb_smem, &bps);
-    if (e != cudaSuccess) return from_cuda(e);
+    cudaError_t e = cudaSuccess;
+    w.args.tm_cols = 0;
+    const char* no_tm = std::getenv("CMIF_DISABLE_TMEM");
+    if (sizeof(T) == 4 && !(no_tm && no_tm[0] == '1')) {
+        const int cols = rows_tm_cols(g.Q, g.KB);
+        if (cols > 0) {
+            e = rows_tm_max_blocks_per_sm(g.Q, &bps);
+            if (e != cudaSuccess) return from_cuda(e);
+            if (bps >= 1) w.args.tm_cols = cols;
+        }
+    }
+    if (w.args.tm_cols > 0) {
+        w.cb_smem = true;
+    } else {
+        const size_t smem_cb = rows_smem_bytes<T>(g.Q, g.KB, true);
+        w.cb_smem = smem_cb <= 200 * 1024;
+        e = rows_max_blocks_per_sm<T>(g.Q, g.KB, w.cb_smem, &bps);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     if (bps < 1) return CMIF_ERR_UNSUPPORTED;
     w.rows_grid = std::min(g.R, bps * p->num_sms);
     const size_t sCB = w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float);
@@ -142,14 +166,19 @@ void fill_io(PipeArgs<T>& a, const int32_t* A, const uint8_t* MA, const int32_t*
     a.st = st;
 }
 
-// One full map into (mi, n, counts), status in p->st (not cleared here).
+// One full map into (mi, n, counts); its status in p->st (reset here) is folded
+// into p->st_total.  stages32 selects the FP32 stages (A's transforms may be
+// reused across calls); an FP64 pass always recomputes everything.
 cmif_status compute_map(cmif_plan p, const int32_t* A, const uint8_t* MA, const int32_t* B, const uint8_t* MB,
-                        double* mi, int32_t* n, int32_t* counts, cudaStream_t s) {
+                        double* mi, int32_t* n, int32_t* counts, cudaStream_t s, unsigned stages32 = STAGE_ALL) {
     const Geom& g = p->g;
+    cudaError_t e0 = cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s);
+    if (e0 != cudaSuccess) return from_cuda(e0);
     if (p->prec == CMIF_FP32 || p->prec == CMIF_AUTO) {
         PipeArgs<float> a = p->w32.args;
         fill_io(a, A, MA, B, MB, mi, n, counts, p->st);
         a.prof = p->prof.enabled ? &p->prof : nullptr;
+        a.stages = stages32;
         a.prec_slot = 0;
         a.conditional = 0;
         cudaError_t e = run_pipeline<float>(g, a, s);
@@ -163,6 +192,7 @@ cmif_status compute_map(cmif_plan p, const int32_t* A, const uint8_t* MA, const 
         PipeArgs<double> a = p->w64.args;
         fill_io(a, A, MA, B, MB, mi, n, counts, p->st);
         a.prof = p->prof.enabled ? &p->prof : nullptr;
+        a.stages = STAGE_ALL;
         a.prec_slot = 1;
         a.conditional = (p->prec == CMIF_AUTO) ? 1 : 0;
         cudaError_t e = run_pipeline<double>(g, a, s);
@@ -171,6 +201,7 @@ cmif_status compute_map(cmif_plan p, const int32_t* A, const uint8_t* MA, const 
     const int slot_default = (p->prec == CMIF_FP64) ? 1 : 0;
     p->prof.begin("finalize", s);
     cudaError_t e = launch_finalize(p->st, 1, slot_default, s);
+    if (e == cudaSuccess) e = launch_merge_status(p->st, p->st_total, slot_default, s);
     p->prof.end(s);
     return from_cuda(e);
 }
@@ -227,15 +258,27 @@ cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W
     }
     if (st == CMIF_OK) {
         p->nparts = 2 * p->num_sms;
-        const size_t o_parts = align_up(sizeof(DevStatus), 256);
+        const size_t o_tot = align_up(sizeof(DevStatus), 256);
+        const size_t o_parts = o_tot + align_up(sizeof(DevStatus), 256);
         const size_t o_n = align_up(o_parts + (size_t)p->nparts * sizeof(PeakPart), 256);
-        const size_t bytes = o_n + (size_t)g.R * g.C * sizeof(int32_t);
+        const size_t o_mi = align_up(o_n + (size_t)g.R * g.C * sizeof(int32_t), 256);
+        const size_t o_wB = align_up(o_mi + (size_t)g.R * g.C * sizeof(double), 256);
+        const size_t o_wM = align_up(o_wB + (size_t)g.HB * g.WB * sizeof(int32_t), 256);
+        const size_t o_pk = align_up(o_wM + (size_t)g.HB * g.WB, 256);
+        const size_t bytes = o_pk + (size_t)kMaxAngles * sizeof(PeakRec);
         e = cudaMalloc(&p->small, bytes);
         if (e != cudaSuccess) { cudaGetLastError(); st = CMIF_ERR_OOM; }
         else {
-            p->st = (DevStatus*)p->small;
-            p->parts = (PeakPart*)((char*)p->small + o_parts);
-            p->nbuf = (int32_t*)((char*)p->small + o_n);
+            char* sb = (char*)p->small;
+            p->st = (DevStatus*)sb;
+            p->st_total = (DevStatus*)(sb + o_tot);
+            p->parts = (PeakPart*)(sb + o_parts);
+            p->nbuf = (int32_t*)(sb + o_n);
+            p->mibuf = (double*)(sb + o_mi);
+            p->wB = (int32_t*)(sb + o_wB);
+            p->wM = (uint8_t*)(sb + o_wM);
+            p->peaks = sb + o_pk;
+            if (cudaMemset(p->st_total, 0, sizeof(DevStatus)) != cudaSuccess) st = CMIF_ERR_CUDA;
             if (cudaMemset(p->st, 0, sizeof(DevStatus)) != cudaSuccess) st = CMIF_ERR_CUDA;
         }
     }
@@ -272,7 +315,7 @@ cmif_status cmif_compute(cmif_plan plan, const int32_t* A, const uint8_t* M_A, c
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
     plan->prof.reset();
-    cudaError_t e = cudaMemsetAsync(plan->st, 0, sizeof(DevStatus), s);
+    cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), s);
     if (e != cudaSuccess) return from_cuda(e);
     int32_t* nm = n_map ? n_map : plan->nbuf;
     cmif_status st = compute_map(plan, A, M_A, B, M_B, mi_map, nm, counts, s);
@@ -336,7 +379,7 @@ cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* ma
     DeviceGuard dg(plan->device);
     DevStatus h{};
     cudaError_t e = cudaStreamSynchronize(plan->last_stream);
-    if (e == cudaSuccess) e = cudaMemcpy(&h, plan->st, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, plan->st_total, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return from_cuda(e);
     if (device_side) {
         *device_side = (h.flags & STATUS_LABEL_RANGE) ? CMIF_ERR_LABEL_RANGE
@@ -345,13 +388,56 @@ cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* ma
                                                       : CMIF_OK;
     }
     if (max_residual) {
-        const int slot = (plan->prec == CMIF_FP64 || (h.flags & STATUS_ESCALATE)) ? 1 : 0;
         float f;
-        std::memcpy(&f, &h.res_bits[slot], sizeof(f));
+        std::memcpy(&f, &h.res_bits[0], sizeof(f));
         *max_residual = f;
     }
     if (escalations) *escalations = h.escalations;
     return CMIF_OK;
+}
+
+cmif_status cmif_rotate_nn(const int32_t* B, const uint8_t* M_B, int H, int W, double theta, int32_t* B_out,
+                           uint8_t* M_out, void* stream) {
+    if (!B || !B_out || !M_out || H < 1 || W < 1 || !std::isfinite(theta)) return CMIF_ERR_INVALID_ARG;
+    return from_cuda(launch_warp_nn(B, M_B, H, W, theta, B_out, M_out, (cudaStream_t)stream));
+}
+
+cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
+                                 const uint8_t* M_B, const double* angles_rad_host, int n_angles, double gamma,
+                                 int top_k, cmif_peak* topk_dev, double* mi_maps, void* stream) {
+    if (!plan || !A || !B || !angles_rad_host || !topk_dev) return CMIF_ERR_INVALID_ARG;
+    if (n_angles < 1 || n_angles > kMaxAngles || top_k < 1 || top_k > n_angles) return CMIF_ERR_INVALID_ARG;
+    if (!(gamma >= 0.0 && gamma <= 1.0)) return CMIF_ERR_INVALID_ARG;
+    for (int i = 0; i < n_angles; ++i)
+        if (!std::isfinite(angles_rad_host[i])) return CMIF_ERR_INVALID_ARG;
+    DeviceGuard dg(plan->device);
+    const Geom& g = plan->g;
+    const size_t RC = (size_t)g.R * g.C;
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    plan->prof.reset();
+    cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), s);
+    if (e != cudaSuccess) return from_cuda(e);
+    PeakRec* peaks = reinterpret_cast<PeakRec*>(plan->peaks);
+    for (int i = 0; i < n_angles; ++i) {
+        plan->prof.begin("warp_nn", s);
+        e = launch_warp_nn(B, M_B, g.HB, g.WB, angles_rad_host[i], plan->wB, plan->wM, s);
+        plan->prof.end(s);
+        if (e != cudaSuccess) return from_cuda(e);
+        double* mi = mi_maps ? mi_maps + (size_t)i * RC : plan->mibuf;
+        const unsigned stages = (i == 0) ? STAGE_ALL : (STAGE_FWD_B | STAGE_PAIRS);
+        cmif_status cs = compute_map(plan, A, M_A, plan->wB, plan->wM, mi, plan->nbuf, nullptr, s, stages);
+        if (cs != CMIF_OK) return cs;
+        plan->prof.begin("peak", s);
+        e = launch_peak(mi, plan->nbuf, (long long)RC, plan->st, gamma, plan->parts, plan->nparts, g.HA, g.WA, g.C,
+                        i, peaks + i, s);
+        plan->prof.end(s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    plan->prof.begin("topk", s);
+    e = launch_topk(peaks, n_angles, top_k, topk_dev, s);
+    plan->prof.end(s);
+    return from_cuda(e);
 }
 
 cmif_status cmif_plan_set_profiling(cmif_plan plan, int enable) {

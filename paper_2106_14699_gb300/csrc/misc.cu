@@ -1,4 +1,5 @@
 // Peak search (Alg. 1), status bookkeeping and twiddle tables.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -71,6 +72,92 @@ __global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, con
     p->dx = (int)(bi % Cout) - (WA - 1);
     p->n = n[bi];
     p->mi = bm;
+}
+
+// ---------------------------------------------------------------------------
+// Nearest-neighbour rotation of the floating image for Alg. 1's rotation grid
+// (Sec. 3.6: NN interpolation because the labels are categorical).  Output
+// pixel (i, j) takes the source  col = c_col + u cos - v sin,
+// row = c_row + u sin + v cos  (u = j - c_col, v = i - c_row, c = ((H-1)/2, (W-1)/2)),
+// each rounded half away from zero; the output mask is 1 iff the source lies
+// in B and M_B(source) = 1, else label and mask are 0.
+__global__ void k_warp_nn(const int32_t* __restrict__ B, const uint8_t* __restrict__ MB, int H, int W, double ct,
+                          double st, int32_t* __restrict__ Bo, uint8_t* __restrict__ Mo) {
+    const long long n = (long long)H * W;
+    const double cr = 0.5 * (H - 1), cc = 0.5 * (W - 1);
+    for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(o / W), j = (int)(o - (long long)i * W);
+        const double u = j - cc, v = i - cr;
+        const double xs = cc + u * ct - v * st;
+        const double ys = cr + u * st + v * ct;
+        const long long si = (long long)round(ys), sj = (long long)round(xs);
+        int32_t lab = 0;
+        uint8_t m = 0;
+        if (si >= 0 && si < H && sj >= 0 && sj < W) {
+            const long long src = si * W + sj;
+            if (!MB || MB[src]) { lab = B[src]; m = 1; }
+        }
+        Bo[o] = lab;
+        Mo[o] = m;
+    }
+}
+
+cudaError_t launch_warp_nn(const int32_t* B, const uint8_t* MB, int H, int W, double theta, int32_t* Bo, uint8_t* Mo,
+                           cudaStream_t s) {
+    const long long n = (long long)H * W;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+    k_warp_nn<<<blocks, 256, 0, s>>>(B, MB, H, W, std::cos(theta), std::sin(theta), Bo, Mo);
+    return cudaGetLastError();
+}
+
+// Fold one map's device status into the call's running total.
+__global__ void k_merge_status(const DevStatus* __restrict__ m, DevStatus* __restrict__ tot, int slot_default) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool esc = (m->flags & STATUS_ESCALATE) != 0;
+        const int slot = esc ? 1 : slot_default;
+        tot->flags |= m->flags;
+        tot->res_bits[0] = max(tot->res_bits[0], m->res_bits[slot]);  // residual of the authoritative pass
+        tot->escalations += m->escalations;
+        tot->max_n = max(tot->max_n, m->max_n);
+    }
+}
+
+cudaError_t launch_merge_status(const DevStatus* m, DevStatus* tot, int slot_default, cudaStream_t s) {
+    k_merge_status<<<1, 32, 0, s>>>(m, tot, slot_default);
+    return cudaGetLastError();
+}
+
+// Alg. 1 over transforms: the per-transform bests sorted by MI (descending),
+// earlier transform first among equals; out[0] is Alg. 1's choice when its MI
+// is > 0 (I starts at 0, strict >).  Slots beyond n get angle_idx = -1.
+__global__ void k_topk(const PeakRec* __restrict__ peaks, int n, int k, PeakRec* __restrict__ out) {
+    __shared__ unsigned char used[4096];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
+    __syncwarp();
+    for (int q = 0; q < k; ++q) {
+        double bm = -INFINITY;
+        int bi = -1;
+        for (int i = threadIdx.x; i < n; i += 32) {
+            if (used[i] || peaks[i].angle_idx < 0) continue;
+            const double m = peaks[i].mi;
+            if (bi < 0 || m > bm || (m == bm && i < bi)) { bm = m; bi = i; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double om = __shfl_xor_sync(0xffffffffu, bm, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (oi >= 0 && (bi < 0 || om > bm || (om == bm && oi < bi))) { bm = om; bi = oi; }
+        }
+        if (threadIdx.x == 0) {
+            if (bi >= 0) { out[q] = peaks[bi]; used[bi] = 1; }
+            else out[q] = {-1, 0, 0, 0, 0.0};
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_topk(const void* peaks, int n, int k, void* out, cudaStream_t s) {
+    k_topk<<<1, 32, 0, s>>>(reinterpret_cast<const PeakRec*>(peaks), n, k, reinterpret_cast<PeakRec*>(out));
+    return cudaGetLastError();
 }
 
 // AUTO: escalate to the FP64 pass when the FP32 residual reached the guard.

@@ -152,6 +152,7 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     a.rows_grid = std::min(g.R, bps * d->num_sms);
     a.cb_smem = true;
     a.prof = nullptr;
+    a.tm_cols = 0;
     e = run_pipeline<float>(g, a, s);
     if (e != cudaSuccess) return to_status(e);
     e = launch_finalize(st, 0, 0, s);

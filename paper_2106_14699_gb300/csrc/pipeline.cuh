@@ -28,6 +28,15 @@ struct PipeArgs {
     int rows_grid;    // persistent grid of the row/epilogue kernel
     bool cb_smem;     // B-marginal accumulators in shared memory
     Profiler* prof;   // optional launch timing (nullptr = off)
+    int tm_cols;      // > 0: use the TMEM / TMA row kernel with this many TMEM columns
+    unsigned stages;  // STAGE_* bits: which parts of the sequence to launch
+};
+
+enum : unsigned {
+    STAGE_FWD_A = 1u,  // level-set transforms of A
+    STAGE_FWD_B = 2u,  // level-set transforms of B
+    STAGE_PAIRS = 4u,  // pair product, inverse transforms, epilogue
+    STAGE_ALL = 7u,
 };
 
 template <typename T>
@@ -40,5 +49,8 @@ template <typename T>
 int rows_threads(int Q);
 template <typename T>
 cudaError_t rows_max_blocks_per_sm(int Q, int KB, bool cb_smem, int* out);
+// TMEM columns the TMEM / TMA row kernel needs for (Q, K_B), or 0 when it does not apply.
+int rows_tm_cols(int Q, int KB);
+cudaError_t rows_tm_max_blocks_per_sm(int Q, int* out);
 
 }  // namespace cmif

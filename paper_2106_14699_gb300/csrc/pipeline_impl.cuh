@@ -2,6 +2,7 @@
 // kernels_f64.cu, which instantiate them for one precision each.
 #pragma once
 #include "pipeline.cuh"
+#include "rows_tm.cuh"
 
 namespace cmif {
 
@@ -67,6 +68,16 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
 template <typename T, int Q>
 static cudaError_t launch_pair_rows(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     using C = RowCfg<T, Q>;
+    if constexpr (sizeof(T) == 4 && (Q == 1024 || Q == 2048)) {
+        if (a.tm_cols > 0) {
+            auto kern = k_pair_rows_tm<Q>;
+            cudaError_t e = ensure_smem(kern, RowTmCfg<Q>::SMEM);
+            if (e != cudaSuccess) return e;
+            kern<<<a.rows_grid, RowTmCfg<Q>::THREADS, RowTmCfg<Q>::SMEM, s>>>(a.Y, g, a.tw, a.mi, a.n, a.counts, a.st,
+                                                                             a.tm_cols);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = pair_rows_smem<T, Q>(g.KB, a.cb_smem);
     if (a.cb_smem) {
         auto kern = k_pair_rows<T, Q, true>;
@@ -93,29 +104,39 @@ struct ProfScope {
 
 template <typename T>
 cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     constexpr bool f32 = sizeof(T) == 4;
-    CMIF_SIZE_SWITCH(g.Q, {
-        ProfScope ps(a.prof, f32 ? "fwd_rows_A_f32" : "fwd_rows_A_f64", s);
-        e = (launch_fwd_rows<T, SZ>(a.A, a.MA, g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st, a.conditional, s));
-    } if (e != cudaSuccess) return e; {
-        ProfScope ps(a.prof, f32 ? "fwd_rows_B_f32" : "fwd_rows_B_f64", s);
-        e = (launch_fwd_rows<T, SZ>(a.B, a.MB, g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st, a.conditional, s));
-    } if (e != cudaSuccess) return e);
-    CMIF_SIZE_SWITCH(g.P, {
-        ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : "fwd_cols_A_f64", s);
-        e = (launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional, s));
-    } if (e != cudaSuccess) return e; {
-        ProfScope ps(a.prof, f32 ? "fwd_cols_B_f32" : "fwd_cols_B_f64", s);
-        e = (launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional, s));
-    } if (e != cudaSuccess) return e; {
-        ProfScope ps(a.prof, f32 ? "pair_cols_f32" : "pair_cols_f64", s);
-        e = (launch_pair_cols<T, SZ>(g, a, s));
-    } if (e != cudaSuccess) return e);
-    CMIF_SIZE_SWITCH(g.Q, {
-        ProfScope ps(a.prof, f32 ? "pair_rows_f32" : "pair_rows_f64", s);
-        e = (launch_pair_rows<T, SZ>(g, a, s));
-    } if (e != cudaSuccess) return e);
+    const unsigned stg = a.stages ? a.stages : STAGE_ALL;
+    if (stg & STAGE_FWD_A) {
+        CMIF_SIZE_SWITCH(g.Q, {
+            ProfScope ps(a.prof, f32 ? "fwd_rows_A_f32" : "fwd_rows_A_f64", s);
+            e = (launch_fwd_rows<T, SZ>(a.A, a.MA, g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st, a.conditional, s));
+        } if (e != cudaSuccess) return e);
+        CMIF_SIZE_SWITCH(g.P, {
+            ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : "fwd_cols_A_f64", s);
+            e = (launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional, s));
+        } if (e != cudaSuccess) return e);
+    }
+    if (stg & STAGE_FWD_B) {
+        CMIF_SIZE_SWITCH(g.Q, {
+            ProfScope ps(a.prof, f32 ? "fwd_rows_B_f32" : "fwd_rows_B_f64", s);
+            e = (launch_fwd_rows<T, SZ>(a.B, a.MB, g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st, a.conditional, s));
+        } if (e != cudaSuccess) return e);
+        CMIF_SIZE_SWITCH(g.P, {
+            ProfScope ps(a.prof, f32 ? "fwd_cols_B_f32" : "fwd_cols_B_f64", s);
+            e = (launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional, s));
+        } if (e != cudaSuccess) return e);
+    }
+    if (stg & STAGE_PAIRS) {
+        CMIF_SIZE_SWITCH(g.P, {
+            ProfScope ps(a.prof, f32 ? "pair_cols_f32" : "pair_cols_f64", s);
+            e = (launch_pair_cols<T, SZ>(g, a, s));
+        } if (e != cudaSuccess) return e);
+        CMIF_SIZE_SWITCH(g.Q, {
+            ProfScope ps(a.prof, f32 ? "pair_rows_f32" : "pair_rows_f64", s);
+            e = (launch_pair_rows<T, SZ>(g, a, s));
+        } if (e != cudaSuccess) return e);
+    }
     return cudaSuccess;
 }
 
@@ -159,6 +180,34 @@ cudaError_t rows_max_blocks_per_sm(int Q, int KB, bool cb_smem, int* out) {
     });
     return cudaSuccess;
 }
+
+#ifdef CMIF_DEFINE_TM_HELPERS
+int rows_tm_cols(int Q, int KB) {
+    int U = 0;
+    if (Q == 2048) U = RowTmCfg<2048>::U;
+    else if (Q == 1024) U = RowTmCfg<1024>::U;
+    else return 0;
+    const int need = tm_cols_needed(KB, U);
+    return need <= 512 ? tm_alloc_cols(need) : 0;
+}
+
+cudaError_t rows_tm_max_blocks_per_sm(int Q, int* out) {
+    if (Q == 2048) {
+        cudaError_t e = ensure_smem(k_pair_rows_tm<2048>, RowTmCfg<2048>::SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pair_rows_tm<2048>, RowTmCfg<2048>::THREADS,
+                                                             RowTmCfg<2048>::SMEM);
+    }
+    if (Q == 1024) {
+        cudaError_t e = ensure_smem(k_pair_rows_tm<1024>, RowTmCfg<1024>::SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pair_rows_tm<1024>, RowTmCfg<1024>::THREADS,
+                                                             RowTmCfg<1024>::SMEM);
+    }
+    *out = 0;
+    return cudaSuccess;
+}
+#endif
 
 #define CMIF_INSTANTIATE(T)                                                             \
     template cudaError_t run_pipeline<T>(const Geom&, const PipeArgs<T>&, cudaStream_t); \

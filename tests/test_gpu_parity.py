@@ -84,6 +84,24 @@ def test_ragged_random(cm, prec_name, shape):
     check_exact(cm, A, MA, B, MB, shape[4], shape[5], getattr(cm, prec_name), gamma=0.3)
 
 
+# Wide maps (Q = 1024 / 2048) run the row kernel that keeps the B-marginals in
+# Tensor Memory and prefetches Y rows with TMA: K_B = 16 takes its fast path,
+# other K_B the general one.  Also check it against the shared-memory kernel.
+WIDE = [((20, 600, 30, 500), (16, 16)), ((16, 300, 12, 400), (5, 7)), ((9, 700, 11, 640), (16, 16)),
+        ((12, 260, 10, 300), (24, 3))]
+
+
+@pytest.mark.parametrize("shape,K", WIDE, ids=lambda x: "x".join(map(str, x)))
+def test_wide_rows_tmem_path(cm, shape, K, monkeypatch):
+    rng = np.random.default_rng(sum(shape) * 7 + K[0])
+    A, MA, B, MB = _rand(rng, *shape, *K)
+    g, ref = check_exact(cm, A, MA, B, MB, K[0], K[1], cm.FP32, gamma=0.5)
+    monkeypatch.setenv("CMIF_DISABLE_TMEM", "1")
+    g2 = run_gpu(cm, A, MA, B, MB, K[0], K[1], cm.FP32, counts=True, gamma=0.5)
+    assert np.array_equal(g2["counts"], g["counts"]) and np.array_equal(g2["n"], g["n"])
+    assert np.array_equal(g2["mi"], g["mi"])
+
+
 def test_null_masks_and_voronoi(cm):
     rng = np.random.default_rng(11)
     A = synth.make_field(rng, 48, 40, 30, 6).image(48, 40)
