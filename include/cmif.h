@@ -70,10 +70,13 @@ typedef enum {
 /* Arithmetic of the FFT correlations.  Counts are exact when every pre-rounding
  * residual |c - round(c)| stays below 0.25 (checked on every call).
  *   CMIF_FP32   : FP32 transforms (fast; exact for balanced labels up to ~1024^2)
- *   CMIF_SPLIT32: two-term FP32 transforms (not built yet: CMIF_ERR_NOT_IMPLEMENTED)
+ *   CMIF_SPLIT32: two-term FP32 transforms (hi + lo floats, ~48 significant
+ *                 bits from FP32 units; exact everywhere in range)
  *   CMIF_FP64   : FP64 transforms (exact everywhere in range; slow on GB300)
- *   CMIF_AUTO   : FP32, re-run in FP64 on the device when the FP32 residual
- *                 breaches the guard (no host round trip). */
+ *   CMIF_AUTO   : FP32, re-run on the device in two-term FP32 when the FP32
+ *                 residual breaches the guard (no host round trip); the
+ *                 environment variable CMIF_AUTO_TIER2=fp64 at plan creation
+ *                 makes the re-run FP64 instead. */
 typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } cmif_precision;
 
 /* Plan flags. */

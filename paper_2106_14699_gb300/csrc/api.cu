@@ -43,7 +43,9 @@ struct cmif_plan_s {
     unsigned flags = 0;
     Workspace<float> w32;
     Workspace<double> w64;
+    Workspace<df32> ws32;  // two-term FP32 (split precision)
     bool has32 = false, has64 = false;
+    cmif_precision tier2 = CMIF_SPLIT32;  // precision of AUTO's re-run
     DevStatus* st = nullptr;      // status of the map being computed (reset per map)
     DevStatus* st_total = nullptr;  // status of the whole call (what cmif_get_status reports)
     PeakPart* parts = nullptr;
@@ -133,6 +135,7 @@ void free_plan(cmif_plan p) {
     cudaDeviceSynchronize();
     if (p->w32.base) cudaFree(p->w32.base);
     if (p->w64.base) cudaFree(p->w64.base);
+    if (p->ws32.base) cudaFree(p->ws32.base);
     if (p->small) cudaFree(p->small);
     if (p->stage) cudaFree(p->stage);
     p->prof.destroy();
@@ -188,17 +191,31 @@ cmif_status compute_map(cmif_plan p, const int32_t* A, const uint8_t* MA, const 
         cudaError_t e = launch_check_escalate(p->st, s);
         if (e != cudaSuccess) return from_cuda(e);
     }
-    if (p->prec == CMIF_FP64 || p->prec == CMIF_AUTO) {
-        PipeArgs<double> a = p->w64.args;
-        fill_io(a, A, MA, B, MB, mi, n, counts, p->st);
-        a.prof = p->prof.enabled ? &p->prof : nullptr;
-        a.stages = STAGE_ALL;
-        a.prec_slot = 1;
-        a.conditional = (p->prec == CMIF_AUTO) ? 1 : 0;
-        cudaError_t e = run_pipeline<double>(g, a, s);
+    // second tier: the plan's FP64 / split precision, or AUTO's re-run (gated on the device)
+    const cmif_precision second = (p->prec == CMIF_AUTO) ? p->tier2 : p->prec;
+    if (p->prec != CMIF_FP32) {
+        const int cond = (p->prec == CMIF_AUTO) ? 1 : 0;
+        cudaError_t e;
+        if (second == CMIF_FP64) {
+            PipeArgs<double> a = p->w64.args;
+            fill_io(a, A, MA, B, MB, mi, n, counts, p->st);
+            a.prof = p->prof.enabled ? &p->prof : nullptr;
+            a.stages = STAGE_ALL;
+            a.prec_slot = 1;
+            a.conditional = cond;
+            e = run_pipeline<double>(g, a, s);
+        } else {
+            PipeArgs<df32> a = p->ws32.args;
+            fill_io(a, A, MA, B, MB, mi, n, counts, p->st);
+            a.prof = p->prof.enabled ? &p->prof : nullptr;
+            a.stages = STAGE_ALL;
+            a.prec_slot = 1;
+            a.conditional = cond;
+            e = run_pipeline<df32>(g, a, s);
+        }
         if (e != cudaSuccess) return from_cuda(e);
     }
-    const int slot_default = (p->prec == CMIF_FP64) ? 1 : 0;
+    const int slot_default = (p->prec == CMIF_FP64 || p->prec == CMIF_SPLIT32) ? 1 : 0;
     p->prof.begin("finalize", s);
     cudaError_t e = launch_finalize(p->st, 1, slot_default, s);
     if (e == cudaSuccess) e = launch_merge_status(p->st, p->st_total, slot_default, s);
@@ -218,8 +235,7 @@ cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W
         return CMIF_ERR_INVALID_ARG;
     if ((long long)H_A * W_A > (1LL << 22) || (long long)H_B * W_B > (1LL << 22)) return CMIF_ERR_INVALID_ARG;
     if (flags & ~CMIF_FLAG_DEBUG_COUNTS) return CMIF_ERR_INVALID_ARG;
-    if (prec == CMIF_SPLIT32) return CMIF_ERR_NOT_IMPLEMENTED;
-    if (prec != CMIF_FP32 && prec != CMIF_FP64 && prec != CMIF_AUTO) return CMIF_ERR_INVALID_ARG;
+    if (prec != CMIF_FP32 && prec != CMIF_SPLIT32 && prec != CMIF_FP64 && prec != CMIF_AUTO) return CMIF_ERR_INVALID_ARG;
     Geom g{};
     g.HA = H_A; g.WA = W_A; g.HB = H_B; g.WB = W_B; g.KA = K_A; g.KB = K_B;
     g.R = H_A + H_B - 1;
@@ -244,17 +260,24 @@ cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W
         st = alloc_workspace<float>(p, p->w32);
         p->has32 = (st == CMIF_OK);
     }
-    if (st == CMIF_OK && (prec == CMIF_FP64 || prec == CMIF_AUTO)) {
+    const char* t2 = std::getenv("CMIF_AUTO_TIER2");  // "fp64" makes AUTO re-run in FP64 instead of split FP32
+    p->tier2 = (t2 && std::strcmp(t2, "fp64") == 0) ? CMIF_FP64 : CMIF_SPLIT32;
+    if (st == CMIF_OK && (prec == CMIF_FP64 || (prec == CMIF_AUTO && p->tier2 == CMIF_FP64))) {
         st = alloc_workspace<double>(p, p->w64);
         p->has64 = (st == CMIF_OK);
+    }
+    if (st == CMIF_OK && (prec == CMIF_SPLIT32 || (prec == CMIF_AUTO && p->tier2 == CMIF_SPLIT32))) {
+        st = alloc_workspace<df32>(p, p->ws32);
     }
     if (st == CMIF_OK) {
         Tw<float> tf;
         Tw<double> td;
-        e = get_twiddles(p->device, &tf, &td);
+        Tw<df32> ts;
+        e = get_twiddles(p->device, &tf, &td, &ts);
         if (e != cudaSuccess) st = from_cuda(e);
         p->w32.args.tw = tf;
         p->w64.args.tw = td;
+        p->ws32.args.tw = ts;
     }
     if (st == CMIF_OK) {
         p->nparts = 2 * p->num_sms;
@@ -301,7 +324,7 @@ cmif_status cmif_plan_destroy(cmif_plan plan) {
 
 cmif_status cmif_plan_workspace_bytes(cmif_plan plan, size_t* bytes) {
     if (!plan || !bytes) return CMIF_ERR_INVALID_ARG;
-    *bytes = plan->w32.bytes + plan->w64.bytes;
+    *bytes = plan->w32.bytes + plan->w64.bytes + plan->ws32.bytes;
     return CMIF_OK;
 }
 

@@ -20,6 +20,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "df32.cuh"
 
 namespace cmif {
 
@@ -117,7 +118,7 @@ __host__ __device__ constexpr int team_m(int N, int mmax) {
     return M;
 }
 template <typename T>
-__host__ __device__ constexpr int max_m() { return sizeof(T) == 4 ? 32 : 16; }
+__host__ __device__ constexpr int max_m() { return sizeof(T) == 4 ? 32 : 16; }  // FP32: 32; FP64 and two-term FP32: 16
 
 // Twiddle tables in device memory, filled once per device from FP64 values.
 //   n[l][k]         = e^{-2 pi i k / 2^l},           k < 2^l

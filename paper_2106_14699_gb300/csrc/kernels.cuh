@@ -67,6 +67,15 @@ template <>
 __device__ __forceinline__ float rint_t<float>(float v) { return rintf(v); }
 template <>
 __device__ __forceinline__ double rint_t<double>(double v) { return rint(v); }
+// nearest integer to hi + lo (|hi + lo| < 2^23): round hi, then let lo move it by one
+template <>
+__device__ __forceinline__ df32 rint_t<df32>(df32 v) {
+    float r = rintf(v.hi);
+    const float d = (v.hi - r) + v.lo;  // v.hi - r is exact
+    if (d > 0.5f) r += 1.f;
+    else if (d < -0.5f) r -= 1.f;
+    return {r, 0.f};
+}
 
 // Map a circular shift index (0..n-1) to the output map index, or -1 when the
 // shift lies in the zero-padding gap (cannot happen for in-range shifts).

@@ -260,12 +260,13 @@ struct DevTables {
     void* buf = nullptr;
     Tw<float> tf{};
     Tw<double> td{};
+    Tw<df32> ts{};
 };
 
 static std::mutex g_tw_mu;
 static DevTables g_tw[64];
 
-cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td) {
+cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td, Tw<df32>* ts) {
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_tw_mu);
     DevTables& t = g_tw[device];
@@ -297,22 +298,28 @@ cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td) {
         }
         const size_t n = re.size();
         std::vector<double> hd(2 * n);
-        std::vector<float> hf(2 * n);
+        std::vector<float> hf(2 * n), hs(4 * n);
         for (size_t i = 0; i < n; ++i) {
             hd[2 * i] = re[i];
             hd[2 * i + 1] = im[i];
             hf[2 * i] = (float)re[i];
             hf[2 * i + 1] = (float)im[i];
+            const float rh = (float)re[i], ih = (float)im[i];
+            hs[4 * i] = rh;
+            hs[4 * i + 1] = (float)(re[i] - (double)rh);
+            hs[4 * i + 2] = ih;
+            hs[4 * i + 3] = (float)(im[i] - (double)ih);
         }
-        const size_t bytes_d = 2 * n * sizeof(double), bytes_f = 2 * n * sizeof(float);
+        const size_t bytes_d = 2 * n * sizeof(double), bytes_f = 2 * n * sizeof(float), bytes_s = 4 * n * sizeof(float);
         int prev = -1;
         cudaGetDevice(&prev);
         cudaError_t e = cudaSetDevice(device);
         if (e != cudaSuccess) return e;
         void* buf = nullptr;
-        e = cudaMalloc(&buf, bytes_d + bytes_f);
+        e = cudaMalloc(&buf, bytes_d + bytes_f + bytes_s);
         if (e == cudaSuccess) e = cudaMemcpy(buf, hd.data(), bytes_d, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy((char*)buf + bytes_d, hf.data(), bytes_f, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy((char*)buf + bytes_d + bytes_f, hs.data(), bytes_s, cudaMemcpyHostToDevice);
         if (prev >= 0) cudaSetDevice(prev);
         if (e != cudaSuccess) {
             if (buf) cudaFree(buf);
@@ -321,11 +328,13 @@ cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td) {
         t.buf = buf;
         const cpx<double>* bd = reinterpret_cast<const cpx<double>*>(buf);
         const cpx<float>* bf = reinterpret_cast<const cpx<float>*>((char*)buf + bytes_d);
-        for (int l = 0; l < 14; ++l) { t.td.n[l] = bd + off_n[l]; t.tf.n[l] = bf + off_n[l]; }
-        for (int l = 0; l < 6; ++l) { t.td.sq[l] = bd + off_sq[l]; t.tf.sq[l] = bf + off_sq[l]; }
+        const cpx<df32>* bs = reinterpret_cast<const cpx<df32>*>((char*)buf + bytes_d + bytes_f);
+        for (int l = 0; l < 14; ++l) { t.td.n[l] = bd + off_n[l]; t.tf.n[l] = bf + off_n[l]; t.ts.n[l] = bs + off_n[l]; }
+        for (int l = 0; l < 6; ++l) { t.td.sq[l] = bd + off_sq[l]; t.tf.sq[l] = bf + off_sq[l]; t.ts.sq[l] = bs + off_sq[l]; }
     }
     if (tf) *tf = t.tf;
     if (td) *td = t.td;
+    if (ts) *ts = t.ts;
     return cudaSuccess;
 }
 

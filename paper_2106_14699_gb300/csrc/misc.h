@@ -24,7 +24,7 @@ cudaError_t launch_warp_nn(const int32_t* B, const uint8_t* MB, int H, int W, do
                            cudaStream_t s);
 cudaError_t launch_merge_status(const DevStatus* m, DevStatus* tot, int slot_default, cudaStream_t s);
 cudaError_t launch_topk(const void* peaks, int n, int k, void* out, cudaStream_t s);
-cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td);
+cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td, Tw<df32>* ts);
 // Host copy of the FP32 twiddle tables (interleaved re, im) and the entry offsets
 // of each table, in the same layout get_twiddles() uploads.
 void twiddle_table_f32(std::vector<float>& out, size_t off_n[14], size_t off_sq[6]);

@@ -3,6 +3,7 @@
 #pragma once
 #include "pipeline.cuh"
 #include "rows_tm.cuh"
+#include <type_traits>
 
 namespace cmif {
 
@@ -59,7 +60,7 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
     cudaError_t e = ensure_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(g.KA * g.KB, (g.Qh + C::TPB - 1) / C::TPB);
-    const T scale = T(1) / (T(g.P) * T(g.Q));  // exact: P*Q is a power of two
+    const T scale = T(1.0 / ((double)g.P * (double)g.Q));  // exact: P*Q is a power of two
     kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KB, g.Qh, g.HA, g.HB, scale, g.R, g.Qs, a.Y, a.tw, a.st,
                                         a.conditional);
     return cudaGetLastError();
@@ -106,34 +107,35 @@ template <typename T>
 cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     constexpr bool f32 = sizeof(T) == 4;
+    constexpr bool split = std::is_same<T, df32>::value;
     const unsigned stg = a.stages ? a.stages : STAGE_ALL;
     if (stg & STAGE_FWD_A) {
         CMIF_SIZE_SWITCH(g.Q, {
-            ProfScope ps(a.prof, f32 ? "fwd_rows_A_f32" : "fwd_rows_A_f64", s);
+            ProfScope ps(a.prof, f32 ? "fwd_rows_A_f32" : split ? "fwd_rows_A_s32" : "fwd_rows_A_f64", s);
             e = (launch_fwd_rows<T, SZ>(a.A, a.MA, g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st, a.conditional, s));
         } if (e != cudaSuccess) return e);
         CMIF_SIZE_SWITCH(g.P, {
-            ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : "fwd_cols_A_f64", s);
+            ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : split ? "fwd_cols_A_s32" : "fwd_cols_A_f64", s);
             e = (launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional, s));
         } if (e != cudaSuccess) return e);
     }
     if (stg & STAGE_FWD_B) {
         CMIF_SIZE_SWITCH(g.Q, {
-            ProfScope ps(a.prof, f32 ? "fwd_rows_B_f32" : "fwd_rows_B_f64", s);
+            ProfScope ps(a.prof, f32 ? "fwd_rows_B_f32" : split ? "fwd_rows_B_s32" : "fwd_rows_B_f64", s);
             e = (launch_fwd_rows<T, SZ>(a.B, a.MB, g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st, a.conditional, s));
         } if (e != cudaSuccess) return e);
         CMIF_SIZE_SWITCH(g.P, {
-            ProfScope ps(a.prof, f32 ? "fwd_cols_B_f32" : "fwd_cols_B_f64", s);
+            ProfScope ps(a.prof, f32 ? "fwd_cols_B_f32" : split ? "fwd_cols_B_s32" : "fwd_cols_B_f64", s);
             e = (launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional, s));
         } if (e != cudaSuccess) return e);
     }
     if (stg & STAGE_PAIRS) {
         CMIF_SIZE_SWITCH(g.P, {
-            ProfScope ps(a.prof, f32 ? "pair_cols_f32" : "pair_cols_f64", s);
+            ProfScope ps(a.prof, f32 ? "pair_cols_f32" : split ? "pair_cols_s32" : "pair_cols_f64", s);
             e = (launch_pair_cols<T, SZ>(g, a, s));
         } if (e != cudaSuccess) return e);
         CMIF_SIZE_SWITCH(g.Q, {
-            ProfScope ps(a.prof, f32 ? "pair_rows_f32" : "pair_rows_f64", s);
+            ProfScope ps(a.prof, f32 ? "pair_rows_f32" : split ? "pair_rows_s32" : "pair_rows_f64", s);
             e = (launch_pair_rows<T, SZ>(g, a, s));
         } if (e != cudaSuccess) return e);
     }

@@ -46,7 +46,6 @@ def test_host_side_argument_errors(libcmif):
     assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 65, 2, cm.FP32, 0) == 1    # K_A > 64
     assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 2, 2, 9, 0) == 1           # bad precision
     assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 2, 2, cm.FP32, 0x80) == 1  # unknown flag
-    assert libcmif.cmif_plan_create_ex(P, 4, 4, 4, 4, 2, 2, cm.SPLIT32, 0) == 7  # not built
     assert libcmif.cmif_plan_create_ex(P, 4096, 1025, 8, 8, 2, 2, cm.FP32, 0) == 1  # H*W > 2^22
     assert libcmif.cmif_plan_create_ex(P, 2049, 2, 2049, 2, 2, 2, cm.FP32, 0) == 8  # P > 4096
     assert libcmif.cmif_plan_create_ex(None, 4, 4, 4, 4, 2, 2, cm.FP32, 0) == 1

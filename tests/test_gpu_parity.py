@@ -76,7 +76,7 @@ RAGGED = [(1, 1, 1, 1, 1, 1), (1, 5, 3, 1, 2, 3), (7, 9, 5, 6, 5, 4), (17, 33, 2
           (64, 70, 31, 45, 13, 24), (70, 70, 70, 70, 8, 8), (5, 130, 9, 120, 4, 4)]
 
 
-@pytest.mark.parametrize("prec_name", ["FP32", "FP64"])
+@pytest.mark.parametrize("prec_name", ["FP32", "SPLIT32", "FP64"])
 @pytest.mark.parametrize("shape", RAGGED, ids=lambda s: "x".join(map(str, s)))
 def test_ragged_random(cm, prec_name, shape):
     rng = np.random.default_rng(hash(shape) % 2**32)
@@ -139,7 +139,7 @@ def test_label_range_reported(cm):
     assert g["status"][0] == "OK"
 
 
-@pytest.mark.parametrize("prec_name", ["FP64", "FP32"])
+@pytest.mark.parametrize("prec_name", ["FP64", "SPLIT32", "FP32"])
 def test_config1_full(cm, prec_name):
     cfg = synth.make_config(1)
     g, ref = check_exact(cm, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 8, 8, getattr(cm, prec_name), gamma=0.5)
@@ -187,9 +187,13 @@ def test_config3_full_size_sampled(cm):
     assert (dy, dx) == tuple(cfg["shift"])
 
 
-def test_auto_escalates_unbalanced_labels(cm):
+@pytest.mark.parametrize("tier2", ["split", "fp64"])
+def test_auto_escalates_unbalanced_labels(cm, tier2, monkeypatch):
     """A dominant label makes FP32 correlations of ~10^6 counts inexact; AUTO
-    must detect it on the device and re-run in FP64 (exact)."""
+    must detect it on the device and re-run in the second tier (two-term FP32
+    by default, FP64 on request), which is exact."""
+    if tier2 == "fp64":
+        monkeypatch.setenv("CMIF_AUTO_TIER2", "fp64")
     rng = np.random.default_rng(21)
     H = 1024
     A = (rng.random((H, H)) < 0.02).astype(np.int32)
