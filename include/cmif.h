@@ -81,6 +81,8 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
 
 /* Plan flags. */
 #define CMIF_FLAG_DEBUG_COUNTS 1u /* allow a non-NULL counts output in cmif_compute */
+#define CMIF_FLAG_GRAPH 2u        /* capture each call's launches in a CUDA graph once and replay it while the
+                                     call's arguments (pointers, gamma, angles) are unchanged */
 
 /* One argmax record of Alg. 1: the displacement chi = (dy, dx) maximising
  * CMIF among shifts with N(chi) >= gamma * max N, for transform angle_idx
@@ -168,6 +170,43 @@ cmif_status cmif_rotate_nn(const int32_t* B, const uint8_t* M_B, int H, int W, d
 cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
                                  const uint8_t* M_B, const double* angles_rad_host, int n_angles, double gamma,
                                  int top_k, cmif_peak* topk_dev, double* mi_maps, void* stream);
+
+/* ---- Batches of image pairs (many sizes, label counts and angle sets) ----
+ * One batch holds one device workspace sized for its largest pair; the pairs
+ * run one after another on the call's stream (each as cmif_align_rotations,
+ * or as cmif_compute when it has no angles), so that workspace serves them
+ * all.  With CMIF_FLAG_GRAPH the whole batch is captured once into a CUDA
+ * graph and replayed.  The paper loops over pairs on the host; the batch is
+ * this library's way of running such a loop (Alg. 1 per pair). */
+typedef struct cmif_batch_s* cmif_batch;
+typedef struct {
+    const int32_t* A;           /* device, H_A x W_A */
+    const uint8_t* M_A;         /* device or NULL */
+    const int32_t* B;           /* device, H_B x W_B */
+    const uint8_t* M_B;         /* device or NULL */
+    int H_A, W_A, H_B, W_B, K_A, K_B;
+    const double* angles_rad;   /* host, n_angles radians (copied at cmif_batch_create) */
+    int n_angles;               /* 0: translation only (one map, angle_idx 0) */
+    double gamma;               /* Alg. 1 overlap fraction in [0, 1] */
+} cmif_pair_desc;
+
+/* Validate the pairs (limits as cmif_plan_create_ex, 0 <= n_angles <= 4096),
+ * copy the descriptors and allocate the shared workspace.  The device images
+ * the descriptors point to must stay valid and unchanged for the batch's life.
+ * prec as for plans; flags: 0 or CMIF_FLAG_GRAPH. */
+cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc* descs, cmif_precision prec,
+                              unsigned flags);
+
+/* Run the batch on stream.  results_dev: device cmif_peak[n_pairs], pair i's
+ * Alg. 1 choice (best over its angles, as topk_dev[0] of cmif_align_rotations).
+ * status_dev: device int32[n_pairs] or NULL, pair i's device-side cmif_status. */
+cmif_status cmif_compute_batch(cmif_batch batch, cmif_peak* results_dev, int32_t* status_dev, void* stream);
+
+/* Device status over the whole last run (synchronises), as cmif_get_status. */
+cmif_status cmif_batch_get_status(cmif_batch batch, cmif_status* device_side, double* max_residual, int* escalations);
+
+/* Free the batch (synchronises its device).  NULL is ignored. */
+cmif_status cmif_batch_destroy(cmif_batch batch);
 
 /* Device status of the last call on this plan (synchronises the plan's
  * last stream).  device_side: CMIF_OK, or the first device problem in the

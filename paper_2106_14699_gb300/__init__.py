@@ -21,6 +21,7 @@ __all__ = ["FP32", "SPLIT32", "FP64", "AUTO", "Plan", "Peak", "CmifError", "lib"
 
 FP32, SPLIT32, FP64, AUTO = 0, 1, 2, 3
 FLAG_DEBUG_COUNTS = 1
+FLAG_GRAPH = 2
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "LABEL_RANGE", 3: "OOM", 4: "CUDA", 5: "PRECISION",
                 6: "TIMEOUT", 7: "NOT_IMPLEMENTED", 8: "UNSUPPORTED"}
 
@@ -31,6 +32,13 @@ class CmifError(RuntimeError):
         super().__init__(f"{what}: {STATUS_NAMES.get(code, code)}" if what else STATUS_NAMES.get(code, str(code)))
 
 
+class PairDesc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("M_A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("M_B", ctypes.c_void_p),
+                ("H_A", ctypes.c_int), ("W_A", ctypes.c_int), ("H_B", ctypes.c_int), ("W_B", ctypes.c_int),
+                ("K_A", ctypes.c_int), ("K_B", ctypes.c_int), ("angles_rad", ctypes.c_void_p),
+                ("n_angles", ctypes.c_int), ("gamma", ctypes.c_double)]
+
+
 class Peak(ctypes.Structure):
     _fields_ = [("angle_idx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dx", ctypes.c_int32),
                 ("n", ctypes.c_int32), ("mi", ctypes.c_double)]
@@ -39,6 +47,7 @@ class Peak(ctypes.Structure):
 EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_destroy", "cmif_plan_workspace_bytes",
            "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
            "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_rotate_nn", "cmif_align_rotations",
+           "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status", "cmif_batch_destroy",
            "cmif_status_string"]
 
 _lib = None
@@ -65,6 +74,10 @@ def lib():
         L.cmif_compute_noalloc.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, D, P, P, P]
         L.cmif_rotate_nn.argtypes = [P, P, I, I, D, P, P, P]
         L.cmif_align_rotations.argtypes = [P, P, P, P, P, P, I, D, I, P, P, P]
+        L.cmif_batch_create.argtypes = [ctypes.POINTER(P), I, P, I, U]
+        L.cmif_compute_batch.argtypes = [P, P, P, P]
+        L.cmif_batch_get_status.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
+        L.cmif_batch_destroy.argtypes = [P]
         L.cmif_status_string.argtypes = [I]
         L.cmif_status_string.restype = ctypes.c_char_p
         for name in EXPORTS[:-1]:
@@ -102,9 +115,9 @@ def _check(code, what):
 class Plan:
     """A CMIF plan for images H_A x W_A and H_B x W_B with K_A, K_B labels."""
 
-    def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False):
+    def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False, graph=False):
         self._h = ctypes.c_void_p()
-        flags = FLAG_DEBUG_COUNTS if debug_counts else 0
+        flags = (FLAG_DEBUG_COUNTS if debug_counts else 0) | (FLAG_GRAPH if graph else 0)
         _check(lib().cmif_plan_create_ex(ctypes.byref(self._h), H_A, W_A, H_B, W_B, K_A, K_B, precision, flags),
                "cmif_plan_create_ex")
         self.H_A, self.W_A, self.H_B, self.W_B, self.K_A, self.K_B = H_A, W_A, H_B, W_B, K_A, K_B
@@ -171,6 +184,49 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """cmif_batch over pairs given as dicts with device tensors A, M_A, B, M_B, K_A, K_B,
+    host angle lists `angles` (radians) and `gamma`."""
+
+    def __init__(self, pairs, precision=FP32, graph=True):
+        self._keep = []
+        descs = (PairDesc * len(pairs))()
+        for i, p in enumerate(pairs):
+            ang = np.ascontiguousarray(np.asarray(p.get("angles", []), dtype=np.float64))
+            self._keep.append(ang)
+            H_A, W_A = p["A"].shape
+            H_B, W_B = p["B"].shape
+            descs[i] = PairDesc(_ptr(p["A"]), _ptr(p.get("M_A")), _ptr(p["B"]), _ptr(p.get("M_B")), H_A, W_A, H_B, W_B,
+                                p["K_A"], p["K_B"], ang.ctypes.data if len(ang) else None, len(ang),
+                                float(p.get("gamma", 0.5)))
+        self._descs = descs
+        self._h = ctypes.c_void_p()
+        _check(lib().cmif_batch_create(ctypes.byref(self._h), len(pairs), ctypes.cast(descs, ctypes.c_void_p),
+                                       precision, FLAG_GRAPH if graph else 0), "cmif_batch_create")
+        self.n = len(pairs)
+
+    def run(self, results_dev, status_dev=None, stream=None):
+        _check(lib().cmif_compute_batch(self._h, _ptr(results_dev), _ptr(status_dev), _stream(stream)),
+               "cmif_compute_batch")
+
+    def status(self):
+        ds, res, esc = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(lib().cmif_batch_get_status(self._h, ctypes.byref(ds), ctypes.byref(res), ctypes.byref(esc)),
+               "cmif_batch_get_status")
+        return STATUS_NAMES.get(ds.value, ds.value), res.value, esc.value
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().cmif_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rotate_nn(B, M_B, theta, B_out, M_out, stream=None):

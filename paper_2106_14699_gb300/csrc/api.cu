@@ -3,7 +3,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "cmif.h"
 #include "kernels.cuh"
@@ -50,7 +52,9 @@ struct cmif_plan_s {
     DevStatus* st_total = nullptr;  // status of the whole call (what cmif_get_status reports)
     PeakPart* parts = nullptr;
     int nparts = 0;
-    void* small = nullptr;  // st + parts + internal N map in one allocation
+    void* mem = nullptr;      // the plan's one device allocation (nullptr when a batch owns the memory)
+    size_t mem_bytes = 0;
+    size_t small_bytes = 0;
     int32_t* nbuf = nullptr;  // N map used when the caller passes no n_map
     double* mibuf = nullptr;  // MI map used by cmif_align_rotations when the caller keeps no maps
     int32_t* wB = nullptr;    // rotated floating image (cmif_align_rotations)
@@ -61,6 +65,12 @@ struct cmif_plan_s {
     size_t stage_bytes = 0;
     cudaStream_t last_stream = nullptr;
     Profiler prof;
+    // CUDA-graph replay (CMIF_FLAG_GRAPH): the captured launch sequence of the last
+    // call, replayed while the call's arguments are unchanged
+    bool use_graph = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
 };
 
 namespace {
@@ -71,15 +81,12 @@ cmif_status from_cuda(cudaError_t e) {
     return CMIF_ERR_CUDA;
 }
 
+// Row-kernel choice for precision T: the TMEM / TMA variant where it applies
+// (FP32, Q = 1024 or 2048), else B-marginals in shared memory when they fit,
+// else in global memory.  Fills tm_cols, cb_smem and rows_grid.
 template <typename T>
-cmif_status alloc_workspace(cmif_plan p, Workspace<T>& w) {
+cmif_status choose_rows(cmif_plan p, Workspace<T>& w) {
     const Geom& g = p->g;
-    const size_t cs = sizeof(cpx<T>);
-    const size_t sT1A = (size_t)g.KA * g.HA * g.Qs * cs, sT1B = (size_t)g.KB * g.HB * g.Qs * cs;
-    const size_t sFA = (size_t)g.KA * g.Qh * g.P * cs, sFB = (size_t)g.KB * g.Qh * g.P * cs;
-    const size_t sY = (size_t)g.KA * g.KB * g.R * g.Qs * cs;
-    // Row kernel: the TMEM / TMA variant where it applies (FP32, Q = 1024 or 2048),
-    // else B-marginal accumulators in shared memory when they fit, else in global memory.
     int bps = 0;
     cudaError_t e = cudaSuccess;
     w.args.tm_cols = 0;
@@ -102,28 +109,49 @@ cmif_status alloc_workspace(cmif_plan p, Workspace<T>& w) {
     }
     if (bps < 1) return CMIF_ERR_UNSUPPORTED;
     w.rows_grid = std::min(g.R, bps * p->num_sms);
-    const size_t sCB = w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float);
-    size_t off = 0;
-    const size_t oT1A = off; off = align_up(off + sT1A, 256);
-    const size_t oT1B = off; off = align_up(off + sT1B, 256);
-    const size_t oFA = off; off = align_up(off + sFA, 256);
-    const size_t oFB = off; off = align_up(off + sFB, 256);
-    const size_t oY = off; off = align_up(off + sY, 256);
-    const size_t oCB = off; off = align_up(off + sCB, 256);
-    void* base = nullptr;
-    e = cudaMalloc(&base, off);
-    if (e != cudaSuccess) { cudaGetLastError(); return CMIF_ERR_OOM; }
-    w.base = base;
-    w.bytes = off;
-    char* b = (char*)base;
-    w.args.T1A = (cpx<T>*)(b + oT1A);
-    w.args.T1B = (cpx<T>*)(b + oT1B);
-    w.args.FA = (cpx<T>*)(b + oFA);
-    w.args.FB = (cpx<T>*)(b + oFB);
-    w.args.Y = (cpx<T>*)(b + oY);
-    w.args.cb_global = w.cb_smem ? nullptr : (float*)(b + oCB);
     w.args.rows_grid = w.rows_grid;
     w.args.cb_smem = w.cb_smem;
+    return CMIF_OK;
+}
+
+// Device bytes of the transform workspace of precision T (after choose_rows).
+template <typename T>
+size_t workspace_bytes(const Geom& g, const Workspace<T>& w) {
+    const size_t cs = sizeof(cpx<T>);
+    size_t off = 0;
+    off = align_up(off + (size_t)g.KA * g.HA * g.Qs * cs, 256);  // T1A
+    off = align_up(off + (size_t)g.KB * g.HB * g.Qs * cs, 256);  // T1B
+    off = align_up(off + (size_t)g.KA * g.Qh * g.P * cs, 256);   // FA
+    off = align_up(off + (size_t)g.KB * g.Qh * g.P * cs, 256);   // FB
+    off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);  // Y
+    off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);  // CB
+    return off;
+}
+
+// Point the workspace's buffers into base (at least workspace_bytes long).
+template <typename T>
+void carve_workspace(const Geom& g, Workspace<T>& w, char* base) {
+    const size_t cs = sizeof(cpx<T>);
+    size_t off = 0;
+    w.args.T1A = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.HA * g.Qs * cs, 256);
+    w.args.T1B = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.HB * g.Qs * cs, 256);
+    w.args.FA = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.Qh * g.P * cs, 256);
+    w.args.FB = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.Qh * g.P * cs, 256);
+    w.args.Y = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);
+    w.args.cb_global = w.cb_smem ? nullptr : (float*)(base + off);
+}
+
+template <typename T>
+cmif_status alloc_workspace(cmif_plan p, Workspace<T>& w) {
+    cmif_status st = choose_rows<T>(p, w);
+    if (st != CMIF_OK) return st;
+    const size_t bytes = workspace_bytes<T>(p->g, w);
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return CMIF_ERR_OOM; }
+    w.base = base;
+    w.bytes = bytes;
+    carve_workspace<T>(p->g, w, (char*)base);
     return CMIF_OK;
 }
 
@@ -133,11 +161,10 @@ void free_plan(cmif_plan p) {
     cudaGetDevice(&prev);
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
-    if (p->w32.base) cudaFree(p->w32.base);
-    if (p->w64.base) cudaFree(p->w64.base);
-    if (p->ws32.base) cudaFree(p->ws32.base);
-    if (p->small) cudaFree(p->small);
+    if (p->mem) cudaFree(p->mem);
     if (p->stage) cudaFree(p->stage);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     p->prof.destroy();
     if (prev >= 0) cudaSetDevice(prev);
     delete p;
@@ -223,18 +250,14 @@ cmif_status compute_map(cmif_plan p, const int32_t* A, const uint8_t* MA, const 
     return from_cuda(e);
 }
 
-}  // namespace
-
-extern "C" {
-
-cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B,
-                                cmif_precision prec, unsigned flags) {
-    if (!out) return CMIF_ERR_INVALID_ARG;
-    *out = nullptr;
+// Validate sizes and flags, set the geometry, pick kernels; allocates nothing
+// (except the per-device twiddle tables on first use).
+cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B, cmif_precision prec,
+                      unsigned flags) {
     if (H_A < 1 || W_A < 1 || H_B < 1 || W_B < 1 || K_A < 1 || K_B < 1 || K_A > 64 || K_B > 64)
         return CMIF_ERR_INVALID_ARG;
     if ((long long)H_A * W_A > (1LL << 22) || (long long)H_B * W_B > (1LL << 22)) return CMIF_ERR_INVALID_ARG;
-    if (flags & ~CMIF_FLAG_DEBUG_COUNTS) return CMIF_ERR_INVALID_ARG;
+    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH)) return CMIF_ERR_INVALID_ARG;
     if (prec != CMIF_FP32 && prec != CMIF_SPLIT32 && prec != CMIF_FP64 && prec != CMIF_AUTO) return CMIF_ERR_INVALID_ARG;
     Geom g{};
     g.HA = H_A; g.WA = W_A; g.HB = H_B; g.WB = W_B; g.KA = K_A; g.KB = K_B;
@@ -245,64 +268,188 @@ cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W
     if (g.P > 4096 || g.Q > 4096) return CMIF_ERR_UNSUPPORTED;
     g.Qh = g.Q / 2 + 1;
     g.Qs = (int)align_up((size_t)g.Qh, 4);
-
-    cmif_plan p = new (std::nothrow) cmif_plan_s();
-    if (!p) return CMIF_ERR_OOM;
     cudaError_t e = cudaGetDevice(&p->device);
-    if (e != cudaSuccess) { delete p; return CMIF_ERR_CUDA; }
+    if (e != cudaSuccess) return CMIF_ERR_CUDA;
     e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (e != cudaSuccess) { delete p; return CMIF_ERR_CUDA; }
+    if (e != cudaSuccess) return CMIF_ERR_CUDA;
     p->g = g;
     p->prec = prec;
     p->flags = flags;
-    cmif_status st = CMIF_OK;
-    if (prec == CMIF_FP32 || prec == CMIF_AUTO) {
-        st = alloc_workspace<float>(p, p->w32);
-        p->has32 = (st == CMIF_OK);
-    }
+    p->use_graph = (flags & CMIF_FLAG_GRAPH) != 0;
     const char* t2 = std::getenv("CMIF_AUTO_TIER2");  // "fp64" makes AUTO re-run in FP64 instead of split FP32
     p->tier2 = (t2 && std::strcmp(t2, "fp64") == 0) ? CMIF_FP64 : CMIF_SPLIT32;
+    cmif_status st = CMIF_OK;
+    if (prec == CMIF_FP32 || prec == CMIF_AUTO) {
+        st = choose_rows<float>(p, p->w32);
+        p->has32 = (st == CMIF_OK);
+    }
     if (st == CMIF_OK && (prec == CMIF_FP64 || (prec == CMIF_AUTO && p->tier2 == CMIF_FP64))) {
-        st = alloc_workspace<double>(p, p->w64);
+        st = choose_rows<double>(p, p->w64);
         p->has64 = (st == CMIF_OK);
     }
     if (st == CMIF_OK && (prec == CMIF_SPLIT32 || (prec == CMIF_AUTO && p->tier2 == CMIF_SPLIT32))) {
-        st = alloc_workspace<df32>(p, p->ws32);
+        st = choose_rows<df32>(p, p->ws32);
     }
-    if (st == CMIF_OK) {
-        Tw<float> tf;
-        Tw<double> td;
-        Tw<df32> ts;
-        e = get_twiddles(p->device, &tf, &td, &ts);
-        if (e != cudaSuccess) st = from_cuda(e);
-        p->w32.args.tw = tf;
-        p->w64.args.tw = td;
-        p->ws32.args.tw = ts;
+    if (st != CMIF_OK) return st;
+    Tw<float> tf;
+    Tw<double> td;
+    Tw<df32> ts;
+    e = get_twiddles(p->device, &tf, &td, &ts);
+    if (e != cudaSuccess) return from_cuda(e);
+    p->w32.args.tw = tf;
+    p->w64.args.tw = td;
+    p->ws32.args.tw = ts;
+    p->nparts = 2 * p->num_sms;
+    return CMIF_OK;
+}
+
+size_t small_bytes_of(const cmif_plan p) {
+    const Geom& g = p->g;
+    size_t off = align_up(sizeof(DevStatus), 256) * 2;
+    off = align_up(off + (size_t)p->nparts * sizeof(PeakPart), 256);
+    off = align_up(off + (size_t)g.R * g.C * sizeof(int32_t), 256);
+    off = align_up(off + (size_t)g.R * g.C * sizeof(double), 256);
+    off = align_up(off + (size_t)g.HB * g.WB * sizeof(int32_t), 256);
+    off = align_up(off + (size_t)g.HB * g.WB, 256);
+    off = align_up(off + (size_t)kMaxAngles * sizeof(PeakRec), 256);
+    return off;
+}
+
+// Device bytes of everything the plan uses: small buffers + one workspace per precision.
+size_t plan_bytes(cmif_plan p) {
+    size_t b = small_bytes_of(p);
+    if (p->has32) b += workspace_bytes<float>(p->g, p->w32);
+    if (p->has64) b += workspace_bytes<double>(p->g, p->w64);
+    if (p->ws32.rows_grid > 0) b += workspace_bytes<df32>(p->g, p->ws32);
+    return b;
+}
+
+// Point the plan's buffers into base (plan_bytes long) and clear its status words.
+cmif_status plan_carve(cmif_plan p, char* base) {
+    const Geom& g = p->g;
+    size_t off = 0;
+    p->st = (DevStatus*)(base + off); off += align_up(sizeof(DevStatus), 256);
+    p->st_total = (DevStatus*)(base + off); off += align_up(sizeof(DevStatus), 256);
+    p->parts = (PeakPart*)(base + off); off = align_up(off + (size_t)p->nparts * sizeof(PeakPart), 256);
+    p->nbuf = (int32_t*)(base + off); off = align_up(off + (size_t)g.R * g.C * sizeof(int32_t), 256);
+    p->mibuf = (double*)(base + off); off = align_up(off + (size_t)g.R * g.C * sizeof(double), 256);
+    p->wB = (int32_t*)(base + off); off = align_up(off + (size_t)g.HB * g.WB * sizeof(int32_t), 256);
+    p->wM = (uint8_t*)(base + off); off = align_up(off + (size_t)g.HB * g.WB, 256);
+    p->peaks = base + off; off = align_up(off + (size_t)kMaxAngles * sizeof(PeakRec), 256);
+    p->small_bytes = off;
+    if (p->has32) { carve_workspace<float>(g, p->w32, base + off); off += workspace_bytes<float>(g, p->w32); }
+    if (p->has64) { carve_workspace<double>(g, p->w64, base + off); off += workspace_bytes<double>(g, p->w64); }
+    if (p->ws32.rows_grid > 0) { carve_workspace<df32>(g, p->ws32, base + off); off += workspace_bytes<df32>(g, p->ws32); }
+    p->w32.bytes = p->has32 ? workspace_bytes<float>(g, p->w32) : 0;
+    p->w64.bytes = p->has64 ? workspace_bytes<double>(g, p->w64) : 0;
+    p->ws32.bytes = p->ws32.rows_grid > 0 ? workspace_bytes<df32>(g, p->ws32) : 0;
+    if (cudaMemset(p->st, 0, 2 * align_up(sizeof(DevStatus), 256)) != cudaSuccess) return CMIF_ERR_CUDA;
+    return CMIF_OK;
+}
+
+template <typename V>
+void key_add(std::vector<unsigned char>& k, const V& v) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+    k.insert(k.end(), b, b + sizeof(V));
+}
+
+// Run `record` (which enqueues a call's launches on the stream it is given)
+// directly, or -- with graph replay on -- capture it once into a CUDA graph on
+// the plan's own stream and replay the graph on s while the call's key (its
+// arguments) is unchanged.  Capture uses relaxed mode and a non-default
+// stream, so the caller's stream may be the legacy default stream.
+template <typename Fn>
+cmif_status run_graph(cmif_plan p, cudaStream_t s, const std::vector<unsigned char>& key, Fn&& record) {
+    if (!p->use_graph) return record(s);
+    cudaError_t e = cudaSuccess;
+    if (!(p->gexec && key == p->gkey)) {
+        if (!p->cap_stream) {
+            e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+        const bool prof = p->prof.enabled;
+        p->prof.enabled = false;  // no per-launch events inside a graph
+        e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) { p->prof.enabled = prof; return from_cuda(e); }
+        cmif_status st = record(p->cap_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(p->cap_stream, &graph);
+        p->prof.enabled = prof;
+        if (st != CMIF_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        if (e != cudaSuccess) return from_cuda(e);
+        e = cudaGraphInstantiate(&p->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { p->gexec = nullptr; return from_cuda(e); }
+        p->gkey = key;
     }
+    p->prof.begin("graph", s);
+    e = cudaGraphLaunch(p->gexec, s);
+    p->prof.end(s);
+    return from_cuda(e);
+}
+
+// Alg. 1 over rotations for one pair (see cmif_align_rotations); enqueues on s.
+cmif_status align_core(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B, const uint8_t* M_B,
+                       const double* angles, int n_angles, double gamma, int top_k, void* topk_dev, double* mi_maps,
+                       cudaStream_t s) {
+    const Geom& g = plan->g;
+    const size_t RC = (size_t)g.R * g.C;
+    cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), s);
+    if (e != cudaSuccess) return from_cuda(e);
+    PeakRec* peaks = reinterpret_cast<PeakRec*>(plan->peaks);
+    for (int i = 0; i < n_angles; ++i) {
+        plan->prof.begin("warp_nn", s);
+        e = launch_warp_nn(B, M_B, g.HB, g.WB, angles[i], plan->wB, plan->wM, s);
+        plan->prof.end(s);
+        if (e != cudaSuccess) return from_cuda(e);
+        double* mi = mi_maps ? mi_maps + (size_t)i * RC : plan->mibuf;
+        const unsigned stages = (i == 0) ? STAGE_ALL : (STAGE_FWD_B | STAGE_PAIRS);
+        cmif_status cs = compute_map(plan, A, M_A, plan->wB, plan->wM, mi, plan->nbuf, nullptr, s, stages);
+        if (cs != CMIF_OK) return cs;
+        plan->prof.begin("peak", s);
+        e = launch_peak(mi, plan->nbuf, (long long)RC, plan->st, gamma, plan->parts, plan->nparts, g.HA, g.WA, g.C,
+                        i, peaks + i, s);
+        plan->prof.end(s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    plan->prof.begin("topk", s);
+    e = launch_topk(peaks, n_angles, top_k, topk_dev, s);
+    plan->prof.end(s);
+    return from_cuda(e);
+}
+
+}  // namespace
+
+struct cmif_batch_s {
+    int device = 0;
+    std::vector<cmif_pair_desc> descs;
+    std::vector<std::vector<double>> angles;
+    std::vector<cmif_plan> plans;  // per pair, all carved from mem
+    void* mem = nullptr;
+    size_t mem_bytes = 0;
+    DevStatus* total = nullptr;    // status of the whole batch
+    cmif_plan_s graph_holder;      // capture stream / graph of the batch
+    cudaStream_t last_stream = nullptr;
+    std::vector<unsigned char> gkey;
+};
+
+extern "C" {
+
+cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B,
+                                cmif_precision prec, unsigned flags) {
+    if (!out) return CMIF_ERR_INVALID_ARG;
+    *out = nullptr;
+    cmif_plan p = new (std::nothrow) cmif_plan_s();
+    if (!p) return CMIF_ERR_OOM;
+    cmif_status st = plan_init(p, H_A, W_A, H_B, W_B, K_A, K_B, prec, flags);
     if (st == CMIF_OK) {
-        p->nparts = 2 * p->num_sms;
-        const size_t o_tot = align_up(sizeof(DevStatus), 256);
-        const size_t o_parts = o_tot + align_up(sizeof(DevStatus), 256);
-        const size_t o_n = align_up(o_parts + (size_t)p->nparts * sizeof(PeakPart), 256);
-        const size_t o_mi = align_up(o_n + (size_t)g.R * g.C * sizeof(int32_t), 256);
-        const size_t o_wB = align_up(o_mi + (size_t)g.R * g.C * sizeof(double), 256);
-        const size_t o_wM = align_up(o_wB + (size_t)g.HB * g.WB * sizeof(int32_t), 256);
-        const size_t o_pk = align_up(o_wM + (size_t)g.HB * g.WB, 256);
-        const size_t bytes = o_pk + (size_t)kMaxAngles * sizeof(PeakRec);
-        e = cudaMalloc(&p->small, bytes);
-        if (e != cudaSuccess) { cudaGetLastError(); st = CMIF_ERR_OOM; }
+        const size_t bytes = plan_bytes(p);
+        cudaError_t e = cudaMalloc(&p->mem, bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); p->mem = nullptr; st = CMIF_ERR_OOM; }
         else {
-            char* sb = (char*)p->small;
-            p->st = (DevStatus*)sb;
-            p->st_total = (DevStatus*)(sb + o_tot);
-            p->parts = (PeakPart*)(sb + o_parts);
-            p->nbuf = (int32_t*)(sb + o_n);
-            p->mibuf = (double*)(sb + o_mi);
-            p->wB = (int32_t*)(sb + o_wB);
-            p->wM = (uint8_t*)(sb + o_wM);
-            p->peaks = sb + o_pk;
-            if (cudaMemset(p->st_total, 0, sizeof(DevStatus)) != cudaSuccess) st = CMIF_ERR_CUDA;
-            if (cudaMemset(p->st, 0, sizeof(DevStatus)) != cudaSuccess) st = CMIF_ERR_CUDA;
+            p->mem_bytes = bytes;
+            st = plan_carve(p, (char*)p->mem);
         }
     }
     if (st != CMIF_OK) {
@@ -324,7 +471,7 @@ cmif_status cmif_plan_destroy(cmif_plan plan) {
 
 cmif_status cmif_plan_workspace_bytes(cmif_plan plan, size_t* bytes) {
     if (!plan || !bytes) return CMIF_ERR_INVALID_ARG;
-    *bytes = plan->w32.bytes + plan->w64.bytes + plan->ws32.bytes;
+    *bytes = plan->mem_bytes;
     return CMIF_OK;
 }
 
@@ -338,20 +485,26 @@ cmif_status cmif_compute(cmif_plan plan, const int32_t* A, const uint8_t* M_A, c
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
     plan->prof.reset();
-    cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), s);
-    if (e != cudaSuccess) return from_cuda(e);
     int32_t* nm = n_map ? n_map : plan->nbuf;
-    cmif_status st = compute_map(plan, A, M_A, B, M_B, mi_map, nm, counts, s);
-    if (st != CMIF_OK) return st;
-    if (peak_dev) {
-        const Geom& g = plan->g;
-        plan->prof.begin("peak", s);
-        e = launch_peak(mi_map, nm, (long long)g.R * g.C, plan->st, gamma, plan->parts, plan->nparts, g.HA, g.WA,
-                        g.C, 0, peak_dev, s);
-        plan->prof.end(s);
+    std::vector<unsigned char> key;
+    key_add(key, 1);
+    key_add(key, A); key_add(key, M_A); key_add(key, B); key_add(key, M_B);
+    key_add(key, mi_map); key_add(key, nm); key_add(key, counts); key_add(key, gamma); key_add(key, peak_dev);
+    return run_graph(plan, s, key, [&](cudaStream_t cs) -> cmif_status {
+        cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), cs);
         if (e != cudaSuccess) return from_cuda(e);
-    }
-    return CMIF_OK;
+        cmif_status st = compute_map(plan, A, M_A, B, M_B, mi_map, nm, counts, cs);
+        if (st != CMIF_OK) return st;
+        if (peak_dev) {
+            const Geom& g = plan->g;
+            plan->prof.begin("peak", cs);
+            e = launch_peak(mi_map, nm, (long long)g.R * g.C, plan->st, gamma, plan->parts, plan->nparts, g.HA,
+                            g.WA, g.C, 0, peak_dev, cs);
+            plan->prof.end(cs);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        return CMIF_OK;
+    });
 }
 
 cmif_status cmif_compute_host(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
@@ -434,33 +587,143 @@ cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t
     for (int i = 0; i < n_angles; ++i)
         if (!std::isfinite(angles_rad_host[i])) return CMIF_ERR_INVALID_ARG;
     DeviceGuard dg(plan->device);
-    const Geom& g = plan->g;
-    const size_t RC = (size_t)g.R * g.C;
     cudaStream_t s = (cudaStream_t)stream;
     plan->last_stream = s;
     plan->prof.reset();
-    cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), s);
-    if (e != cudaSuccess) return from_cuda(e);
-    PeakRec* peaks = reinterpret_cast<PeakRec*>(plan->peaks);
-    for (int i = 0; i < n_angles; ++i) {
-        plan->prof.begin("warp_nn", s);
-        e = launch_warp_nn(B, M_B, g.HB, g.WB, angles_rad_host[i], plan->wB, plan->wM, s);
-        plan->prof.end(s);
-        if (e != cudaSuccess) return from_cuda(e);
-        double* mi = mi_maps ? mi_maps + (size_t)i * RC : plan->mibuf;
-        const unsigned stages = (i == 0) ? STAGE_ALL : (STAGE_FWD_B | STAGE_PAIRS);
-        cmif_status cs = compute_map(plan, A, M_A, plan->wB, plan->wM, mi, plan->nbuf, nullptr, s, stages);
-        if (cs != CMIF_OK) return cs;
-        plan->prof.begin("peak", s);
-        e = launch_peak(mi, plan->nbuf, (long long)RC, plan->st, gamma, plan->parts, plan->nparts, g.HA, g.WA, g.C,
-                        i, peaks + i, s);
-        plan->prof.end(s);
-        if (e != cudaSuccess) return from_cuda(e);
+    std::vector<unsigned char> key;
+    key_add(key, 2);
+    key_add(key, A); key_add(key, M_A); key_add(key, B); key_add(key, M_B);
+    key_add(key, gamma); key_add(key, top_k); key_add(key, topk_dev); key_add(key, mi_maps); key_add(key, n_angles);
+    for (int i = 0; i < n_angles; ++i) key_add(key, angles_rad_host[i]);
+    return run_graph(plan, s, key, [&](cudaStream_t cs) -> cmif_status {
+        return align_core(plan, A, M_A, B, M_B, angles_rad_host, n_angles, gamma, top_k, topk_dev, mi_maps, cs);
+    });
+}
+
+cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc* descs, cmif_precision prec,
+                              unsigned flags) {
+    if (!out) return CMIF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_pairs < 1 || !descs || (flags & ~CMIF_FLAG_GRAPH)) return CMIF_ERR_INVALID_ARG;
+    for (int i = 0; i < n_pairs; ++i) {
+        const cmif_pair_desc& d = descs[i];
+        if (!d.A || !d.B || d.n_angles < 0 || d.n_angles > kMaxAngles || (d.n_angles > 0 && !d.angles_rad))
+            return CMIF_ERR_INVALID_ARG;
+        if (!(d.gamma >= 0.0 && d.gamma <= 1.0)) return CMIF_ERR_INVALID_ARG;
+        for (int k = 0; k < d.n_angles; ++k)
+            if (!std::isfinite(d.angles_rad[k])) return CMIF_ERR_INVALID_ARG;
     }
-    plan->prof.begin("topk", s);
-    e = launch_topk(peaks, n_angles, top_k, topk_dev, s);
-    plan->prof.end(s);
-    return from_cuda(e);
+    cmif_batch b = new (std::nothrow) cmif_batch_s();
+    if (!b) return CMIF_ERR_OOM;
+    auto fail = [&](cmif_status st) {
+        for (cmif_plan p : b->plans) { p->mem = nullptr; free_plan(p); }
+        if (b->mem) cudaFree(b->mem);
+        delete b;
+        return st;
+    };
+    if (cudaGetDevice(&b->device) != cudaSuccess) return fail(CMIF_ERR_CUDA);
+    b->descs.assign(descs, descs + n_pairs);
+    size_t max_bytes = 0;
+    for (int i = 0; i < n_pairs; ++i) {
+        const cmif_pair_desc& d = descs[i];
+        b->angles.emplace_back(d.angles_rad, d.angles_rad + d.n_angles);
+        cmif_plan p = new (std::nothrow) cmif_plan_s();
+        if (!p) return fail(CMIF_ERR_OOM);
+        b->plans.push_back(p);
+        cmif_status st = plan_init(p, d.H_A, d.W_A, d.H_B, d.W_B, d.K_A, d.K_B, prec, 0u);
+        if (st != CMIF_OK) return fail(st);
+        max_bytes = std::max(max_bytes, plan_bytes(p));
+    }
+    // pairs run one after another on one stream, so one workspace serves them all
+    const size_t tot_off = align_up(max_bytes, 256);
+    if (cudaMalloc(&b->mem, tot_off + 256) != cudaSuccess) { cudaGetLastError(); b->mem = nullptr; return fail(CMIF_ERR_OOM); }
+    b->mem_bytes = tot_off + 256;
+    for (cmif_plan p : b->plans) {
+        cmif_status st = plan_carve(p, (char*)b->mem);
+        if (st != CMIF_OK) return fail(st);
+    }
+    b->total = (DevStatus*)((char*)b->mem + tot_off);
+    if (cudaMemset(b->total, 0, sizeof(DevStatus)) != cudaSuccess) return fail(CMIF_ERR_CUDA);
+    b->graph_holder.use_graph = (flags & CMIF_FLAG_GRAPH) != 0;
+    b->graph_holder.device = b->device;
+    *out = b;
+    return CMIF_OK;
+}
+
+cmif_status cmif_compute_batch(cmif_batch batch, cmif_peak* results_dev, int32_t* status_dev, void* stream) {
+    if (!batch || !results_dev) return CMIF_ERR_INVALID_ARG;
+    DeviceGuard dg(batch->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    batch->last_stream = s;
+    std::vector<unsigned char> key;
+    key_add(key, 3);
+    key_add(key, results_dev);
+    key_add(key, status_dev);
+    return run_graph(&batch->graph_holder, s, key, [&](cudaStream_t cs) -> cmif_status {
+        cudaError_t e = cudaMemsetAsync(batch->total, 0, sizeof(DevStatus), cs);
+        if (e != cudaSuccess) return from_cuda(e);
+        for (size_t i = 0; i < batch->plans.size(); ++i) {
+            cmif_plan p = batch->plans[i];
+            const cmif_pair_desc& d = batch->descs[i];
+            cmif_status st;
+            if (d.n_angles == 0) {
+                e = cudaMemsetAsync(p->st_total, 0, sizeof(DevStatus), cs);
+                if (e != cudaSuccess) return from_cuda(e);
+                st = compute_map(p, d.A, d.M_A, d.B, d.M_B, p->mibuf, p->nbuf, nullptr, cs);
+                if (st != CMIF_OK) return st;
+                e = launch_peak(p->mibuf, p->nbuf, (long long)p->g.R * p->g.C, p->st, d.gamma, p->parts, p->nparts,
+                                p->g.HA, p->g.WA, p->g.C, 0, results_dev + i, cs);
+                if (e != cudaSuccess) return from_cuda(e);
+            } else {
+                st = align_core(p, d.A, d.M_A, d.B, d.M_B, batch->angles[i].data(), d.n_angles, d.gamma, 1,
+                                results_dev + i, nullptr, cs);
+                if (st != CMIF_OK) return st;
+            }
+            if (status_dev) {
+                e = launch_status_code(p->st_total, status_dev + i, cs);
+                if (e != cudaSuccess) return from_cuda(e);
+            }
+            e = launch_merge_status(p->st_total, batch->total, 0, cs);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        return CMIF_OK;
+    });
+}
+
+cmif_status cmif_batch_get_status(cmif_batch batch, cmif_status* device_side, double* max_residual, int* escalations) {
+    if (!batch) return CMIF_ERR_INVALID_ARG;
+    DeviceGuard dg(batch->device);
+    DevStatus h{};
+    cudaError_t e = cudaStreamSynchronize(batch->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, batch->total, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (device_side)
+        *device_side = (h.flags & STATUS_LABEL_RANGE) ? CMIF_ERR_LABEL_RANGE
+                     : (h.flags & STATUS_PRECISION)   ? CMIF_ERR_PRECISION
+                     : (h.flags & STATUS_TIMEOUT)     ? CMIF_ERR_TIMEOUT
+                                                      : CMIF_OK;
+    if (max_residual) {
+        float f;
+        std::memcpy(&f, &h.res_bits[0], sizeof(f));
+        *max_residual = f;
+    }
+    if (escalations) *escalations = h.escalations;
+    return CMIF_OK;
+}
+
+cmif_status cmif_batch_destroy(cmif_batch batch) {
+    if (!batch) return CMIF_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(batch->device);
+    cudaDeviceSynchronize();
+    for (cmif_plan p : batch->plans) { p->mem = nullptr; free_plan(p); }
+    if (batch->mem) cudaFree(batch->mem);
+    if (batch->graph_holder.gexec) { cudaGraphExecDestroy(batch->graph_holder.gexec); batch->graph_holder.gexec = nullptr; }
+    if (batch->graph_holder.cap_stream) { cudaStreamDestroy(batch->graph_holder.cap_stream); batch->graph_holder.cap_stream = nullptr; }
+    if (prev >= 0) cudaSetDevice(prev);
+    delete batch;
+    return CMIF_OK;
 }
 
 cmif_status cmif_plan_set_profiling(cmif_plan plan, int enable) {

@@ -160,6 +160,19 @@ cudaError_t launch_topk(const void* peaks, int n, int k, void* out, cudaStream_t
     return cudaGetLastError();
 }
 
+// A status word as a cmif_status code (0 OK, 2 LABEL_RANGE, 5 PRECISION, 6 TIMEOUT).
+__global__ void k_status_code_of(const DevStatus* st, int32_t* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const unsigned f = st->flags;
+        *out = (f & STATUS_LABEL_RANGE) ? 2 : (f & STATUS_PRECISION) ? 5 : (f & STATUS_TIMEOUT) ? 6 : 0;
+    }
+}
+
+cudaError_t launch_status_code(const DevStatus* st, int32_t* out, cudaStream_t s) {
+    k_status_code_of<<<1, 32, 0, s>>>(st, out);
+    return cudaGetLastError();
+}
+
 // AUTO: escalate to the FP64 pass when the FP32 residual reached the guard.
 __global__ void k_check_escalate(DevStatus* st) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {

@@ -23,6 +23,7 @@ cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_defau
 cudaError_t launch_warp_nn(const int32_t* B, const uint8_t* MB, int H, int W, double theta, int32_t* Bo, uint8_t* Mo,
                            cudaStream_t s);
 cudaError_t launch_merge_status(const DevStatus* m, DevStatus* tot, int slot_default, cudaStream_t s);
+cudaError_t launch_status_code(const DevStatus* st, int32_t* out, cudaStream_t s);
 cudaError_t launch_topk(const void* peaks, int n, int k, void* out, cudaStream_t s);
 cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td, Tw<df32>* ts);
 // Host copy of the FP32 twiddle tables (interleaved re, im) and the entry offsets
