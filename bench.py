@@ -41,8 +41,8 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # by the units processed (2047/511 output rows; 1025/257 kx columns).  Set to
 # None when a kernel changes after its capture.
 NCU_TRAFFIC = {
-    "pair_rows_f32": (1.077061e9 + 19.25376e6) * 2047 / 511,
-    "pair_cols_f32": (156.884992e6 + 1.144764e9) * 1025 / 257,
+    "pair_rows_f32": None,
+    "pair_cols_f32": None,
 }
 
 
@@ -213,6 +213,74 @@ def run_profile_shape(args):
                       "workspace_gb": plan.workspace_bytes() / 1e9}), flush=True)
 
 
+def run_secondary(args):
+    """The other configurations as bench lines of the same metric (device-timed, graph replay)."""
+    import torch
+    import paper_2106_14699_gb300 as cm
+    import synth
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    d = lambda x: None if x is None else torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    if args.workload in ("single256", "plain64"):
+        cid = 2 if args.workload == "single256" else 1
+        cfg = synth.make_config(cid)
+        H, W = cfg["A"].shape
+        K = cfg["K_A"]
+        prec = cm.FP32 if cid == 2 else cm.FP64
+        plan = cm.Plan(H, W, H, W, K, K, prec, graph=True)
+        R, C = 2 * H - 1, 2 * W - 1
+        mi = torch.empty((R, C), dtype=torch.float64, device=dev)
+        n = torch.empty((R, C), dtype=torch.int32, device=dev)
+        pk = torch.empty(24, dtype=torch.uint8, device=dev)
+        ins = [d(cfg[k]) for k in ("A", "M_A", "B", "M_B")]
+        step = lambda: plan.compute(ins[0], ins[1], ins[2], ins[3], mi, n, None, 0.5, pk)
+        units, name = R * C, cfg["name"] + (" FP32" if prec == cm.FP32 else " FP64")
+    elif args.workload == "rotation":
+        cfg = synth.make_config(4)
+        H, W = cfg["A"].shape
+        plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True)
+        top = torch.empty(24 * 5, dtype=torch.uint8, device=dev)
+        A, B = d(cfg["A"]), d(cfg["B"])
+        step = lambda: plan.align_rotations(A, None, B, None, cfg["angles"], 0.5, 5, top)
+        units, name = (2 * H - 1) * (2 * W - 1) * len(cfg["angles"]), cfg["name"] + " FP32"
+    else:
+        cfg = synth.make_config(5)
+        pairs = [dict(A=d(p["A"]), M_A=d(p["M_A"]), B=d(p["B"]), M_B=d(p["M_B"]), K_A=p["K_A"], K_B=p["K_B"],
+                      angles=p["angles"], gamma=0.5) for p in cfg["pairs"]]
+        plan = cm.Batch(pairs, cm.FP32, graph=True)
+        res = torch.empty(24 * len(pairs), dtype=torch.uint8, device=dev)
+        stat = torch.empty(len(pairs), dtype=torch.int32, device=dev)
+        step = lambda: plan.run(res, stat)
+        units = sum((p["A"].shape[0] + p["B"].shape[0] - 1) * (p["A"].shape[1] + p["B"].shape[1] - 1) * len(p["angles"])
+                    for p in cfg["pairs"])
+        name = cfg["name"] + " FP32"
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    clk = ClockSampler(0)
+    clk.start()
+    stream = torch.cuda.current_stream()
+    for i in range(steps):
+        flush.zero_()
+        e0[i].record(stream)
+        step()
+        e1[i].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / steps
+    st = plan.status()
+    print(json.dumps({"metric": METRIC.replace("at 1024², K=16", "on " + name), "value": units / (ms * 1e-3),
+                      "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "FP32" in name else "f64",
+                      "data": "synthetic", "config": {"workload": name, "units_per_step": units,
+                                                       "l2": "flushed between steps (256 MB write)"},
+                      "clocks": clocks, "device_status": {"status": st[0], "max_residual": st[1], "escalations": st[2]}}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,6 +289,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="single1024",
+                    choices=["single1024", "rotation", "batch", "single256", "plain64"],
+                    help="single1024 (default, the headline): config 3; rotation: config 4 (512^2, 64 angles); "
+                         "batch: config 5 (128 uneven pairs x 4 angles); single256 / plain64: configs 2 / 1")
     ap.add_argument("--profile-shape", default=None,
                     help="HxW: run only the device step loop on a planted pair of this size (for ncu captures)")
     args = ap.parse_args()
@@ -235,6 +307,9 @@ def main():
         return
     if args.profile_shape:
         run_profile_shape(args)
+        return
+    if args.workload != "single1024":
+        run_secondary(args)
         return
 
     import torch

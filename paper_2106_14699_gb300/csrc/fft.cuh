@@ -155,30 +155,10 @@ __host__ __device__ constexpr int grp_scratch_bytes() {
 //   twq      : Tw::sq for this M;  twn : Tw::n for N (used when R > 1)
 // Result: v[brev(k2, M)] = X[R*(j + M*k2) + r], k2 in [0, M).
 // Every lane of every warp taking part must call this (it uses __syncwarp).
-template <int M, int R, int DIR, typename T, typename Load>
-__device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
-                                         const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
-    constexpr int NQ = M * M;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-        const int m = j + M * i;
-        if constexpr (R == 1) {
-            v[i] = load(m);
-        } else {
-            // radix-R decimation in frequency: y_r[m] = w_N^{m r} sum_s x[m + s NQ] w_R^{s r}
-            cpx<T> acc = load(m);
-#pragma unroll
-            for (int s = 1; s < R; ++s) {
-                cpx<T> x = load(m + s * NQ);
-                if constexpr (R == 2) {
-                    acc = (r & 1) ? acc - x : acc + x;
-                } else {
-                    acc = acc + cmul(x, twl<DIR>(twn, ((s * r) % R) * NQ));
-                }
-            }
-            v[i] = (r == 0) ? acc : cmul(acc, twl<DIR>(twn, m * r));
-        }
-    }
+// The four-step core on values already in registers: v[i] = y[j + M*i] for the
+// group's M*M-point sequence y.  Result: v[brev(k2, M)] = Y[j + M*k2].
+template <int M, int DIR, typename T>
+__device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, const cpx<T>* __restrict__ twq) {
     dft_reg<M, DIR>(v);  // v[brev(k1)] = A[j][k1]
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) v[brev(k1, M)] = cmul(v[brev(k1, M)], twl<DIR>(twq, k1 * M + j));
@@ -208,6 +188,33 @@ __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& lo
         __syncwarp();
     }
     dft_reg<M, DIR>(v);  // v[brev(k2)] = X_r[j + M k2]
+}
+
+template <int M, int R, int DIR, typename T, typename Load>
+__device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
+                                         const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
+    constexpr int NQ = M * M;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const int m = j + M * i;
+        if constexpr (R == 1) {
+            v[i] = load(m);
+        } else {
+            // radix-R decimation in frequency: y_r[m] = w_N^{m r} sum_s x[m + s NQ] w_R^{s r}
+            cpx<T> acc = load(m);
+#pragma unroll
+            for (int s = 1; s < R; ++s) {
+                cpx<T> x = load(m + s * NQ);
+                if constexpr (R == 2) {
+                    acc = (r & 1) ? acc - x : acc + x;
+                } else {
+                    acc = acc + cmul(x, twl<DIR>(twn, ((s * r) % R) * NQ));
+                }
+            }
+            v[i] = (r == 0) ? acc : cmul(acc, twl<DIR>(twn, m * r));
+        }
+    }
+    team_fft_core<M, DIR>(v, j, sm, twq);
 }
 
 }  // namespace cmif

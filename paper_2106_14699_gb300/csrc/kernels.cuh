@@ -29,16 +29,20 @@ namespace cmif {
 // order independent and cheap (integer adds).  log2 of the mantissa comes
 // from the MUFU lg2 approximation.
 __device__ __forceinline__ long long clog2c_fixed(float c) {
-    if (c < 1.5f) return 0;  // 0 log 0 = 0 (Sec. 3.2) and 1 log 1 = 0
     const int ci = __float_as_int(c + 8388608.0f) - 0x4B000000;
     const int bits = __float_as_int(c);
-    const int e = (bits >> 23) - 127;
     const float m = __int_as_float((bits & 0x7FFFFF) | 0x3F800000);
     const float lm = __log2f(m);
-    const int lmi = __float_as_int(fmaf(lm, (float)(1 << kFixBits), 12582912.0f)) - 0x4B400000;
-    const int L = (e << kFixBits) + lmi;
+    // (e << F) + round(lm * 2^F), e = exponent of c, with the constants folded
+    int L = ((bits >> 23) << kFixBits) + __float_as_int(fmaf(lm, (float)(1 << kFixBits), 12582912.0f)) -
+            (0x4B400000 + (127 << kFixBits));
+    L = bits <= 0x3F800000 ? 0 : L;  // c in {0, 1}: c log c = 0 (Sec. 3.2: 0 log 0 = 0)
     return (long long)ci * (long long)L;
 }
+
+// Nearest integer of |v| < 2^22 with two FP32 adds (the 1.5 * 2^23 shift
+// leaves no fraction bits).
+__device__ __forceinline__ float round_fp32(float v) { return (v + 12582912.0f) - 12582912.0f; }
 
 // MI(chi) = (S + N log2 N) / N, where S = sum_joint c log2 c - sum_A - sum_B and
 // every c log2 c term (N log2 N included) comes from clog2c_fixed, so that MI is
@@ -164,7 +168,7 @@ struct ColCfg {
 template <typename T, int P>
 __global__ void __launch_bounds__(ColCfg<T, P>::THREADS)
 k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cpx<T>* __restrict__ F, Tw<T> tw,
-           const DevStatus* __restrict__ st, int conditional) {
+           const DevStatus* __restrict__ st, int conditional, T out_scale) {
     using C = ColCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R;
@@ -183,66 +187,151 @@ k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cp
     if (!active) return;
     cpx<T>* out = F + ((size_t)plane * Qh + kx) * P;
 #pragma unroll
-    for (int k2 = 0; k2 < M; ++k2) out[R * (j + M * k2) + r] = v[brev(k2, M)];
+    for (int k2 = 0; k2 < M; ++k2) {
+        const cpx<T> z = v[brev(k2, M)];
+        out[R * (j + M * k2) + r] = {z.x * out_scale, z.y * out_scale};
+    }
+}
+
+// Read-only loads of complex values through the non-coherent path.
+__device__ __forceinline__ cpx<float> __ldg(const cpx<float>* p) {
+    const float2 v = ::__ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cpx<double> __ldg(const cpx<double>* p) {
+    const double2 v = ::__ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cpx<df32> __ldg(const cpx<df32>* p) {
+    const float4 v = ::__ldg(reinterpret_cast<const float4*>(p));
+    return {df32(v.x, v.y), df32(v.z, v.w)};
+}
+
+// ---------------------------------------------------------------------------
+// Copy n twiddles from global to shared memory (whole block).
+template <typename T>
+__device__ __forceinline__ void stage_table(cpx<T>* dst, const cpx<T>* __restrict__ src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
 // ---------------------------------------------------------------------------
 // Pair product + inverse column transform.  Block = (pair, kx block): pairs
 // vary fastest so that the blocks resident at one time read the same few
 // spectrum columns (L2 reuse).  The transformed columns are transposed
-// through shared memory in two halves of rows and written as row chunks of
-// TPB adjacent kx (full 32-byte sectors).
+// through shared memory, one half of the rows at a time, into per-group
+// sub-tiles whose column slot is XOR-swizzled by the row (conflict-free
+// writes), and leave as row chunks of TPB adjacent kx.
 template <typename T, int P>
 struct PairColsCfg {
     using G = TeamGeom<T, P>;
-    static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
+    static constexpr int M = G::M, R = G::R, TEAM = G::TEAM, NQ = M * M;
     static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
     static constexpr int THREADS = TPB * TEAM;
-    static constexpr int TS = TPB + 1;  // tile row stride (complex), padded
-    static constexpr size_t TILE = (size_t)(P / 2) * TS * sizeof(cpx<T>);
+    static constexpr int SWZ = TPB >= 16 ? 0 : (TPB == 8 ? 1 : (TPB == 4 ? 2 : 3));
+    // one buffer per block: the teams' group-transform exchange, then the P x TPB output tile
+    static constexpr size_t XBUF = (size_t)TPB * P * sizeof(cpx<T>);
     static constexpr size_t FFT = (size_t)TPB * G::SCRATCH;
-    static constexpr size_t SMEM = TILE > FFT ? TILE : FFT;
+    static constexpr size_t MAIN = (XBUF > FFT ? XBUF : FFT);
+    static constexpr int TW_N = R > 1 ? P : 0;  // combine twiddles W_P^k
+    static constexpr size_t SMEM = MAIN + (size_t)(NQ + TW_N) * sizeof(cpx<T>);
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;
 };
 
+// Pair product + inverse column transform of length P = R*M*M.  Block = (pair,
+// kx block); pairs vary fastest so that the blocks resident at one time read
+// the same few spectrum columns (L2 reuse).  Decimation in time across the R
+// groups of a team: group r transforms the M*M samples ky = R*m + r (every
+// input is loaded and multiplied once per team), the groups exchange their
+// sub-transforms through shared memory, and group r forms the outputs
+// [r*M*M, (r+1)*M*M) by the radix-R butterfly.  The exchange buffer then
+// serves as a P x TPB tile (column slots XOR-swizzled by row, conflict-free
+// writes) whose rows leave as chunks of TPB adjacent kx.
 template <typename T, int P>
 __global__ void __launch_bounds__(PairColsCfg<T, P>::THREADS, PairColsCfg<T, P>::MIN_BLOCKS)
 k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KB, int Qh, int HA, int HB,
-            T scale, int Rout, int Qs, cpx<T>* __restrict__ Y, Tw<T> tw,
-            const DevStatus* __restrict__ st, int conditional) {
+            int Rout, int Qs, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st, int conditional) {
     using C = PairColsCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
-    constexpr int M = C::M, R = C::R, TPB = C::TPB, TS = C::TS;
+    constexpr int M = C::M, R = C::R, TPB = C::TPB, NQ = C::NQ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* tile = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* tw_sq = reinterpret_cast<cpx<T>*>(smem_raw + C::MAIN);
+    cpx<T>* tw_n = tw_sq + NQ;
+    stage_table(tw_sq, tw.sq[ilog2c(M)], NQ);
+    if (R > 1) stage_table(tw_n, tw.n[ilog2c(P)], C::TW_N);
+    __syncthreads();
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
     const int pair = blockIdx.x, kx0 = blockIdx.y * TPB, kx = kx0 + team;
     const int a = pair / KB, b = pair % KB;
     const bool active = kx < Qh;
     const cpx<T>* fa = FA + ((size_t)a * Qh + (active ? kx : 0)) * P;
     const cpx<T>* fb = FB + ((size_t)b * Qh + (active ? kx : 0)) * P;
-    auto load = [&](int ky) -> cpx<T> {
-        if (!active) return {T(0), T(0)};
-        const cpx<T> z = cmulc(fb[ky], fa[ky]);  // conj(F_a) F_b
-        return {z.x * scale, z.y * scale};
-    };
+    // group r: the samples ky = R*m + r, m = j + M*i.  conj(F_a) F_b, F_b carrying the
+    // 1/(P Q) of the inverse.  All F loads are issued first (straight into the
+    // transform registers), then the F_b loads with the products: two waves of
+    // M independent loads per lane.
     cpx<T> v[M];
-    team_fft<M, R, +1>(v, r, j, load, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(),
-                       tw.sq[ilog2c(M)], tw.n[ilog2c(P)]);
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = __ldg(reinterpret_cast<const cpx<T>*>(fa) + R * (j + M * i) + r);
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = cmulc(__ldg(reinterpret_cast<const cpx<T>*>(fb) + R * (j + M * i) + r), v[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = {T(0), T(0)};
+    }
+    team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
+    cpx<T>* tx = xbuf + (size_t)team * P;  // this team's R sub-transforms
+    if constexpr (R > 1) {
+        __syncthreads();  // every group is done with its transpose scratch (aliases xbuf)
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) tx[r * NQ + j + M * k2] = v[brev(k2, M)];
+        __syncthreads();
+        // X[k + r NQ] = sum_s W_P^{s (k + r NQ)} E_s[k]   (inverse direction)
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) {
+            const int k = j + M * k2;
+            cpx<T> acc = tx[k];
+#pragma unroll
+            for (int s2 = 1; s2 < R; ++s2)
+                acc = acc + cmul(tx[s2 * NQ + k], twl<+1>(tw_n, (s2 * (k + r * NQ)) & (P - 1)));
+            v[brev(k2, M)] = acc;
+        }
+    }
+    __syncthreads();  // exchange reads done: the buffer becomes the tile
+    // row = r*NQ + j + M*k2; tile slot (row, team) swizzled by row
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) {
+        const int row = r * NQ + j + M * k2;
+        xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = v[brev(k2, M)];
+    }
+    __syncthreads();
     cpx<T>* yp = Y + (size_t)pair * Rout * Qs;
+    for (int row = threadIdx.x; row < P; row += C::THREADS) {
+        const int orow = circ_to_out(row, P, HA, HB - 1);
+        if (orow < 0) continue;
+        const int sw = (row >> C::SWZ) & (TPB - 1);
+        const cpx<T>* src = xbuf + (size_t)row * TPB;
+        cpx<T>* dst = yp + (size_t)orow * Qs + kx0;
+        if constexpr (sizeof(T) == 4 && TPB == 4) {
+            // one 32-byte row chunk: two 16-byte loads, undo the swizzle, two 16-byte stores
+            // (kx0 + 4 <= Qs always: Qs is a multiple of 4)
+            const float4 p0 = reinterpret_cast<const float4*>(src)[0];
+            const float4 p1 = reinterpret_cast<const float4*>(src)[1];
+            const float2 ph[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
+                                  make_float2(p1.z, p1.w)};
+            float2 lg[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        __syncthreads();
+            for (int c = 0; c < 4; ++c) {
+                const int pc = c ^ sw;
+                lg[c] = pc == 0 ? ph[0] : pc == 1 ? ph[1] : pc == 2 ? ph[2] : ph[3];
+            }
+            reinterpret_cast<float4*>(dst)[0] = make_float4(lg[0].x, lg[0].y, lg[1].x, lg[1].y);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(lg[2].x, lg[2].y, lg[3].x, lg[3].y);
+        } else {
 #pragma unroll
-        for (int k2 = h * (M / 2); k2 < (h + 1) * (M / 2); ++k2)
-            tile[(size_t)(R * (j + M * k2) + r - h * (P / 2)) * TS + team] = v[brev(k2, M)];
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < (P / 2) * TPB; idx += C::THREADS) {
-            const int rl = idx / TPB, t = idx - rl * TPB, k = kx0 + t;
-            if (k >= Qh) continue;
-            const int orow = circ_to_out(rl + h * (P / 2), P, HA, HB - 1);
-            if (orow < 0) continue;
-            yp[(size_t)orow * Qs + k] = tile[(size_t)rl * TS + t];
+            for (int c = 0; c < TPB; ++c)
+                if (kx0 + c < Qs) dst[c] = src[c ^ sw];
         }
     }
 }

@@ -42,13 +42,13 @@ static cudaError_t launch_fwd_rows(const int32_t* X, const uint8_t* MX, int H, i
 
 template <typename T, int P>
 static cudaError_t launch_fwd_cols(const cpx<T>* T1, int H, int K, int Qh, int Qs, cpx<T>* F, const Tw<T>& tw,
-                                   const DevStatus* st, int conditional, cudaStream_t s) {
+                                   const DevStatus* st, int conditional, T out_scale, cudaStream_t s) {
     using C = ColCfg<T, P>;
     auto kern = k_fwd_cols<T, P>;
     cudaError_t e = ensure_smem(kern, C::SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((Qh + C::TPB - 1) / C::TPB, K);
-    kern<<<grid, C::THREADS, C::SMEM, s>>>(T1, H, K, Qh, Qs, F, tw, st, conditional);
+    kern<<<grid, C::THREADS, C::SMEM, s>>>(T1, H, K, Qh, Qs, F, tw, st, conditional, out_scale);
     return cudaGetLastError();
 }
 
@@ -60,8 +60,7 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
     cudaError_t e = ensure_smem(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(g.KA * g.KB, (g.Qh + C::TPB - 1) / C::TPB);
-    const T scale = T(1.0 / ((double)g.P * (double)g.Q));  // exact: P*Q is a power of two
-    kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KB, g.Qh, g.HA, g.HB, scale, g.R, g.Qs, a.Y, a.tw, a.st,
+    kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, a.Y, a.tw, a.st,
                                         a.conditional);
     return cudaGetLastError();
 }
@@ -116,7 +115,7 @@ cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
         } if (e != cudaSuccess) return e);
         CMIF_SIZE_SWITCH(g.P, {
             ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : split ? "fwd_cols_A_s32" : "fwd_cols_A_f64", s);
-            e = (launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional, s));
+            e = (launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional, T(1), s));
         } if (e != cudaSuccess) return e);
     }
     if (stg & STAGE_FWD_B) {
@@ -126,7 +125,9 @@ cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
         } if (e != cudaSuccess) return e);
         CMIF_SIZE_SWITCH(g.P, {
             ProfScope ps(a.prof, f32 ? "fwd_cols_B_f32" : split ? "fwd_cols_B_s32" : "fwd_cols_B_f64", s);
-            e = (launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional, s));
+            // B's spectra carry the 1/(P Q) of the unnormalised inverse transform (a power of two: exact)
+            e = (launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional,
+                                        T(1.0 / ((double)g.P * (double)g.Q)), s));
         } if (e != cudaSuccess) return e);
     }
     if (stg & STAGE_PAIRS) {

@@ -127,7 +127,10 @@ struct RowTmCfg {
     static constexpr size_t OFF_STAGE = (size_t)NT * REGION;
     static constexpr size_t OFF_BAR = OFF_STAGE + (size_t)NT * STAGE_BYTES;
     static constexpr size_t OFF_HOLD = OFF_BAR + NT * 8;
-    static constexpr size_t SMEM = OFF_HOLD + 16;
+    static constexpr int NQ = M * M;
+    static constexpr int TW_PRE = R > 1 ? (R - 1) * NQ + 1 : 0;
+    static constexpr size_t OFF_TW = OFF_HOLD + 16;                   // twiddles staged in shared memory:
+    static constexpr size_t SMEM = OFF_TW + (size_t)(NQ + L + TW_PRE) * 8;  // four-step, C2R, pre-step
     static_assert(TEAM == 32, "one warp per transform");
     static_assert(UH >= 1 && QH % THREADS == 0, "whole positions per thread");
     static_assert(REGION >= QH * 4, "scratch holds one pass");
@@ -157,7 +160,12 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
 
     const int KA = g.KA, KB = g.KB, npairs = KA * KB, Rout = g.R, Cout = g.C, Qs = g.Qs;
     const size_t RC = (size_t)Rout * Cout;
-    const cpx<float>* twq_c2r = tw.n[ilog2c(Q)];
+    cpx<float>* tw_sq = reinterpret_cast<cpx<float>*>(smem_raw + C::OFF_TW);
+    cpx<float>* twq_c2r = tw_sq + C::NQ;
+    cpx<float>* tw_pre = twq_c2r + L;
+    stage_table(tw_sq, tw.sq[ilog2c(M)], C::NQ);
+    stage_table(twq_c2r, tw.n[ilog2c(Q)], L);
+    if (R > 1) stage_table(tw_pre, tw.n[ilog2c(L)], C::TW_PRE);
 
     if (tid == 0) s_abort = 0;
     if (lane == 0) mbar_init(bar, 1);
@@ -225,8 +233,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 return {e.x - o.y, e.y + o.x};
             };
             cpx<float> v[M];
-            team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw.sq[ilog2c(M)],
-                               tw.n[ilog2c(L)]);
+            team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw_sq, tw_pre);
             // the staging buffer is free again: prefetch this team's next active item
             // (the next round of this row, else round 0 of its next row)
             __syncwarp();
@@ -237,7 +244,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
             }
 #pragma unroll
             for (int k = 0; k < M; ++k) {
-                const float cr = rintf(v[k].x), ci = rintf(v[k].y);
+                const float cr = round_fp32(v[k].x), ci = round_fp32(v[k].y);
                 res_max = fmaxf(res_max, fmaxf(fabsf(v[k].x - cr), fabsf(v[k].y - ci)));
                 v[k].x = cr;
                 v[k].y = ci;
