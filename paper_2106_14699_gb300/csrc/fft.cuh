@@ -162,7 +162,29 @@ __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, c
     dft_reg<M, DIR>(v);  // v[brev(k1)] = A[j][k1]
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) v[brev(k1, M)] = cmul(v[brev(k1, M)], twl<DIR>(twq, k1 * M + j));
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && M == 32) {
+        // Rows of 32 floats in 8 blocks of 4; element (row, col) sits in block
+        // (col/4) ^ (row % 8).  Column writes (one float per lane) are a
+        // permutation of the row's 32 banks; row reads take 16-byte loads and the
+        // 8 lanes of each 16-byte phase hit 8 different blocks: conflict-free.
+        float* sf = reinterpret_cast<float*>(sm);
+        const int jb = j >> 2, jl = j & 3;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            __syncwarp();
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1)
+                sf[k1 * M + (((jb ^ k1) & 7) << 2) + jl] = half ? v[brev(k1, M)].y : v[brev(k1, M)].x;
+            __syncwarp();
+#pragma unroll
+            for (int b4 = 0; b4 < 8; ++b4) {
+                const float4 q = *reinterpret_cast<const float4*>(sf + j * M + (((b4 ^ j) & 7) << 2));
+                if (half) { v[4 * b4].y = q.x; v[4 * b4 + 1].y = q.y; v[4 * b4 + 2].y = q.z; v[4 * b4 + 3].y = q.w; }
+                else      { v[4 * b4].x = q.x; v[4 * b4 + 1].x = q.y; v[4 * b4 + 2].x = q.z; v[4 * b4 + 3].x = q.w; }
+            }
+        }
+        __syncwarp();
+    } else if constexpr (sizeof(T) == 4) {
         float* sf = reinterpret_cast<float*>(sm);
         __syncwarp();
 #pragma unroll
