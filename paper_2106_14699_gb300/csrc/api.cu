@@ -110,6 +110,7 @@ cmif_status choose_rows(cmif_plan p, Workspace<T>& w) {
     if (bps < 1) return CMIF_ERR_UNSUPPORTED;
     w.rows_grid = std::min(g.R, bps * p->num_sms);
     w.args.rows_grid = w.rows_grid;
+    w.args.num_sms = p->num_sms;
     w.args.cb_smem = w.cb_smem;
     return CMIF_OK;
 }

@@ -185,11 +185,13 @@ k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cp
     team_fft<M, R, -1>(v, r, j, load, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(),
                        tw.sq[ilog2c(M)], tw.n[ilog2c(P)]);
     if (!active) return;
+    // Column ky is stored at slot (ky % R) * M*M + ky / R: the samples that one
+    // group of the pair-product transform (same P, same R) takes are contiguous.
     cpx<T>* out = F + ((size_t)plane * Qh + kx) * P;
 #pragma unroll
     for (int k2 = 0; k2 < M; ++k2) {
         const cpx<T> z = v[brev(k2, M)];
-        out[R * (j + M * k2) + r] = {z.x * out_scale, z.y * out_scale};
+        out[r * (M * M) + j + M * k2] = {z.x * out_scale, z.y * out_scale};
     }
 }
 
@@ -237,22 +239,27 @@ struct PairColsCfg {
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;
 };
 
-// Pair product + inverse column transform of length P = R*M*M.  Block = (pair,
-// kx block); pairs vary fastest so that the blocks resident at one time read
-// the same few spectrum columns (L2 reuse).  Decimation in time across the R
-// groups of a team: group r transforms the M*M samples ky = R*m + r (every
-// input is loaded and multiplied once per team), the groups exchange their
-// sub-transforms through shared memory, and group r forms the outputs
-// [r*M*M, (r+1)*M*M) by the radix-R butterfly.  The exchange buffer then
-// serves as a P x TPB tile (column slots XOR-swizzled by row, conflict-free
-// writes) whose rows leave as chunks of TPB adjacent kx.
+// Pair product + inverse column transform of length P = R*M*M.  Persistent
+// blocks walk the items (pair, kx block) with pairs varying fastest, so that
+// the items in flight at one time read the same few spectrum columns (L2
+// reuse).  Decimation in time across the R groups of a team: group r
+// transforms the M*M samples ky = R*m + r (every input is loaded and
+// multiplied once per team), the groups exchange their sub-transforms through
+// shared memory, and group r forms the outputs [r*M*M, (r+1)*M*M) by the
+// radix-R butterfly.  The exchange buffer then serves as a P x TPB tile
+// (column slots XOR-swizzled by row, conflict-free writes) whose rows leave
+// as chunks of TPB adjacent kx.  While the tile leaves, the F_a loads of the
+// block's next item are already in flight, and items at the head of a kx
+// block ask L2 for the spectrum columns two kx blocks ahead.
 template <typename T, int P>
 __global__ void __launch_bounds__(PairColsCfg<T, P>::THREADS, PairColsCfg<T, P>::MIN_BLOCKS)
-k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KB, int Qh, int HA, int HB,
+k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA, int KB, int Qh, int HA, int HB,
             int Rout, int Qs, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st, int conditional) {
     using C = PairColsCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB, NQ = C::NQ;
+    const int npairs = KA * KB, nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb;
+    if ((int)blockIdx.x >= n_items) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* tw_sq = reinterpret_cast<cpx<T>*>(smem_raw + C::MAIN);
@@ -261,78 +268,95 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KB
     if (R > 1) stage_table(tw_n, tw.n[ilog2c(P)], C::TW_N);
     __syncthreads();
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
-    const int pair = blockIdx.x, kx0 = blockIdx.y * TPB, kx = kx0 + team;
-    const int a = pair / KB, b = pair % KB;
-    const bool active = kx < Qh;
-    const cpx<T>* fa = FA + ((size_t)a * Qh + (active ? kx : 0)) * P;
-    const cpx<T>* fb = FB + ((size_t)b * Qh + (active ? kx : 0)) * P;
-    // group r: the samples ky = R*m + r, m = j + M*i.  conj(F_a) F_b, F_b carrying the
-    // 1/(P Q) of the inverse.  All F loads are issued first (straight into the
-    // transform registers), then the F_b loads with the products: two waves of
-    // M independent loads per lane.
+    // group r: the samples ky = R*m + r, m = j + M*i, stored contiguously from slot
+    // r*NQ (the forward column transform's output order).  conj(F_a) F_b, F_b
+    // carrying the 1/(P Q) of the inverse.
     cpx<T> v[M];
-    if (active) {
+    auto load_fa = [&](int it) {
+        const int kx = (it / npairs) * TPB + team, a = (it % npairs) / KB;
+        if (kx < Qh) {
+            const cpx<T>* ga = FA + ((size_t)a * Qh + kx) * P + r * NQ + j;
 #pragma unroll
-        for (int i = 0; i < M; ++i) v[i] = __ldg(reinterpret_cast<const cpx<T>*>(fa) + R * (j + M * i) + r);
-#pragma unroll
-        for (int i = 0; i < M; ++i) v[i] = cmulc(__ldg(reinterpret_cast<const cpx<T>*>(fb) + R * (j + M * i) + r), v[i]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < M; ++i) v[i] = {T(0), T(0)};
-    }
-    team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
-    cpx<T>* tx = xbuf + (size_t)team * P;  // this team's R sub-transforms
-    if constexpr (R > 1) {
-        __syncthreads();  // every group is done with its transpose scratch (aliases xbuf)
-#pragma unroll
-        for (int k2 = 0; k2 < M; ++k2) tx[r * NQ + j + M * k2] = v[brev(k2, M)];
-        __syncthreads();
-        // X[k + r NQ] = sum_s W_P^{s (k + r NQ)} E_s[k]   (inverse direction)
-#pragma unroll
-        for (int k2 = 0; k2 < M; ++k2) {
-            const int k = j + M * k2;
-            cpx<T> acc = tx[k];
-#pragma unroll
-            for (int s2 = 1; s2 < R; ++s2)
-                acc = acc + cmul(tx[s2 * NQ + k], twl<+1>(tw_n, (s2 * (k + r * NQ)) & (P - 1)));
-            v[brev(k2, M)] = acc;
-        }
-    }
-    __syncthreads();  // exchange reads done: the buffer becomes the tile
-    // row = r*NQ + j + M*k2; tile slot (row, team) swizzled by row
-#pragma unroll
-    for (int k2 = 0; k2 < M; ++k2) {
-        const int row = r * NQ + j + M * k2;
-        xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = v[brev(k2, M)];
-    }
-    __syncthreads();
-    cpx<T>* yp = Y + (size_t)pair * Rout * Qs;
-    for (int row = threadIdx.x; row < P; row += C::THREADS) {
-        const int orow = circ_to_out(row, P, HA, HB - 1);
-        if (orow < 0) continue;
-        const int sw = (row >> C::SWZ) & (TPB - 1);
-        const cpx<T>* src = xbuf + (size_t)row * TPB;
-        cpx<T>* dst = yp + (size_t)orow * Qs + kx0;
-        if constexpr (sizeof(T) == 4 && TPB == 4) {
-            // one 32-byte row chunk: two 16-byte loads, undo the swizzle, two 16-byte stores
-            // (kx0 + 4 <= Qs always: Qs is a multiple of 4)
-            const float4 p0 = reinterpret_cast<const float4*>(src)[0];
-            const float4 p1 = reinterpret_cast<const float4*>(src)[1];
-            const float2 ph[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
-                                  make_float2(p1.z, p1.w)};
-            float2 lg[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int pc = c ^ sw;
-                lg[c] = pc == 0 ? ph[0] : pc == 1 ? ph[1] : pc == 2 ? ph[2] : ph[3];
-            }
-            reinterpret_cast<float4*>(dst)[0] = make_float4(lg[0].x, lg[0].y, lg[1].x, lg[1].y);
-            reinterpret_cast<float4*>(dst)[1] = make_float4(lg[2].x, lg[2].y, lg[3].x, lg[3].y);
+            for (int i = 0; i < M; ++i) v[i] = __ldg(ga + M * i);
         } else {
 #pragma unroll
-            for (int c = 0; c < TPB; ++c)
-                if (kx0 + c < Qs) dst[c] = src[c ^ sw];
+            for (int i = 0; i < M; ++i) v[i] = {T(0), T(0)};
         }
+    };
+    load_fa(blockIdx.x);
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int pair = item % npairs, kxb = item / npairs;
+        const int kx0 = kxb * TPB, kx = kx0 + team, b = pair % KB;
+        if (kx < Qh) {
+            const cpx<T>* gb = FB + ((size_t)b * Qh + kx) * P + r * NQ + j;
+#pragma unroll
+            for (int i = 0; i < M; ++i) v[i] = cmulc(__ldg(gb + M * i), v[i]);
+        }
+        if (pair < KA + KB && (int)threadIdx.x < TPB && kxb + 2 < nkxb) {
+            // the items of this kx block with pair < K_A + K_B each prefetch one
+            // spectrum's columns of kx block kxb + 2 into L2 (one bulk request per column)
+            const int kf = (kxb + 2) * TPB + threadIdx.x;
+            if (kf < Qh) {
+                const cpx<T>* src = pair < KA ? FA + ((size_t)pair * Qh + kf) * P : FB + ((size_t)(pair - KA) * Qh + kf) * P;
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((unsigned)(P * sizeof(cpx<T>)))
+                             : "memory");
+            }
+        }
+        team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
+        cpx<T>* tx = xbuf + (size_t)team * P;  // this team's R sub-transforms
+        if constexpr (R > 1) {
+            __syncthreads();  // every group is done with its transpose scratch (aliases xbuf)
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) tx[r * NQ + j + M * k2] = v[brev(k2, M)];
+            __syncthreads();
+            // X[k + r NQ] = sum_s W_P^{s (k + r NQ)} E_s[k]   (inverse direction)
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const int k = j + M * k2;
+                cpx<T> acc = tx[k];
+#pragma unroll
+                for (int s2 = 1; s2 < R; ++s2)
+                    acc = acc + cmul(tx[s2 * NQ + k], twl<+1>(tw_n, (s2 * (k + r * NQ)) & (P - 1)));
+                v[brev(k2, M)] = acc;
+            }
+        }
+        __syncthreads();  // exchange reads done: the buffer becomes the tile
+        // row = r*NQ + j + M*k2; tile slot (row, team) swizzled by row
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) {
+            const int row = r * NQ + j + M * k2;
+            xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = v[brev(k2, M)];
+        }
+        __syncthreads();
+        if (item + (int)gridDim.x < n_items) load_fa(item + gridDim.x);
+        cpx<T>* yp = Y + (size_t)pair * Rout * Qs;
+        if constexpr (sizeof(T) == 4 && TPB == 4) {
+            // Each 32-byte row chunk leaves as two 16-byte halves written by adjacent
+            // lanes (one sector per lane pair).  Logical columns 2h, 2h+1 sit in
+            // physical half h ^ (sw >> 1), swapped when sw is odd.  kx0 + 4 <= Qs
+            // always (Qs is a multiple of 4).
+            for (int q = threadIdx.x; q < 2 * P; q += C::THREADS) {
+                const int row = q >> 1, h = q & 1;
+                const int orow = circ_to_out(row, P, HA, HB - 1);
+                if (orow < 0) continue;
+                const int sw = (row >> C::SWZ) & 3;
+                float4 pv = reinterpret_cast<const float4*>(xbuf)[2 * row + (h ^ (sw >> 1))];
+                if (sw & 1) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
+                reinterpret_cast<float4*>(yp + (size_t)orow * Qs + kx0)[h] = pv;
+            }
+        } else {
+            for (int row = threadIdx.x; row < P; row += C::THREADS) {
+                const int orow = circ_to_out(row, P, HA, HB - 1);
+                if (orow < 0) continue;
+                const int sw = (row >> C::SWZ) & (TPB - 1);
+                const cpx<T>* src = xbuf + (size_t)row * TPB;
+                cpx<T>* dst = yp + (size_t)orow * Qs + kx0;
+#pragma unroll
+                for (int c = 0; c < TPB; ++c)
+                    if (kx0 + c < Qs) dst[c] = src[c ^ sw];
+            }
+        }
+        __syncthreads();  // tile reads done before the next item's transform scratch (aliases the tile)
     }
 }
 

@@ -150,6 +150,7 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     a.mi = mi_map; a.n = nm; a.counts = nullptr; a.st = st;
     a.prec_slot = 0; a.conditional = 0;
     a.rows_grid = std::min(g.R, bps * d->num_sms);
+    a.num_sms = d->num_sms;
     a.cb_smem = true;
     a.prof = nullptr;
     a.tm_cols = 0;

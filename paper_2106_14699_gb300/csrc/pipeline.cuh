@@ -26,6 +26,7 @@ struct PipeArgs {
     int prec_slot;    // 0: FP32 residual slot, 1: FP64
     int conditional;  // run only when STATUS_ESCALATE is set (AUTO re-run)
     int rows_grid;    // persistent grid of the row/epilogue kernel
+    int num_sms;      // SMs of the device (persistent grid of the pair-column kernel)
     bool cb_smem;     // B-marginal accumulators in shared memory
     Profiler* prof;   // optional launch timing (nullptr = off)
     int tm_cols;      // > 0: use the TMEM / TMA row kernel with this many TMEM columns

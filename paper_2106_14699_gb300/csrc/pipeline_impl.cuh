@@ -59,8 +59,18 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
     const size_t smem = pair_cols_smem<T, P>();
     cudaError_t e = ensure_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(g.KA * g.KB, (g.Qh + C::TPB - 1) / C::TPB);
-    kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, a.Y, a.tw, a.st,
+    // persistent grid: every resident block slot of the device, at most one per item
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::THREADS, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = n > 0 ? n : 1;
+    }
+    const long long items = (long long)g.KA * g.KB * ((g.Qh + C::TPB - 1) / C::TPB);
+    const long long slots = a.num_sms > 0 ? (long long)per_sm * a.num_sms : items;
+    const int grid = (int)(items < slots ? items : slots);
+    kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KA, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, a.Y, a.tw, a.st,
                                         a.conditional);
     return cudaGetLastError();
 }
