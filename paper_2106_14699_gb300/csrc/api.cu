@@ -126,6 +126,7 @@ size_t workspace_bytes(const Geom& g, const Workspace<T>& w) {
     off = align_up(off + (size_t)g.KB * g.Qh * g.P * cs, 256);   // FB
     off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);  // Y
     off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);  // CB
+    off = align_up(off + sizeof(int), 256);  // work counter
     return off;
 }
 
@@ -140,6 +141,8 @@ void carve_workspace(const Geom& g, Workspace<T>& w, char* base) {
     w.args.FB = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.Qh * g.P * cs, 256);
     w.args.Y = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);
     w.args.cb_global = w.cb_smem ? nullptr : (float*)(base + off);
+    off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);
+    w.args.work_ctr = (int*)(base + off);
 }
 
 template <typename T>

@@ -250,23 +250,30 @@ struct PairColsCfg {
 // (column slots XOR-swizzled by row, conflict-free writes) whose rows leave
 // as chunks of TPB adjacent kx.  While the tile leaves, the F_a loads of the
 // block's next item are already in flight, and items at the head of a kx
-// block ask L2 for the spectrum columns two kx blocks ahead.
+// block ask L2 for the spectrum columns two kx blocks ahead.  work_ctr must
+// be zero at launch.
 template <typename T, int P>
 __global__ void __launch_bounds__(PairColsCfg<T, P>::THREADS, PairColsCfg<T, P>::MIN_BLOCKS)
 k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA, int KB, int Qh, int HA, int HB,
-            int Rout, int Qs, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st, int conditional) {
+            int Rout, int Qs, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st, int conditional,
+            int* __restrict__ work_ctr) {
     using C = PairColsCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB, NQ = C::NQ;
     const int npairs = KA * KB, nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb;
-    if ((int)blockIdx.x >= n_items) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
     cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* tw_sq = reinterpret_cast<cpx<T>*>(smem_raw + C::MAIN);
     cpx<T>* tw_n = tw_sq + NQ;
+    // Items are handed out in order from a counter (zeroed before the launch), so
+    // that the items in flight stay within a few kx blocks whatever the blocks' pace.
+    if (threadIdx.x == 0) s_item = atomicAdd(work_ctr, 1);
     stage_table(tw_sq, tw.sq[ilog2c(M)], NQ);
     if (R > 1) stage_table(tw_n, tw.n[ilog2c(P)], C::TW_N);
     __syncthreads();
+    int item = s_item;
+    if (item >= n_items) return;
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
     // group r: the samples ky = R*m + r, m = j + M*i, stored contiguously from slot
     // r*NQ (the forward column transform's output order).  conj(F_a) F_b, F_b
@@ -283,8 +290,10 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             for (int i = 0; i < M; ++i) v[i] = {T(0), T(0)};
         }
     };
-    load_fa(blockIdx.x);
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    load_fa(item);
+    while (true) {
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(work_ctr, 1);
         const int pair = item % npairs, kxb = item / npairs;
         const int kx0 = kxb * TPB, kx = kx0 + team, b = pair % KB;
         if (kx < Qh) {
@@ -303,6 +312,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             }
         }
         team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
+        if (threadIdx.x == 0) s_item = next;  // read by all after the tile barrier below
         cpx<T>* tx = xbuf + (size_t)team * P;  // this team's R sub-transforms
         if constexpr (R > 1) {
             __syncthreads();  // every group is done with its transpose scratch (aliases xbuf)
@@ -328,7 +338,8 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = v[brev(k2, M)];
         }
         __syncthreads();
-        if (item + (int)gridDim.x < n_items) load_fa(item + gridDim.x);
+        next = s_item;
+        if (next < n_items) load_fa(next);
         cpx<T>* yp = Y + (size_t)pair * Rout * Qs;
         if constexpr (sizeof(T) == 4 && TPB == 4) {
             // Each 32-byte row chunk leaves as two 16-byte halves written by adjacent
@@ -356,7 +367,9 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                     if (kx0 + c < Qs) dst[c] = src[c ^ sw];
             }
         }
-        __syncthreads();  // tile reads done before the next item's transform scratch (aliases the tile)
+        __syncthreads();  // tile reads (and s_item) done before the next item reuses them
+        if (next >= n_items) break;
+        item = next;
     }
 }
 

@@ -117,7 +117,7 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     if (e != cudaSuccess) return to_status(e);
     if (bps < 1) return CMIF_ERR_UNSUPPORTED;
 
-    // Carve the fixed array: [twiddles | status | peak partials | N map | T1A | T1B | FA | FB | Y].
+    // Carve the fixed array: [twiddles | status | peak partials | N map | T1A | T1B | FA | FB | Y | counter].
     const size_t cs = sizeof(cpx<float>);
     const int nparts = 2 * d->num_sms;
     size_t off = d->tw_bytes;
@@ -129,6 +129,7 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     const size_t oFA = off; off = up256(off + (size_t)g.KA * g.Qh * g.P * cs);
     const size_t oFB = off; off = up256(off + (size_t)g.KB * g.Qh * g.P * cs);
     const size_t oY = off; off = up256(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs);
+    const size_t oCtr = off; off = up256(off + sizeof(int));
     if (off > kNoAllocBytes) return CMIF_ERR_UNSUPPORTED;
 
     unsigned char* b = d->base;
@@ -146,6 +147,7 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     a.FB = reinterpret_cast<cpx<float>*>(b + oFB);
     a.Y = reinterpret_cast<cpx<float>*>(b + oY);
     a.cb_global = nullptr;
+    a.work_ctr = reinterpret_cast<int*>(b + oCtr);
     a.tw = d->tw;
     a.mi = mi_map; a.n = nm; a.counts = nullptr; a.st = st;
     a.prec_slot = 0; a.conditional = 0;

@@ -18,6 +18,7 @@ struct PipeArgs {
     cpx<T>* FB;   // [K_B][Qh][P]
     cpx<T>* Y;    // [K_A*K_B][R][Qs] column-inverted products, output rows only
     float* cb_global;  // [rows_grid][K_B][Q] when !cb_smem
+    int* work_ctr;     // item counter of the pair-column kernel (zeroed before each launch)
     Tw<T> tw;
     double* mi;
     int32_t* n;

@@ -70,8 +70,10 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
     const long long items = (long long)g.KA * g.KB * ((g.Qh + C::TPB - 1) / C::TPB);
     const long long slots = a.num_sms > 0 ? (long long)per_sm * a.num_sms : items;
     const int grid = (int)(items < slots ? items : slots);
+    e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
     kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KA, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, a.Y, a.tw, a.st,
-                                        a.conditional);
+                                        a.conditional, a.work_ctr);
     return cudaGetLastError();
 }
 
