@@ -341,30 +341,30 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
         next = s_item;
         if (next < n_items) load_fa(next);
         cpx<T>* yp = Y + (size_t)pair * Rout * Qs;
-        if constexpr (sizeof(T) == 4 && TPB == 4) {
-            // Each 32-byte row chunk leaves as two 16-byte halves written by adjacent
-            // lanes (one sector per lane pair).  Logical columns 2h, 2h+1 sit in
-            // physical half h ^ (sw >> 1), swapped when sw is odd.  kx0 + 4 <= Qs
-            // always (Qs is a multiple of 4).
-            for (int q = threadIdx.x; q < 2 * P; q += C::THREADS) {
-                const int row = q >> 1, h = q & 1;
+        if constexpr (sizeof(T) == 4 && TPB >= 2) {
+            // Each row chunk of TPB complex leaves as TPB/2 16-byte pieces written by
+            // adjacent lanes.  Logical columns 2h, 2h+1 sit in physical piece
+            // h ^ (sw >> 1), swapped when sw is odd.  Qs and kx0 are even, so a
+            // piece is either wholly inside the row (kx0 + 2h < Qs) or wholly out;
+            // for TPB <= 4 always inside (Qs is a multiple of 4).
+            constexpr int PPR = TPB / 2;
+            for (int q = threadIdx.x; q < P * PPR; q += C::THREADS) {
+                const int row = q / PPR, h = q % PPR;
                 const int orow = circ_to_out(row, P, HA, HB - 1);
-                if (orow < 0) continue;
-                const int sw = (row >> C::SWZ) & 3;
-                float4 pv = reinterpret_cast<const float4*>(xbuf)[2 * row + (h ^ (sw >> 1))];
+                if (orow < 0 || (TPB > 4 && kx0 + 2 * h >= Qs)) continue;
+                const int sw = (row >> C::SWZ) & (TPB - 1);
+                float4 pv = reinterpret_cast<const float4*>(xbuf)[row * PPR + (h ^ (sw >> 1))];
                 if (sw & 1) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
                 reinterpret_cast<float4*>(yp + (size_t)orow * Qs + kx0)[h] = pv;
             }
         } else {
-            for (int row = threadIdx.x; row < P; row += C::THREADS) {
+            // one complex per lane, adjacent lanes on adjacent columns of a row
+            for (int q = threadIdx.x; q < P * TPB; q += C::THREADS) {
+                const int row = q / TPB, c = q % TPB;
                 const int orow = circ_to_out(row, P, HA, HB - 1);
-                if (orow < 0) continue;
+                if (orow < 0 || kx0 + c >= Qs) continue;
                 const int sw = (row >> C::SWZ) & (TPB - 1);
-                const cpx<T>* src = xbuf + (size_t)row * TPB;
-                cpx<T>* dst = yp + (size_t)orow * Qs + kx0;
-#pragma unroll
-                for (int c = 0; c < TPB; ++c)
-                    if (kx0 + c < Qs) dst[c] = src[c ^ sw];
+                yp[(size_t)orow * Qs + kx0 + c] = xbuf[(size_t)row * TPB + (c ^ sw)];
             }
         }
         __syncthreads();  // tile reads (and s_item) done before the next item reuses them
