@@ -33,6 +33,16 @@ template <typename T>
 __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T>
 __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+// FP32: one packed two-lane instruction per complex add / subtract (sm_100+
+// FADD2 / FFMA2; each lane rounds like the scalar op, a - b as fma(b, -1, a)).
+__device__ __forceinline__ cpx<float> operator+(cpx<float> a, cpx<float> b) {
+    const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    return {r.x, r.y};
+}
+__device__ __forceinline__ cpx<float> operator-(cpx<float> a, cpx<float> b) {
+    const float2 r = __ffma2_rn(make_float2(b.x, b.y), make_float2(-1.f, -1.f), make_float2(a.x, a.y));
+    return {r.x, r.y};
+}
 template <typename T>
 __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
@@ -89,7 +99,9 @@ __device__ __forceinline__ cpx<T> twc(cpx<T> d, int k) {
 
 // In-register M-point DFT, natural order in, bit-reversed order out:
 // after the call v[brev(k, M)] = sum_n v_in[n] e^{DIR 2 pi i n k / M}.
-template <int M, int DIR, typename T>
+// PACK = false keeps the butterflies' adds in scalar form (the +-i twiddles then
+// stay free operand negations), for kernels where that issues fewer instructions.
+template <int M, int DIR, bool PACK = true, typename T>
 __device__ __forceinline__ void dft_reg(cpx<T> (&v)[M]) {
 #pragma unroll
     for (int span = M / 2; span >= 1; span >>= 1) {
@@ -98,8 +110,13 @@ __device__ __forceinline__ void dft_reg(cpx<T> (&v)[M]) {
 #pragma unroll
             for (int j = 0; j < span; ++j) {
                 cpx<T> a = v[start + j], b = v[start + j + span];
-                v[start + j] = a + b;
-                v[start + j + span] = twc<M, DIR>(a - b, j * (M / (2 * span)));
+                if constexpr (PACK) {
+                    v[start + j] = a + b;
+                    v[start + j + span] = twc<M, DIR>(a - b, j * (M / (2 * span)));
+                } else {
+                    v[start + j] = cpx<T>{a.x + b.x, a.y + b.y};
+                    v[start + j + span] = twc<M, DIR>(cpx<T>{a.x - b.x, a.y - b.y}, j * (M / (2 * span)));
+                }
             }
         }
     }
@@ -157,9 +174,9 @@ __host__ __device__ constexpr int grp_scratch_bytes() {
 // Every lane of every warp taking part must call this (it uses __syncwarp).
 // The four-step core on values already in registers: v[i] = y[j + M*i] for the
 // group's M*M-point sequence y.  Result: v[brev(k2, M)] = Y[j + M*k2].
-template <int M, int DIR, typename T>
+template <int M, int DIR, bool PACK = true, typename T>
 __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, const cpx<T>* __restrict__ twq) {
-    dft_reg<M, DIR>(v);  // v[brev(k1)] = A[j][k1]
+    dft_reg<M, DIR, PACK>(v);  // v[brev(k1)] = A[j][k1]
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) v[brev(k1, M)] = cmul(v[brev(k1, M)], twl<DIR>(twq, k1 * M + j));
     if constexpr (sizeof(T) == 4 && M == 32) {
@@ -209,10 +226,10 @@ __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, c
         for (int n2 = 0; n2 < M; ++n2) v[n2] = sc[j * M + (n2 ^ j)];
         __syncwarp();
     }
-    dft_reg<M, DIR>(v);  // v[brev(k2)] = X_r[j + M k2]
+    dft_reg<M, DIR, PACK>(v);  // v[brev(k2)] = X_r[j + M k2]
 }
 
-template <int M, int R, int DIR, typename T, typename Load>
+template <int M, int R, int DIR, bool PACK = true, typename T, typename Load>
 __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
                                          const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
     constexpr int NQ = M * M;
@@ -236,7 +253,7 @@ __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& lo
             v[i] = (r == 0) ? acc : cmul(acc, twl<DIR>(twn, m * r));
         }
     }
-    team_fft_core<M, DIR>(v, j, sm, twq);
+    team_fft_core<M, DIR, PACK>(v, j, sm, twq);
 }
 
 }  // namespace cmif

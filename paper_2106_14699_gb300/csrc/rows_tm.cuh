@@ -233,7 +233,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 return {e.x - o.y, e.y + o.x};
             };
             cpx<float> v[M];
-            team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw_sq, tw_pre);
+            team_fft<M, R, +1, false>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw_sq, tw_pre);
             // the staging buffer is free again: prefetch this team's next active item
             // (the next round of this row, else round 0 of its next row)
             __syncwarp();
