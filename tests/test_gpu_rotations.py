@@ -113,3 +113,20 @@ def test_config4_planted_rotation_and_shift(cm):
     mis = [t[4] for t in top]
     assert all(mis[i] >= mis[i + 1] for i in range(4))
     plan.close()
+
+
+def test_sharded_entry_single_rank_equals_direct(cm):
+    """shard.align_rotations_sharded without a process group = one rank holding
+    every angle: its merged top-k equals cmif_align_rotations' device top-k."""
+    from paper_2106_14699_gb300 import shard
+    cfg = synth.make_config(4, scale=64 / 512)
+    A, B = _dev(cfg["A"]), _dev(cfg["B"])
+    H, W = cfg["A"].shape
+    angles = list(cfg["angles"][::4])
+    plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32)
+    top = torch.empty(24 * 5, dtype=torch.uint8, device="cuda:0")
+    plan.align_rotations(A, None, B, None, angles, 0.5, 5, top)
+    direct = cm.peaks_from_bytes(top, 5)
+    merged = shard.align_rotations_sharded(plan, A, None, B, None, angles, 0.5, 5)
+    assert merged == direct
+    plan.close()
