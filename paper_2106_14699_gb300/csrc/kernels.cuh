@@ -100,7 +100,13 @@ struct TeamGeom {
 };
 
 // ---------------------------------------------------------------------------
-// Forward row transforms.  Item = (row y, plane pair pp): planes 2pp, 2pp+1.
+// Forward row transforms.  Block = (row y, TPB plane pairs); team t takes the
+// plane pair pp = blockIdx.y * TPB + t (planes 2pp, 2pp+1).  The block first
+// stages the row as one byte per pixel (the label, or kMaskedOut where the
+// mask is 0; the label range is checked here), then every team builds its two
+// level sets from shared memory.
+constexpr unsigned char kMaskedOut = 255;
+
 template <typename T, int Q>
 struct FwdRowsCfg {
     using G = TeamGeom<T, Q>;
@@ -108,7 +114,7 @@ struct FwdRowsCfg {
     static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
     static constexpr int THREADS = TPB * TEAM;
     static constexpr int REGION = (int)(Q * sizeof(cpx<T>)) > G::SCRATCH ? (int)(Q * sizeof(cpx<T>)) : G::SCRATCH;
-    static constexpr size_t SMEM = (size_t)TPB * REGION;
+    static constexpr size_t smem(int W) { return (size_t)TPB * REGION + (((size_t)W + 15) & ~(size_t)15); }
 };
 
 template <typename T, int Q>
@@ -119,27 +125,32 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, int H,
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* code = smem_raw + (size_t)C::TPB * C::REGION;
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
     const int npp = (K + 1) / 2;
-    const long long item = (long long)blockIdx.x * C::TPB + team;
-    const bool active = item < (long long)H * npp;
-    const int y = active ? (int)(item / npp) : 0, pp = active ? (int)(item % npp) : 0;
+    const int y = blockIdx.x, pp = blockIdx.y * C::TPB + team;
+    const bool active = pp < npp;
     const int la = 2 * pp, lb = 2 * pp + 1;
-    unsigned char* region = smem_raw + (size_t)team * C::REGION;
-    cpx<T>* sm = reinterpret_cast<cpx<T>*>(region);
     const int32_t* xr = X + (size_t)y * W;
     const uint8_t* mr = MX ? MX + (size_t)y * W : nullptr;
     bool bad = false;
+    for (int x = threadIdx.x; x < W; x += C::THREADS) {
+        const int lab = __ldg(xr + x);
+        const bool m = mr ? (__ldg(mr + x) != 0) : true;
+        if (m && (lab < 0 || lab >= K)) bad = true;
+        code[x] = m && lab >= 0 && lab < K ? (unsigned char)lab : kMaskedOut;
+    }
+    if (bad && blockIdx.y == 0) atomicOr(&st->flags, STATUS_LABEL_RANGE);
+    __syncthreads();
+    unsigned char* region = smem_raw + (size_t)team * C::REGION;
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(region);
     auto load = [&](int x) -> cpx<T> {
         if (!active || x >= W) return {T(0), T(0)};
-        const int lab = xr[x];
-        const bool m = mr ? (mr[x] != 0) : true;
-        if (m && (lab < 0 || lab >= K)) bad = true;
-        return {(m && lab == la) ? T(1) : T(0), (m && lab == lb) ? T(1) : T(0)};
+        const int c = code[x];
+        return {c == la ? T(1) : T(0), c == lb ? T(1) : T(0)};
     };
     cpx<T> v[M];
     team_fft<M, R, -1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)], tw.n[ilog2c(Q)]);
-    if (bad && pp == 0) atomicOr(&st->flags, STATUS_LABEL_RANGE);
     __syncthreads();
 #pragma unroll
     for (int k2 = 0; k2 < M; ++k2) sm[R * (j + M * k2) + r] = v[brev(k2, M)];
@@ -155,14 +166,20 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, int H,
 }
 
 // ---------------------------------------------------------------------------
-// Forward column transforms.  Item = (plane, kx).
+// Forward column transforms.  Block = (TPB adjacent kx columns, plane).  The
+// block first stages its H x TPB input tile in shared memory with coalesced
+// 16-byte loads (column slots XOR-swizzled by row, so that the teams' column
+// reads are conflict-free), then each team transforms one column.
 template <typename T, int P>
 struct ColCfg {
     using G = TeamGeom<T, P>;
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
     static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
     static constexpr int THREADS = TPB * TEAM;
-    static constexpr size_t SMEM = (size_t)TPB * G::SCRATCH;
+    static constexpr int SWZ = TPB >= 16 ? 0 : (TPB == 8 ? 1 : (TPB == 4 ? 2 : 3));
+    static constexpr size_t SCR = (size_t)TPB * G::SCRATCH;
+    static constexpr size_t TILE_MAX = (size_t)P * TPB * sizeof(cpx<T>);  // H <= P rows
+    static constexpr size_t smem(int H) { return SCR + (size_t)H * TPB * sizeof(cpx<T>); }
 };
 
 template <typename T, int P>
@@ -171,15 +188,36 @@ k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cp
            const DevStatus* __restrict__ st, int conditional, T out_scale) {
     using C = ColCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
-    constexpr int M = C::M, R = C::R;
+    constexpr int M = C::M, R = C::R, TPB = C::TPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* tile = reinterpret_cast<cpx<T>*>(smem_raw + C::SCR);
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
-    const int kx = blockIdx.x * C::TPB + team, plane = blockIdx.y;
+    const int kx0 = blockIdx.x * TPB, kx = kx0 + team, plane = blockIdx.y;
+    const cpx<T>* src = T1 + (size_t)plane * H * Qs + kx0;
+    if constexpr (sizeof(T) == 4 && TPB >= 2) {
+        // 16-byte pieces (two columns each); Qs and kx0 are even, so a piece is
+        // wholly inside the row or wholly beyond Qs (never read: zeros)
+        constexpr int PPR = TPB / 2;
+        for (int q = threadIdx.x; q < H * PPR; q += C::THREADS) {
+            const int y = q / PPR, h = q % PPR;
+            float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kx0 + 2 * h < Qs) pv = __ldg(reinterpret_cast<const float4*>(src + (size_t)y * Qs) + h);
+            const int sw = (y >> C::SWZ) & (TPB - 1);
+            if (sw & 1) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
+            reinterpret_cast<float4*>(tile)[y * PPR + (h ^ (sw >> 1))] = pv;
+        }
+    } else {
+        for (int q = threadIdx.x; q < H * TPB; q += C::THREADS) {
+            const int y = q / TPB, c = q % TPB;
+            const int sw = (y >> C::SWZ) & (TPB - 1);
+            tile[y * TPB + (c ^ sw)] = kx0 + c < Qs ? src[(size_t)y * Qs + c] : cpx<T>{T(0), T(0)};
+        }
+    }
+    __syncthreads();
     const bool active = kx < Qh;
-    const cpx<T>* col = T1 + (size_t)plane * H * Qs + kx;
     auto load = [&](int y) -> cpx<T> {
         if (!active || y >= H) return {T(0), T(0)};
-        return col[(size_t)y * Qs];
+        return tile[y * TPB + (team ^ ((y >> C::SWZ) & (TPB - 1)))];
     };
     cpx<T> v[M];
     team_fft<M, R, -1>(v, r, j, load, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(),

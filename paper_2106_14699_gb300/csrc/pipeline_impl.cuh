@@ -32,11 +32,10 @@ static cudaError_t launch_fwd_rows(const int32_t* X, const uint8_t* MX, int H, i
                                    const Tw<T>& tw, DevStatus* st, int conditional, cudaStream_t s) {
     using C = FwdRowsCfg<T, Q>;
     auto kern = k_fwd_rows<T, Q>;
-    cudaError_t e = ensure_smem(kern, C::SMEM);
+    cudaError_t e = ensure_smem(kern, C::smem(Q));
     if (e != cudaSuccess) return e;
-    const long long items = (long long)H * ((K + 1) / 2);
-    const unsigned blocks = (unsigned)((items + C::TPB - 1) / C::TPB);
-    kern<<<blocks, C::THREADS, C::SMEM, s>>>(X, MX, H, W, K, Qs, T1, tw, st, conditional);
+    dim3 grid(H, ((K + 1) / 2 + C::TPB - 1) / C::TPB);
+    kern<<<grid, C::THREADS, C::smem(W), s>>>(X, MX, H, W, K, Qs, T1, tw, st, conditional);
     return cudaGetLastError();
 }
 
@@ -45,10 +44,10 @@ static cudaError_t launch_fwd_cols(const cpx<T>* T1, int H, int K, int Qh, int Q
                                    const DevStatus* st, int conditional, T out_scale, cudaStream_t s) {
     using C = ColCfg<T, P>;
     auto kern = k_fwd_cols<T, P>;
-    cudaError_t e = ensure_smem(kern, C::SMEM);
+    cudaError_t e = ensure_smem(kern, C::smem(P));
     if (e != cudaSuccess) return e;
     dim3 grid((Qh + C::TPB - 1) / C::TPB, K);
-    kern<<<grid, C::THREADS, C::SMEM, s>>>(T1, H, K, Qh, Qs, F, tw, st, conditional, out_scale);
+    kern<<<grid, C::THREADS, C::smem(H), s>>>(T1, H, K, Qh, Qs, F, tw, st, conditional, out_scale);
     return cudaGetLastError();
 }
 
