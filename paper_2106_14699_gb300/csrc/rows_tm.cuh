@@ -223,14 +223,19 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                     s_abort = 1;
                 }
             }
-            // Hermitian split: z = IDFT_L(E + iO), z[m] = x[2m] + i x[2m+1]
+            // Hermitian split: z = IDFT_L(E + iO), z[m] = x[2m] + i x[2m+1].  With
+            // t = e^{-2 pi i k/Q} from the table: E = y_k + conj(y_{L-k}),
+            // iO = (y_k - conj(y_{L-k})) * i conj(t) = d * (t.y, t.x); packed adds.
             auto load = [&](int k) -> cpx<float> {
                 if (!act) return {0.f, 0.f};
-                const cpx<float> yk = stage[k], ym = stage[L - k];
-                const cpx<float> e = {yk.x + ym.x, yk.y - ym.y};
-                const cpx<float> d = {yk.x - ym.x, yk.y + ym.y};
-                const cpx<float> o = cmul(d, twl<+1>(twq_c2r, k));
-                return {e.x - o.y, e.y + o.x};
+                const float2 yk = reinterpret_cast<const float2*>(stage)[k];
+                const float2 ym = reinterpret_cast<const float2*>(stage)[L - k];
+                const float2 e = __ffma2_rn(ym, make_float2(1.f, -1.f), yk);
+                const float2 d = __ffma2_rn(ym, make_float2(-1.f, 1.f), yk);
+                const cpx<float> t = twq_c2r[k];
+                const cpx<float> io = cmul(cpx<float>{d.x, d.y}, cpx<float>{t.y, t.x});
+                const float2 z = __fadd2_rn(e, make_float2(io.x, io.y));
+                return {z.x, z.y};
             };
             cpx<float> v[M];
             team_fft<M, R, +1, false>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw_sq, tw_pre);
@@ -244,10 +249,14 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
             }
 #pragma unroll
             for (int k = 0; k < M; ++k) {
-                const float cr = round_fp32(v[k].x), ci = round_fp32(v[k].y);
-                res_max = fmaxf(res_max, fmaxf(fabsf(v[k].x - cr), fabsf(v[k].y - ci)));
-                v[k].x = cr;
-                v[k].y = ci;
+                // nearest integers (the 1.5 * 2^23 shift, packed) and the residual
+                const float2 x = make_float2(v[k].x, v[k].y);
+                const float2 c = __fadd2_rn(__fadd2_rn(x, make_float2(12582912.0f, 12582912.0f)),
+                                            make_float2(-12582912.0f, -12582912.0f));
+                const float2 dv = __ffma2_rn(c, make_float2(-1.f, -1.f), x);
+                res_max = fmaxf(res_max, fmaxf(fabsf(dv.x), fabsf(dv.y)));
+                v[k].x = c.x;
+                v[k].y = c.y;
             }
             const int nt = min(NT, npairs - base);
             const int a0 = base / KB, b0 = base - a0 * KB;
