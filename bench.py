@@ -235,14 +235,31 @@ def run_secondary(args):
         ins = [d(cfg[k]) for k in ("A", "M_A", "B", "M_B")]
         step = lambda: plan.compute(ins[0], ins[1], ins[2], ins[3], mi, n, None, 0.5, pk)
         units, name = R * C, cfg["name"] + (" FP32" if prec == cm.FP32 else " FP64")
-    elif args.workload == "rotation":
+    elif args.workload in ("rotation", "rotation-window"):
         cfg = synth.make_config(4)
         H, W = cfg["A"].shape
-        plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True)
+        win = args.workload == "rotation-window"
+        plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True, window=win)
         top = torch.empty(24 * 5, dtype=torch.uint8, device=dev)
         A, B = d(cfg["A"]), d(cfg["B"])
         step = lambda: plan.align_rotations(A, None, B, None, cfg["angles"], 0.5, 5, top)
-        units, name = (2 * H - 1) * (2 * W - 1) * len(cfg["angles"]), cfg["name"] + " FP32"
+        if win:  # X_S of the padded search: |chi_i| <= ceil(size_i (1 - gamma)) (equal sizes)
+            py, px = math.ceil(H * 0.5), math.ceil(W * 0.5)
+            units = (2 * min(py, H - 1) + 1) * (2 * min(px, W - 1) + 1) * len(cfg["angles"])
+            name = cfg["name"] + " padded-window FP32"
+        else:
+            units, name = (2 * H - 1) * (2 * W - 1) * len(cfg["angles"]), cfg["name"] + " FP32"
+    elif args.workload == "two-stage":
+        cfg = synth.make_config(4)
+        H, W = cfg["A"].shape
+        # no graph: the two stages have different angle lists (one cached graph would be re-captured each call)
+        plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=False, window=True)
+        A, B = d(cfg["A"]), d(cfg["B"])
+        u = [(i + 0.5) / 16 for i in range(16)]
+        step = lambda: plan.align_two_stage(A, None, B, None, 64, u, 0.5)
+        py, px = math.ceil(H * 0.5), math.ceil(W * 0.5)
+        units = (2 * min(py, H - 1) + 1) * (2 * min(px, W - 1) + 1) * (64 + len(u))
+        name = cfg["name"] + " two-stage 64+16 padded-window FP32"
     else:
         cfg = synth.make_config(5)
         pairs = [dict(A=d(p["A"]), M_A=d(p["M_A"]), B=d(p["B"]), M_B=d(p["M_B"]), K_A=p["K_A"], K_B=p["K_B"],
@@ -290,7 +307,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single1024",
-                    choices=["single1024", "rotation", "batch", "single256", "plain64"],
+                    choices=["single1024", "rotation", "rotation-window", "two-stage", "batch", "single256",
+                             "plain64"],
                     help="single1024 (default, the headline): config 3; rotation: config 4 (512^2, 64 angles); "
                          "batch: config 5 (128 uneven pairs x 4 angles); single256 / plain64: configs 2 / 1")
     ap.add_argument("--profile-shape", default=None,

@@ -83,6 +83,13 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
 #define CMIF_FLAG_DEBUG_COUNTS 1u /* allow a non-NULL counts output in cmif_compute */
 #define CMIF_FLAG_GRAPH 2u        /* capture each call's launches in a CUDA graph once and replay it while the
                                      call's arguments (pointers, gamma, angles) are unchanged */
+#define CMIF_FLAG_WINDOW 4u       /* Alg. 1's padded search window (Sec. 4, Alg. 1 line 2: A and M_A zero-padded
+                                     by p_i = ceil(|X_B|_i (1 - gamma)) along each axis).  X_S becomes the shifts
+                                     that keep B's domain inside padded A's: chi_i in [|X_B|_i - |X_A|_i - p_i, p_i]
+                                     (|chi_i| <= p_i for equal sizes), intersected with the full range.  Only the
+                                     window's map rows are computed (rows outside it are returned as MI = 0,
+                                     N = 0); max N and the peak are taken over the window.  A call whose window
+                                     is empty (B cannot fit inside padded A) returns CMIF_ERR_INVALID_ARG. */
 
 /* One argmax record of Alg. 1: the displacement chi = (dy, dx) maximising
  * CMIF among shifts with N(chi) >= gamma * max N, for transform angle_idx
@@ -171,6 +178,25 @@ cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t
                                  const uint8_t* M_B, const double* angles_rad_host, int n_angles, double gamma,
                                  int top_k, cmif_peak* topk_dev, double* mi_maps, void* stream);
 
+/* Two-stage rigid alignment (Sec. 4, the paragraph after Alg. 1): (i) Alg. 1
+ * over the grid theta_t = 2 pi t / n_grid, t < n_grid; (ii) Alg. 1 over
+ * n_refine angles theta* + (2 u_i - 1) 2 pi / n_grid around the grid winner
+ * theta* (0 when no grid angle has I_T > 0), continuing stage (i)'s I and
+ * T-hat (a refinement angle replaces the grid choice only when its I_T is
+ * strictly greater).  The paper samples the refinement angles uniformly from
+ * that interval; here the caller passes the uniform draws u_i in [0, 1], so
+ * that a run is reproducible.
+ *   n_grid        : 1..4096;  refine_u_host: host double[n_refine] (NULL if 0)
+ *   best_host     : host; angle_idx = t for a grid angle, n_grid + i for
+ *                   refinement angle i, -1 for the identity
+ *   best_angle_rad: host; the winning rotation angle (0 for the identity)
+ * Synchronous: waits for stage (i) to choose the refinement interval and for
+ * stage (ii) to finish.  The plan's flags (CMIF_FLAG_WINDOW, CMIF_FLAG_GRAPH)
+ * apply to both stages. */
+cmif_status cmif_align_two_stage(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
+                                 const uint8_t* M_B, int n_grid, const double* refine_u_host, int n_refine,
+                                 double gamma, cmif_peak* best_host, double* best_angle_rad, void* stream);
+
 /* ---- Batches of image pairs (many sizes, label counts and angle sets) ----
  * One batch holds one device workspace sized for its largest pair; the pairs
  * run one after another on the call's stream (each as cmif_align_rotations,
@@ -193,7 +219,7 @@ typedef struct {
 /* Validate the pairs (limits as cmif_plan_create_ex, 0 <= n_angles <= 4096),
  * copy the descriptors and allocate the shared workspace.  The device images
  * the descriptors point to must stay valid and unchanged for the batch's life.
- * prec as for plans; flags: 0 or CMIF_FLAG_GRAPH. */
+ * prec as for plans; flags: 0, CMIF_FLAG_GRAPH and/or CMIF_FLAG_WINDOW. */
 cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc* descs, cmif_precision prec,
                               unsigned flags);
 

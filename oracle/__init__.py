@@ -19,6 +19,15 @@ Functions and the passages they follow:
 * ``gamma_argmax``, ``align`` -- the per-transform gamma-gated argmax and the
                      strict-greater update over transforms of Alg. 1.  Pinned by
                      hand-built cases.
+* ``alg1_padded`` -- one transform of Alg. 1 with its ZERO-PAD step (Alg. 1
+                     line 2, Sec. 4): A and M_A padded by ceil(|X_B|_i (1 - gamma))
+                     zeros along each axis, the direct CMIF of the padded pair, X_S
+                     = the shifts that keep B's domain inside padded A's, and the
+                     gated argmax over X_S.  Pinned by tests/test_oracle.py
+                     (padding changes nothing inside X_S; full-mask cases).
+* ``align_two_stage`` -- the two-stage rigid search of Sec. 4 (grid, then random
+                     refinement in [theta - 2 pi/|Omega|, theta + 2 pi/|Omega|]), the
+                     uniform draws passed in.  Pinned by hand-checked compositions.
 """
 from __future__ import annotations
 
@@ -196,3 +205,79 @@ def align(per_angle, gamma, top_k=1):
             best = (t, idx, i_t, n_t)
     order = sorted(range(len(recs)), key=lambda k: (-recs[k][2], recs[k][0]))
     return best, [recs[k] for k in order[:top_k]]
+
+
+def alg1_padded(A, M_A, B, M_B, K_A, K_B, gamma):
+    """One transform of Alg. 1 with the ZERO-PAD step (Alg. 1 line 2).
+
+    Pads A and M_A by p_i = ceil(|X_B|_i (1 - gamma)) zeros on both sides of
+    each axis, computes the direct CMIF of (padded A, B), restricts it to X_S =
+    the shifts at which B's whole domain lies inside padded A's, and takes the
+    gamma-gated argmax there (max N over X_S; ties: lowest row-major index).
+    Returns dict(dy, dx, mi, n, window=(dy_lo, dy_hi, dx_lo, dx_hi)) with the
+    displacement relative to the UNPADDED A (the padding shifts chi by p).
+    """
+    A = np.asarray(A)
+    H_A, W_A = A.shape
+    H_B, W_B = np.asarray(B).shape
+    py = int(np.ceil(H_B * (1.0 - gamma)))
+    px = int(np.ceil(W_B * (1.0 - gamma)))
+    Ap = np.zeros((H_A + 2 * py, W_A + 2 * px), dtype=A.dtype)
+    Ap[py:py + H_A, px:px + W_A] = A
+    Mp = np.zeros(Ap.shape, dtype=np.uint8)
+    Mp[py:py + H_A, px:px + W_A] = 1 if M_A is None else np.asarray(M_A, dtype=np.uint8)
+    ref = cmif(Ap, Mp, B, M_B, K_A, K_B)
+    Hp, Wp = Ap.shape
+    # padded-map row index = chi'_y + Hp - 1; B inside padded A: chi'_y in [H_B - Hp, 0]
+    rows = np.arange(H_B - Hp, 1) + Hp - 1
+    cols = np.arange(W_B - Wp, 1) + Wp - 1
+    if rows.size == 0 or cols.size == 0:
+        return None
+    sub_mi = ref["mi"][np.ix_(rows, cols)]
+    sub_n = ref["n"][np.ix_(rows, cols)]
+    idx, mi, n = gamma_argmax(sub_mi, sub_n, gamma)
+    i, j = divmod(idx, cols.size)
+    # chi' = padded-map index - (Hp - 1); chi (unpadded A) = chi' + p
+    dy = int(rows[i]) - (Hp - 1) + py
+    dx = int(cols[j]) - (Wp - 1) + px
+    win = (H_B - Hp + py, py, W_B - Wp + px, px)
+    return dict(dy=dy, dx=dx, mi=mi, n=n, window=win, sub_mi=sub_mi, sub_n=sub_n)
+
+
+def align_two_stage(A, M_A, B, M_B, K_A, K_B, n_grid, refine_u, gamma, padded=False, warp=None):
+    """Two-stage rigid alignment (Sec. 4): Alg. 1 over theta_t = 2 pi t / n_grid,
+    then over theta* + (2 u_i - 1) 2 pi / n_grid (theta* = the grid choice, 0 for
+    the identity), keeping I and T-hat across the stages (strict >).
+
+    Returns ((angle_idx, dy, dx, n, mi), theta); angle_idx = t for grid angles,
+    n_grid + i for refinement angle i, -1 for the identity.  ``warp(B, M_B,
+    theta) -> (B_theta, M_theta)`` replaces ``warp_nn`` when given (a test can
+    pass the warped images of another implementation, so that count parity does
+    not depend on rounding ties of the warp).
+    """
+    warp = warp or warp_nn
+
+    def per_angle(theta):
+        wB, wM = warp(B, M_B, theta)
+        if padded:
+            r = alg1_padded(A, M_A, wB, wM, K_A, K_B, gamma)
+            return r["dy"], r["dx"], r["n"], r["mi"]
+        ref = cmif(A, M_A, wB, wM, K_A, K_B)
+        idx, mi, n = gamma_argmax(ref["mi"], ref["n"], gamma)
+        C = ref["mi"].shape[1]
+        i, j = divmod(idx, C)
+        return i - (np.asarray(A).shape[0] - 1), j - (np.asarray(A).shape[1] - 1), n, mi
+
+    best, theta_best = (-1, 0, 0, 0, 0.0), 0.0
+    grid = [2.0 * np.pi * t / n_grid for t in range(n_grid)]
+    for t, th in enumerate(grid):
+        dy, dx, n, mi = per_angle(th)
+        if mi > best[4]:
+            best, theta_best = (t, dy, dx, n, mi), th
+    base = theta_best
+    for i, u in enumerate(refine_u):
+        th = base + (2.0 * float(u) - 1.0) * 2.0 * np.pi / n_grid
+        dy, dx, n, mi = per_angle(th)
+        if mi > best[4]:
+            best, theta_best = (n_grid + i, dy, dx, n, mi), th
+    return best, theta_best

@@ -22,6 +22,7 @@ __all__ = ["FP32", "SPLIT32", "FP64", "AUTO", "Plan", "Peak", "CmifError", "lib"
 FP32, SPLIT32, FP64, AUTO = 0, 1, 2, 3
 FLAG_DEBUG_COUNTS = 1
 FLAG_GRAPH = 2
+FLAG_WINDOW = 4
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "LABEL_RANGE", 3: "OOM", 4: "CUDA", 5: "PRECISION",
                 6: "TIMEOUT", 7: "NOT_IMPLEMENTED", 8: "UNSUPPORTED"}
 
@@ -47,8 +48,8 @@ class Peak(ctypes.Structure):
 EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_destroy", "cmif_plan_workspace_bytes",
            "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
            "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_rotate_nn", "cmif_align_rotations",
-           "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status", "cmif_batch_destroy",
-           "cmif_status_string"]
+           "cmif_align_two_stage", "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status",
+           "cmif_batch_destroy", "cmif_status_string"]
 
 _lib = None
 
@@ -74,6 +75,7 @@ def lib():
         L.cmif_compute_noalloc.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, D, P, P, P]
         L.cmif_rotate_nn.argtypes = [P, P, I, I, D, P, P, P]
         L.cmif_align_rotations.argtypes = [P, P, P, P, P, P, I, D, I, P, P, P]
+        L.cmif_align_two_stage.argtypes = [P, P, P, P, P, I, P, I, D, ctypes.POINTER(Peak), ctypes.POINTER(D), P]
         L.cmif_batch_create.argtypes = [ctypes.POINTER(P), I, P, I, U]
         L.cmif_compute_batch.argtypes = [P, P, P, P]
         L.cmif_batch_get_status.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
@@ -115,9 +117,10 @@ def _check(code, what):
 class Plan:
     """A CMIF plan for images H_A x W_A and H_B x W_B with K_A, K_B labels."""
 
-    def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False, graph=False):
+    def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False, graph=False, window=False):
         self._h = ctypes.c_void_p()
-        flags = (FLAG_DEBUG_COUNTS if debug_counts else 0) | (FLAG_GRAPH if graph else 0)
+        flags = (FLAG_DEBUG_COUNTS if debug_counts else 0) | (FLAG_GRAPH if graph else 0) | \
+            (FLAG_WINDOW if window else 0)
         _check(lib().cmif_plan_create_ex(ctypes.byref(self._h), H_A, W_A, H_B, W_B, K_A, K_B, precision, flags),
                "cmif_plan_create_ex")
         self.H_A, self.W_A, self.H_B, self.W_B, self.K_A, self.K_B = H_A, W_A, H_B, W_B, K_A, K_B
@@ -150,6 +153,15 @@ class Plan:
         _check(lib().cmif_align_rotations(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), ang.ctypes.data,
                                           len(ang), float(gamma), int(top_k), _ptr(topk_dev), _ptr(mi_maps),
                                           _stream(stream)), "cmif_align_rotations")
+
+    def align_two_stage(self, A, M_A, B, M_B, n_grid, refine_u, gamma, stream=None):
+        """Two-stage rigid alignment; returns ((angle_idx, dy, dx, n, mi), angle_rad); synchronises."""
+        u = np.ascontiguousarray(np.asarray(refine_u, dtype=np.float64))
+        pk, ang = Peak(), ctypes.c_double()
+        _check(lib().cmif_align_two_stage(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), int(n_grid),
+                                          u.ctypes.data if len(u) else None, len(u), float(gamma), ctypes.byref(pk),
+                                          ctypes.byref(ang), _stream(stream)), "cmif_align_two_stage")
+        return (pk.angle_idx, pk.dy, pk.dx, pk.n, pk.mi), ang.value
 
     def status(self):
         """(device status name, max residual, escalations) of the last call; synchronises."""
@@ -190,7 +202,7 @@ class Batch:
     """cmif_batch over pairs given as dicts with device tensors A, M_A, B, M_B, K_A, K_B,
     host angle lists `angles` (radians) and `gamma`."""
 
-    def __init__(self, pairs, precision=FP32, graph=True):
+    def __init__(self, pairs, precision=FP32, graph=True, window=False):
         self._keep = []
         descs = (PairDesc * len(pairs))()
         for i, p in enumerate(pairs):
@@ -204,7 +216,8 @@ class Batch:
         self._descs = descs
         self._h = ctypes.c_void_p()
         _check(lib().cmif_batch_create(ctypes.byref(self._h), len(pairs), ctypes.cast(descs, ctypes.c_void_p),
-                                       precision, FLAG_GRAPH if graph else 0), "cmif_batch_create")
+                                       precision, (FLAG_GRAPH if graph else 0) | (FLAG_WINDOW if window else 0)),
+               "cmif_batch_create")
         self.n = len(pairs)
 
     def run(self, results_dev, status_dev=None, stream=None):

@@ -59,7 +59,7 @@ struct cmif_plan_s {
     double* mibuf = nullptr;  // MI map used by cmif_align_rotations when the caller keeps no maps
     int32_t* wB = nullptr;    // rotated floating image (cmif_align_rotations)
     uint8_t* wM = nullptr;    // its rotated-support mask
-    void* peaks = nullptr;    // per-transform peaks, kMaxAngles records
+    void* peaks = nullptr;    // per-transform peaks, kMaxAngles records (+ 2 for the two-stage search)
     // host-buffer path staging (allocated lazily by cmif_compute_host)
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -200,12 +200,31 @@ void fill_io(PipeArgs<T>& a, const int32_t* A, const uint8_t* MA, const int32_t*
     a.st = st;
 }
 
+// Alg. 1's search window (Sec. 4: A zero-padded by ceil(|X_B|_i (1 - gamma)) along
+// each axis; X_S = the shifts that keep B's domain inside padded A's):
+//   chi_i in [|X_B|_i - |X_A|_i - p_i, p_i], intersected with the full range.
+// In output indices (row = chi_y + H_A - 1) that is [H_B - 1 - p_y, H_A - 1 + p_y].
+// Without CMIF_FLAG_WINDOW the window is the whole map.  Returns false when the
+// window is empty (B cannot fit inside padded A).
+bool call_geom(const cmif_plan p, double gamma, Geom* out) {
+    Geom g = p->g;
+    if (p->flags & CMIF_FLAG_WINDOW) {
+        const int py = (int)std::ceil(g.HB * (1.0 - gamma)), px = (int)std::ceil(g.WB * (1.0 - gamma));
+        g.r0 = std::max(0, g.HB - 1 - py);
+        g.r1 = std::min(g.R, g.HA + py);
+        g.c0 = std::max(0, g.WB - 1 - px);
+        g.c1 = std::min(g.C, g.WA + px);
+    }
+    *out = g;
+    return g.r0 < g.r1 && g.c0 < g.c1;
+}
+
 // One full map into (mi, n, counts); its status in p->st (reset here) is folded
 // into p->st_total.  stages32 selects the FP32 stages (A's transforms may be
 // reused across calls); an FP64 pass always recomputes everything.
-cmif_status compute_map(cmif_plan p, const int32_t* A, const uint8_t* MA, const int32_t* B, const uint8_t* MB,
-                        double* mi, int32_t* n, int32_t* counts, cudaStream_t s, unsigned stages32 = STAGE_ALL) {
-    const Geom& g = p->g;
+cmif_status compute_map(cmif_plan p, const Geom& g, const int32_t* A, const uint8_t* MA, const int32_t* B,
+                        const uint8_t* MB, double* mi, int32_t* n, int32_t* counts, cudaStream_t s,
+                        unsigned stages32 = STAGE_ALL) {
     cudaError_t e0 = cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s);
     if (e0 != cudaSuccess) return from_cuda(e0);
     if (p->prec == CMIF_FP32 || p->prec == CMIF_AUTO) {
@@ -261,7 +280,7 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     if (H_A < 1 || W_A < 1 || H_B < 1 || W_B < 1 || K_A < 1 || K_B < 1 || K_A > 64 || K_B > 64)
         return CMIF_ERR_INVALID_ARG;
     if ((long long)H_A * W_A > (1LL << 22) || (long long)H_B * W_B > (1LL << 22)) return CMIF_ERR_INVALID_ARG;
-    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH)) return CMIF_ERR_INVALID_ARG;
+    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW)) return CMIF_ERR_INVALID_ARG;
     if (prec != CMIF_FP32 && prec != CMIF_SPLIT32 && prec != CMIF_FP64 && prec != CMIF_AUTO) return CMIF_ERR_INVALID_ARG;
     Geom g{};
     g.HA = H_A; g.WA = W_A; g.HB = H_B; g.WB = W_B; g.KA = K_A; g.KB = K_B;
@@ -272,6 +291,7 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     if (g.P > 4096 || g.Q > 4096) return CMIF_ERR_UNSUPPORTED;
     g.Qh = g.Q / 2 + 1;
     g.Qs = (int)align_up((size_t)g.Qh, 4);
+    g.r0 = 0; g.r1 = g.R; g.c0 = 0; g.c1 = g.C;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return CMIF_ERR_CUDA;
     e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -315,7 +335,7 @@ size_t small_bytes_of(const cmif_plan p) {
     off = align_up(off + (size_t)g.R * g.C * sizeof(double), 256);
     off = align_up(off + (size_t)g.HB * g.WB * sizeof(int32_t), 256);
     off = align_up(off + (size_t)g.HB * g.WB, 256);
-    off = align_up(off + (size_t)kMaxAngles * sizeof(PeakRec), 256);
+    off = align_up(off + (size_t)(kMaxAngles + 2) * sizeof(PeakRec), 256);
     return off;
 }
 
@@ -339,7 +359,7 @@ cmif_status plan_carve(cmif_plan p, char* base) {
     p->mibuf = (double*)(base + off); off = align_up(off + (size_t)g.R * g.C * sizeof(double), 256);
     p->wB = (int32_t*)(base + off); off = align_up(off + (size_t)g.HB * g.WB * sizeof(int32_t), 256);
     p->wM = (uint8_t*)(base + off); off = align_up(off + (size_t)g.HB * g.WB, 256);
-    p->peaks = base + off; off = align_up(off + (size_t)kMaxAngles * sizeof(PeakRec), 256);
+    p->peaks = base + off; off = align_up(off + (size_t)(kMaxAngles + 2) * sizeof(PeakRec), 256);
     p->small_bytes = off;
     if (p->has32) { carve_workspace<float>(g, p->w32, base + off); off += workspace_bytes<float>(g, p->w32); }
     if (p->has64) { carve_workspace<double>(g, p->w64, base + off); off += workspace_bytes<double>(g, p->w64); }
@@ -397,7 +417,8 @@ cmif_status run_graph(cmif_plan p, cudaStream_t s, const std::vector<unsigned ch
 cmif_status align_core(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B, const uint8_t* M_B,
                        const double* angles, int n_angles, double gamma, int top_k, void* topk_dev, double* mi_maps,
                        cudaStream_t s) {
-    const Geom& g = plan->g;
+    Geom g;
+    if (!call_geom(plan, gamma, &g)) return CMIF_ERR_INVALID_ARG;
     const size_t RC = (size_t)g.R * g.C;
     cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), s);
     if (e != cudaSuccess) return from_cuda(e);
@@ -408,12 +429,15 @@ cmif_status align_core(cmif_plan plan, const int32_t* A, const uint8_t* M_A, con
         plan->prof.end(s);
         if (e != cudaSuccess) return from_cuda(e);
         double* mi = mi_maps ? mi_maps + (size_t)i * RC : plan->mibuf;
+        if (mi_maps && (g.r0 > 0 || g.r1 < g.R)) {  // rows outside the window are not computed: zero
+            e = cudaMemsetAsync(mi, 0, RC * sizeof(double), s);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
         const unsigned stages = (i == 0) ? STAGE_ALL : (STAGE_FWD_B | STAGE_PAIRS);
-        cmif_status cs = compute_map(plan, A, M_A, plan->wB, plan->wM, mi, plan->nbuf, nullptr, s, stages);
+        cmif_status cs = compute_map(plan, g, A, M_A, plan->wB, plan->wM, mi, plan->nbuf, nullptr, s, stages);
         if (cs != CMIF_OK) return cs;
         plan->prof.begin("peak", s);
-        e = launch_peak(mi, plan->nbuf, (long long)RC, plan->st, gamma, plan->parts, plan->nparts, g.HA, g.WA, g.C,
-                        i, peaks + i, s);
+        e = launch_peak(mi, plan->nbuf, g, plan->st, gamma, plan->parts, plan->nparts, i, peaks + i, s);
         plan->prof.end(s);
         if (e != cudaSuccess) return from_cuda(e);
     }
@@ -494,16 +518,24 @@ cmif_status cmif_compute(cmif_plan plan, const int32_t* A, const uint8_t* M_A, c
     key_add(key, 1);
     key_add(key, A); key_add(key, M_A); key_add(key, B); key_add(key, M_B);
     key_add(key, mi_map); key_add(key, nm); key_add(key, counts); key_add(key, gamma); key_add(key, peak_dev);
+    Geom g;
+    if (!call_geom(plan, gamma, &g)) return CMIF_ERR_INVALID_ARG;
     return run_graph(plan, s, key, [&](cudaStream_t cs) -> cmif_status {
         cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), cs);
         if (e != cudaSuccess) return from_cuda(e);
-        cmif_status st = compute_map(plan, A, M_A, B, M_B, mi_map, nm, counts, cs);
+        if (g.r0 > 0 || g.r1 < g.R) {  // rows outside the window are not computed: zero
+            const size_t RC = (size_t)g.R * g.C;
+            e = cudaMemsetAsync(mi_map, 0, RC * sizeof(double), cs);
+            if (e == cudaSuccess) e = cudaMemsetAsync(nm, 0, RC * sizeof(int32_t), cs);
+            if (e == cudaSuccess && counts)
+                e = cudaMemsetAsync(counts, 0, RC * sizeof(int32_t) * ((size_t)g.KA * g.KB + g.KA + g.KB), cs);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        cmif_status st = compute_map(plan, g, A, M_A, B, M_B, mi_map, nm, counts, cs);
         if (st != CMIF_OK) return st;
         if (peak_dev) {
-            const Geom& g = plan->g;
             plan->prof.begin("peak", cs);
-            e = launch_peak(mi_map, nm, (long long)g.R * g.C, plan->st, gamma, plan->parts, plan->nparts, g.HA,
-                            g.WA, g.C, 0, peak_dev, cs);
+            e = launch_peak(mi_map, nm, g, plan->st, gamma, plan->parts, plan->nparts, 0, peak_dev, cs);
             plan->prof.end(cs);
             if (e != cudaSuccess) return from_cuda(e);
         }
@@ -604,11 +636,63 @@ cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t
     });
 }
 
+cmif_status cmif_align_two_stage(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
+                                 const uint8_t* M_B, int n_grid, const double* refine_u_host, int n_refine,
+                                 double gamma, cmif_peak* best_host, double* best_angle_rad, void* stream) {
+    if (!plan || !A || !B || !best_host || !best_angle_rad) return CMIF_ERR_INVALID_ARG;
+    if (n_grid < 1 || n_grid > kMaxAngles || n_refine < 0 || n_refine > kMaxAngles || (n_refine > 0 && !refine_u_host))
+        return CMIF_ERR_INVALID_ARG;
+    for (int i = 0; i < n_refine; ++i)
+        if (!(refine_u_host[i] >= 0.0 && refine_u_host[i] <= 1.0)) return CMIF_ERR_INVALID_ARG;
+    DeviceGuard dg(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const double two_pi = 6.283185307179586476925286766559;
+    PeakRec* slot = reinterpret_cast<PeakRec*>(plan->peaks) + kMaxAngles;  // two records past the per-angle ones
+    // (i) grid search over theta_t = 2 pi t / |Omega|
+    std::vector<double> grid(n_grid);
+    for (int t = 0; t < n_grid; ++t) grid[t] = two_pi * t / n_grid;
+    cmif_status st = cmif_align_rotations(plan, A, M_A, B, M_B, grid.data(), n_grid, gamma, 1,
+                                          reinterpret_cast<cmif_peak*>(slot), nullptr, stream);
+    if (st != CMIF_OK) return st;
+    PeakRec best{};
+    cudaError_t e = cudaMemcpyAsync(&best, slot, sizeof(PeakRec), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    // Alg. 1 keeps the identity (I = 0) unless some transform has I_T > 0
+    if (!(best.angle_idx >= 0 && best.mi > 0.0)) best = {-1, 0, 0, 0, 0.0};
+    double best_theta = best.angle_idx >= 0 ? grid[best.angle_idx] : 0.0;
+    // (ii) random refinement: theta + (2u - 1) 2 pi / |Omega|, continuing Alg. 1's (I, T-hat)
+    if (n_refine > 0) {
+        std::vector<double> ref(n_refine);
+        const double half = two_pi / n_grid;
+        for (int i = 0; i < n_refine; ++i) ref[i] = best_theta + (2.0 * refine_u_host[i] - 1.0) * half;
+        st = cmif_align_rotations(plan, A, M_A, B, M_B, ref.data(), n_refine, gamma, 1,
+                                  reinterpret_cast<cmif_peak*>(slot + 1), nullptr, stream);
+        if (st != CMIF_OK) return st;
+        PeakRec r2{};
+        e = cudaMemcpyAsync(&r2, slot + 1, sizeof(PeakRec), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return from_cuda(e);
+        if (r2.angle_idx >= 0 && r2.mi > best.mi) {
+            best_theta = ref[r2.angle_idx];
+            best = r2;
+            best.angle_idx += n_grid;
+        }
+    }
+    best_host->angle_idx = best.angle_idx;
+    best_host->dy = best.dy;
+    best_host->dx = best.dx;
+    best_host->n = best.n;
+    best_host->mi = best.mi;
+    *best_angle_rad = best_theta;
+    return CMIF_OK;
+}
+
 cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc* descs, cmif_precision prec,
                               unsigned flags) {
     if (!out) return CMIF_ERR_INVALID_ARG;
     *out = nullptr;
-    if (n_pairs < 1 || !descs || (flags & ~CMIF_FLAG_GRAPH)) return CMIF_ERR_INVALID_ARG;
+    if (n_pairs < 1 || !descs || (flags & ~(CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW))) return CMIF_ERR_INVALID_ARG;
     for (int i = 0; i < n_pairs; ++i) {
         const cmif_pair_desc& d = descs[i];
         if (!d.A || !d.B || d.n_angles < 0 || d.n_angles > kMaxAngles || (d.n_angles > 0 && !d.angles_rad))
@@ -634,7 +718,7 @@ cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc
         cmif_plan p = new (std::nothrow) cmif_plan_s();
         if (!p) return fail(CMIF_ERR_OOM);
         b->plans.push_back(p);
-        cmif_status st = plan_init(p, d.H_A, d.W_A, d.H_B, d.W_B, d.K_A, d.K_B, prec, 0u);
+        cmif_status st = plan_init(p, d.H_A, d.W_A, d.H_B, d.W_B, d.K_A, d.K_B, prec, flags & CMIF_FLAG_WINDOW);
         if (st != CMIF_OK) return fail(st);
         max_bytes = std::max(max_bytes, plan_bytes(p));
     }
@@ -673,10 +757,11 @@ cmif_status cmif_compute_batch(cmif_batch batch, cmif_peak* results_dev, int32_t
             if (d.n_angles == 0) {
                 e = cudaMemsetAsync(p->st_total, 0, sizeof(DevStatus), cs);
                 if (e != cudaSuccess) return from_cuda(e);
-                st = compute_map(p, d.A, d.M_A, d.B, d.M_B, p->mibuf, p->nbuf, nullptr, cs);
+                Geom g;
+                if (!call_geom(p, d.gamma, &g)) return CMIF_ERR_INVALID_ARG;
+                st = compute_map(p, g, d.A, d.M_A, d.B, d.M_B, p->mibuf, p->nbuf, nullptr, cs);
                 if (st != CMIF_OK) return st;
-                e = launch_peak(p->mibuf, p->nbuf, (long long)p->g.R * p->g.C, p->st, d.gamma, p->parts, p->nparts,
-                                p->g.HA, p->g.WA, p->g.C, 0, results_dev + i, cs);
+                e = launch_peak(p->mibuf, p->nbuf, g, p->st, d.gamma, p->parts, p->nparts, 0, results_dev + i, cs);
                 if (e != cudaSuccess) return from_cuda(e);
             } else {
                 st = align_core(p, d.A, d.M_A, d.B, d.M_B, batch->angles[i].data(), d.n_angles, d.gamma, 1,

@@ -27,6 +27,10 @@ struct Geom {
     int P, Q;            // transform sizes (powers of two >= R, C)
     int Qh;              // Q/2 + 1 half-spectrum columns
     int Qs;              // padded row stride (complex elements) of row-major spectra
+    // Search window of the call: output rows [r0, r1) are computed, and X_S is
+    // rows [r0, r1) x columns [c0, c1) (max N and the peak are taken over it).
+    // The whole map unless Alg. 1's padded window is on.
+    int r0, r1, c0, c1;
 };
 
 constexpr float kResidualGuard = 0.25f;  // a count whose pre-rounding residual reaches this is not trusted

@@ -293,8 +293,8 @@ struct PairColsCfg {
 template <typename T, int P>
 __global__ void __launch_bounds__(PairColsCfg<T, P>::THREADS, PairColsCfg<T, P>::MIN_BLOCKS)
 k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA, int KB, int Qh, int HA, int HB,
-            int Rout, int Qs, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st, int conditional,
-            int* __restrict__ work_ctr) {
+            int Rout, int Qs, int r0, int r1, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st,
+            int conditional, int* __restrict__ work_ctr) {
     using C = PairColsCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB, NQ = C::NQ;
@@ -389,7 +389,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             for (int q = threadIdx.x; q < P * PPR; q += C::THREADS) {
                 const int row = q / PPR, h = q % PPR;
                 const int orow = circ_to_out(row, P, HA, HB - 1);
-                if (orow < 0 || (TPB > 4 && kx0 + 2 * h >= Qs)) continue;
+                if (orow < r0 || orow >= r1 || (TPB > 4 && kx0 + 2 * h >= Qs)) continue;
                 const int sw = (row >> C::SWZ) & (TPB - 1);
                 float4 pv = reinterpret_cast<const float4*>(xbuf)[row * PPR + (h ^ (sw >> 1))];
                 if (sw & 1) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
@@ -400,7 +400,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             for (int q = threadIdx.x; q < P * TPB; q += C::THREADS) {
                 const int row = q / TPB, c = q % TPB;
                 const int orow = circ_to_out(row, P, HA, HB - 1);
-                if (orow < 0 || kx0 + c >= Qs) continue;
+                if (orow < r0 || orow >= r1 || kx0 + c >= Qs) continue;
                 const int sw = (row >> C::SWZ) & (TPB - 1);
                 yp[(size_t)orow * Qs + kx0 + c] = xbuf[(size_t)row * TPB + (c ^ sw)];
             }
@@ -461,7 +461,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
     float res_max = 0.f;
     int row_max_n = 0;
 
-    for (int row = blockIdx.x; row < Rout; row += gridDim.x) {
+    for (int row = g.r0 + blockIdx.x; row < g.r1; row += gridDim.x) {
         long long S[U];
         float CA[U];
         int N[U];
@@ -567,7 +567,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
             const size_t o = (size_t)row * Cout + cidx;
             mi_map[o] = mi_finish(S[u], N[u]);
             if (n_map) n_map[o] = N[u];
-            row_max_n = max(row_max_n, N[u]);
+            if (cidx >= g.c0 && cidx < g.c1) row_max_n = max(row_max_n, N[u]);
         }
         __syncthreads();
     }

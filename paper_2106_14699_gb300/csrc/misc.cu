@@ -17,12 +17,18 @@ __device__ __forceinline__ bool better(double m1, long long i1, double m2, long 
     return m1 > m2 || (m1 == m2 && i1 < i2);
 }
 
-__global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __restrict__ n, long long RC,
-                               const DevStatus* __restrict__ st, double gamma, PeakPart* __restrict__ parts) {
+// Scans the search window rows [r0, r1) x columns [c0, c1) of the (R x Cout) maps;
+// indices stay row-major map indices (ties: lowest).
+__global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __restrict__ n, int Cout, int r0, int r1,
+                               int c0, int c1, const DevStatus* __restrict__ st, double gamma,
+                               PeakPart* __restrict__ parts) {
     const double thr = gamma * (double)st->max_n;
+    const int wc = c1 - c0;
+    const long long cnt = (long long)(r1 - r0) * wc;
     double bm = -INFINITY;
     long long bi = -1;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < RC; i += (long long)gridDim.x * blockDim.x) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x) {
+        const long long i = (long long)(r0 + t / wc) * Cout + c0 + t % wc;
         if ((double)n[i] >= thr) {
             const double m = mi[i];
             if (bi < 0 || better(m, i, bm, bi)) { bm = m; bi = i; }
@@ -191,10 +197,10 @@ __global__ void k_finalize(DevStatus* st, int slot_if_escalated, int slot_defaul
     }
 }
 
-cudaError_t launch_peak(const double* mi, const int32_t* n, long long RC, const DevStatus* st, double gamma,
-                        PeakPart* parts, int nparts, int HA, int WA, int Cout, int angle_idx, void* peak_out,
-                        cudaStream_t s) {
-    k_peak_partial<<<nparts, 256, 0, s>>>(mi, n, RC, st, gamma, parts);
+cudaError_t launch_peak(const double* mi, const int32_t* n, const Geom& g, const DevStatus* st, double gamma,
+                        PeakPart* parts, int nparts, int angle_idx, void* peak_out, cudaStream_t s) {
+    const int HA = g.HA, WA = g.WA, Cout = g.C;
+    k_peak_partial<<<nparts, 256, 0, s>>>(mi, n, Cout, g.r0, g.r1, g.c0, g.c1, st, gamma, parts);
     k_peak_final<<<1, 256, 0, s>>>(parts, nparts, mi, n, HA, WA, Cout, angle_idx, peak_out);
     return cudaGetLastError();
 }

@@ -95,6 +95,7 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     g.HA = H_A; g.WA = W_A; g.HB = H_B; g.WB = W_B; g.KA = K_A; g.KB = K_B;
     g.R = H_A + H_B - 1;
     g.C = W_A + W_B - 1;
+    g.r0 = 0; g.r1 = g.R; g.c0 = 0; g.c1 = g.C;  // the whole map
     g.P = 16;
     while (g.P < g.R) g.P <<= 1;
     g.Q = 16;
@@ -161,8 +162,7 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     e = launch_finalize(st, 0, 0, s);
     if (e != cudaSuccess) return to_status(e);
     if (peak_dev) {
-        e = launch_peak(mi_map, nm, (long long)g.R * g.C, st, gamma, reinterpret_cast<PeakPart*>(b + oParts), nparts,
-                        g.HA, g.WA, g.C, 0, peak_dev, s);
+        e = launch_peak(mi_map, nm, g, st, gamma, reinterpret_cast<PeakPart*>(b + oParts), nparts, 0, peak_dev, s);
         if (e != cudaSuccess) return to_status(e);
     }
     if (status_dev) {

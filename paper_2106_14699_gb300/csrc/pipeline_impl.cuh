@@ -71,8 +71,8 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
     const int grid = (int)(items < slots ? items : slots);
     e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KA, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, a.Y, a.tw, a.st,
-                                        a.conditional, a.work_ctr);
+    kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KA, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, g.r0, g.r1, a.Y, a.tw,
+                                        a.st, a.conditional, a.work_ctr);
     return cudaGetLastError();
 }
 

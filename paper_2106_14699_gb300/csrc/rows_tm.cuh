@@ -189,12 +189,12 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
         }
         pending = true;
     };
-    if (blockIdx.x < Rout && team < npairs) issue(blockIdx.x, team);
+    if (g.r0 + (int)blockIdx.x < g.r1 && team < npairs) issue(g.r0 + blockIdx.x, team);
 
     float res_max = 0.f;
     int row_max_n = 0;
     bool aborted = false;
-    for (int row = blockIdx.x; row < Rout && !aborted; row += gridDim.x) {
+    for (int row = g.r0 + blockIdx.x; row < g.r1 && !aborted; row += gridDim.x) {
         long long S[U];
         float CA[U];
         int N[U];
@@ -245,7 +245,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
             if (act && !pending) {
                 int nrow = row, npair = pair + NT;
                 if (npair >= npairs) { nrow = row + gridDim.x; npair = team; }
-                if (nrow < Rout) issue(nrow, npair);
+                if (nrow < g.r1) issue(nrow, npair);
             }
 #pragma unroll
             for (int k = 0; k < M; ++k) {
@@ -390,7 +390,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 const size_t o = (size_t)row * Cout + cidx;
                 mi_map[o] = mi_finish(S[u], N[u]);
                 if (n_map) n_map[o] = N[u];
-                row_max_n = max(row_max_n, N[u]);
+                if (cidx >= g.c0 && cidx < g.c1) row_max_n = max(row_max_n, N[u]);
             }
         }
         __syncthreads();

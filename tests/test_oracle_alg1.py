@@ -1,0 +1,105 @@
+"""Pins of the oracle's Alg. 1 extensions: the ZERO-PAD search window
+(Alg. 1 line 2, Sec. 4) and the two-stage rigid search (Sec. 4).
+
+Each pin ties the oracle to something other than itself: the unpadded direct
+CMIF at the same displacement (padding with mask 0 adds no pixel pairs), the
+overlap-area bound of the gamma gate for full masks, the label entropy of a
+template cut out of A (MI(chi*) = H(B), Sec. 2), and the strict-greater rule
+of Alg. 1 across the two stages.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+scipy_stats = pytest.importorskip("scipy.stats")
+
+
+def _labels(rng, H, W, K):
+    A = rng.integers(0, K, (H, W)).astype(np.int32)
+    A[: H // 2, : W // 2] = 0          # some structure so that maps have a clear peak
+    A[H // 2:, W // 2:] = K - 1
+    return A
+
+
+@pytest.mark.parametrize("shapes", [((10, 12), (10, 12)), ((13, 11), (7, 6)), ((9, 9), (9, 5))])
+@pytest.mark.parametrize("gamma", [0.0, 0.3, 0.75])
+def test_padded_window_equals_unpadded_cmif(shapes, gamma):
+    """Inside X_S the padded pair's CMIF and N equal the unpadded pair's at the same chi."""
+    rng = np.random.default_rng(5)
+    (HA, WA), (HB, WB) = shapes
+    A = _labels(rng, HA, WA, 3)
+    B = rng.integers(0, 3, (HB, WB)).astype(np.int32)
+    MB = (rng.random((HB, WB)) > 0.2).astype(np.uint8)
+    r = oracle.alg1_padded(A, None, B, MB, 3, 3, gamma)
+    full = oracle.cmif(A, None, B, MB, 3, 3)
+    dy_lo, dy_hi, dx_lo, dx_hi = r["window"]
+    for i, dy in enumerate(range(dy_lo, dy_hi + 1)):
+        for j, dx in enumerate(range(dx_lo, dx_hi + 1)):
+            if -(HA - 1) <= dy <= HB - 1 and -(WA - 1) <= dx <= WB - 1:
+                assert r["sub_n"][i, j] == full["n"][dy + HA - 1, dx + WA - 1]
+                assert abs(r["sub_mi"][i, j] - full["mi"][dy + HA - 1, dx + WA - 1]) < 1e-12
+            else:
+                assert r["sub_n"][i, j] == 0      # no overlap at all
+    assert full["n"][r["dy"] + HA - 1, r["dx"] + WA - 1] == r["n"]
+
+
+@pytest.mark.parametrize("gamma", [0.25, 0.5, 0.8])
+def test_padded_equals_gated_full_map_for_full_masks(gamma):
+    """Full masks, equal sizes: N(chi) = (H - |dy|)(W - |dx|) >= gamma H W forces
+    |dy| <= H (1 - gamma) <= p_y, so the window excludes no shift that passes the
+    gate, and max N (at chi = 0) lies inside it: both forms of Alg. 1 agree."""
+    rng = np.random.default_rng(9)
+    A = _labels(rng, 14, 12, 4)
+    B = np.roll(A, (2, -3), axis=(0, 1))
+    B[rng.random(B.shape) < 0.2] = 1
+    r = oracle.alg1_padded(A, None, B, None, 4, 4, gamma)
+    full = oracle.cmif(A, None, B, None, 4, 4)
+    idx, mi, n = oracle.gamma_argmax(full["mi"], full["n"], gamma)
+    dy, dx = divmod(idx, full["mi"].shape[1])
+    assert (r["dy"], r["dx"], r["n"]) == (dy - 13, dx - 11, n)
+    assert r["mi"] == mi
+
+
+def test_template_cut_out_of_reference():
+    """B = A[y0:y0+h, x0:x0+w]: at chi = (-y0, -x0) every B pixel meets its own
+    source, the joint histogram is diagonal and MI = H(B) (the label entropy of
+    B, scipy); no other shift in X_S can exceed H(B)."""
+    rng = np.random.default_rng(21)
+    A = rng.integers(0, 5, (24, 30)).astype(np.int32)
+    y0, x0, h, w = 7, 11, 9, 10
+    B = A[y0:y0 + h, x0:x0 + w].copy()
+    r = oracle.alg1_padded(A, None, B, None, 5, 5, 0.9)
+    hb = scipy_stats.entropy(np.bincount(B.ravel(), minlength=5), base=2)
+    assert (r["dy"], r["dx"]) == (-y0, -x0)
+    assert abs(r["mi"] - hb) < 1e-12 and r["n"] == h * w
+    # template matching: X_S spans every placement of B inside A plus p of overhang
+    dy_lo, dy_hi, dx_lo, dx_hi = r["window"]
+    assert dy_lo <= -(24 - h) and dy_hi >= 0 and dx_lo <= -(30 - w) and dx_hi >= 0
+
+
+def test_two_stage_rules():
+    rng = np.random.default_rng(3)
+    A = _labels(rng, 16, 16, 3)
+    B, MB = oracle.warp_nn(A, None, math.radians(50.0))
+    n_grid = 8
+    # no refinement draws: stage (i) alone = Alg. 1 over the grid
+    best, theta = oracle.align_two_stage(A, None, B, MB, 3, 3, n_grid, [], 0.5)
+    per = []
+    for t in range(n_grid):
+        wB, wM = oracle.warp_nn(B, MB, 2 * math.pi * t / n_grid)
+        ref = oracle.cmif(A, None, wB, wM, 3, 3)
+        per.append((ref["mi"], ref["n"]))
+    b1, _ = oracle.align(per, 0.5)
+    assert best[0] == b1[0] and best[4] == b1[2] and theta == 2 * math.pi * b1[0] / n_grid
+    # u = 1/2 re-evaluates the grid winner itself: equal I_T, strict > keeps stage (i)
+    best2, theta2 = oracle.align_two_stage(A, None, B, MB, 3, 3, n_grid, [0.5], 0.5)
+    assert best2 == best and theta2 == theta
+    # refinement never lowers I, and a refined winner lies within one grid step
+    u = [0.05, 0.3, 0.62, 0.9, 0.77]
+    best3, theta3 = oracle.align_two_stage(A, None, B, MB, 3, 3, n_grid, u, 0.5)
+    assert best3[4] >= best[4]
+    if best3[0] >= n_grid:
+        assert abs(theta3 - theta) <= 2 * math.pi / n_grid + 1e-12
