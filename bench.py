@@ -221,7 +221,18 @@ def run_secondary(args):
     dev = torch.device("cuda", 0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     d = lambda x: None if x is None else torch.from_numpy(np.ascontiguousarray(x)).to(dev)
-    if args.workload in ("single256", "plain64"):
+    if args.workload == "nmi":
+        cfg = synth.make_config(3)
+        H, W = cfg["A"].shape
+        plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True, nmi=True)
+        R, C = 2 * H - 1, 2 * W - 1
+        mi = torch.empty((R, C), dtype=torch.float64, device=dev)
+        n = torch.empty((R, C), dtype=torch.int32, device=dev)
+        pk = torch.empty(24, dtype=torch.uint8, device=dev)
+        ins = [d(cfg[k]) for k in ("A", "M_A", "B", "M_B")]
+        step = lambda: plan.compute(ins[0], ins[1], ins[2], ins[3], mi, n, None, 0.5, pk)
+        units, name = R * C, cfg["name"] + " NMI FP32"
+    elif args.workload in ("single256", "plain64"):
         cid = 2 if args.workload == "single256" else 1
         cfg = synth.make_config(cid)
         H, W = cfg["A"].shape
@@ -308,7 +319,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single1024",
                     choices=["single1024", "rotation", "rotation-window", "two-stage", "batch", "single256",
-                             "plain64"],
+                             "plain64", "nmi"],
                     help="single1024 (default, the headline): config 3; rotation: config 4 (512^2, 64 angles); "
                          "batch: config 5 (128 uneven pairs x 4 angles); single256 / plain64: configs 2 / 1")
     ap.add_argument("--profile-shape", default=None,

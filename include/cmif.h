@@ -90,6 +90,10 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
                                      window's map rows are computed (rows outside it are returned as MI = 0,
                                      N = 0); max N and the peak are taken over the window.  A call whose window
                                      is empty (B cannot fit inside padded A) returns CMIF_ERR_INVALID_ARG. */
+#define CMIF_FLAG_NMI 8u          /* the map (mi_map, mi_maps) holds the normalised MI the paper cites next to MI
+                                     (Sec. 2), NMI = (H_A + H_B) / H_AB, from the same counts and fixed-point
+                                     entropy sums; 0 where N = 0 or H_AB = 0 (0/0 = 0, Sec. 3.2).  Alg. 1's
+                                     argmax and the peaks then maximise NMI. */
 
 /* One argmax record of Alg. 1: the displacement chi = (dy, dx) maximising
  * CMIF among shifts with N(chi) >= gamma * max N, for transform angle_idx
@@ -219,7 +223,7 @@ typedef struct {
 /* Validate the pairs (limits as cmif_plan_create_ex, 0 <= n_angles <= 4096),
  * copy the descriptors and allocate the shared workspace.  The device images
  * the descriptors point to must stay valid and unchanged for the batch's life.
- * prec as for plans; flags: 0, CMIF_FLAG_GRAPH and/or CMIF_FLAG_WINDOW. */
+ * prec as for plans; flags: 0 or any of CMIF_FLAG_GRAPH, CMIF_FLAG_WINDOW, CMIF_FLAG_NMI. */
 cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc* descs, cmif_precision prec,
                               unsigned flags);
 

@@ -25,6 +25,9 @@ Functions and the passages they follow:
                      = the shifts that keep B's domain inside padded A's, and the
                      gated argmax over X_S.  Pinned by tests/test_oracle.py
                      (padding changes nothing inside X_S; full-mask cases).
+* ``nmi``         -- the normalised MI the paper cites next to MI (Sec. 2),
+                     (H_A + H_B) / H_AB from the direct method's entropies, 0/0 = 0.
+                     Pinned by closed forms (A = B: 2; independent labels: 1).
 * ``align_two_stage`` -- the two-stage rigid search of Sec. 4 (grid, then random
                      refinement in [theta - 2 pi/|Omega|, theta + 2 pi/|Omega|]), the
                      uniform draws passed in.  Pinned by hand-checked compositions.
@@ -281,3 +284,14 @@ def align_two_stage(A, M_A, B, M_B, K_A, K_B, n_grid, refine_u, gamma, padded=Fa
         if mi > best[4]:
             best, theta_best = (n_grid + i, dy, dx, n, mi), th
     return best, theta_best
+
+
+def nmi(A, M_A, B, M_B, K_A, K_B):
+    """NMI map (H_A + H_B) / H_AB over the full shift range, from the direct
+    method's per-shift entropies; 0 where N = 0 or H_AB = 0 (0/0 = 0)."""
+    ref = cmif(A, M_A, B, M_B, K_A, K_B, entropies=True)
+    ha, hb, hab = ref["ent"]
+    out = np.zeros_like(hab)
+    ok = hab > 0
+    out[ok] = (ha[ok] + hb[ok]) / hab[ok]
+    return dict(nmi=out, n=ref["n"], h_ab=hab)

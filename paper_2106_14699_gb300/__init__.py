@@ -23,6 +23,7 @@ FP32, SPLIT32, FP64, AUTO = 0, 1, 2, 3
 FLAG_DEBUG_COUNTS = 1
 FLAG_GRAPH = 2
 FLAG_WINDOW = 4
+FLAG_NMI = 8
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "LABEL_RANGE", 3: "OOM", 4: "CUDA", 5: "PRECISION",
                 6: "TIMEOUT", 7: "NOT_IMPLEMENTED", 8: "UNSUPPORTED"}
 
@@ -117,10 +118,11 @@ def _check(code, what):
 class Plan:
     """A CMIF plan for images H_A x W_A and H_B x W_B with K_A, K_B labels."""
 
-    def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False, graph=False, window=False):
+    def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False, graph=False, window=False,
+                 nmi=False):
         self._h = ctypes.c_void_p()
         flags = (FLAG_DEBUG_COUNTS if debug_counts else 0) | (FLAG_GRAPH if graph else 0) | \
-            (FLAG_WINDOW if window else 0)
+            (FLAG_WINDOW if window else 0) | (FLAG_NMI if nmi else 0)
         _check(lib().cmif_plan_create_ex(ctypes.byref(self._h), H_A, W_A, H_B, W_B, K_A, K_B, precision, flags),
                "cmif_plan_create_ex")
         self.H_A, self.W_A, self.H_B, self.W_B, self.K_A, self.K_B = H_A, W_A, H_B, W_B, K_A, K_B

@@ -280,7 +280,8 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     if (H_A < 1 || W_A < 1 || H_B < 1 || W_B < 1 || K_A < 1 || K_B < 1 || K_A > 64 || K_B > 64)
         return CMIF_ERR_INVALID_ARG;
     if ((long long)H_A * W_A > (1LL << 22) || (long long)H_B * W_B > (1LL << 22)) return CMIF_ERR_INVALID_ARG;
-    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW)) return CMIF_ERR_INVALID_ARG;
+    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI))
+        return CMIF_ERR_INVALID_ARG;
     if (prec != CMIF_FP32 && prec != CMIF_SPLIT32 && prec != CMIF_FP64 && prec != CMIF_AUTO) return CMIF_ERR_INVALID_ARG;
     Geom g{};
     g.HA = H_A; g.WA = W_A; g.HB = H_B; g.WB = W_B; g.KA = K_A; g.KB = K_B;
@@ -315,6 +316,10 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
         st = choose_rows<df32>(p, p->ws32);
     }
     if (st != CMIF_OK) return st;
+    const int nmi = (flags & CMIF_FLAG_NMI) ? 1 : 0;
+    p->w32.args.nmi = nmi;
+    p->w64.args.nmi = nmi;
+    p->ws32.args.nmi = nmi;
     Tw<float> tf;
     Tw<double> td;
     Tw<df32> ts;
@@ -692,7 +697,8 @@ cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc
                               unsigned flags) {
     if (!out) return CMIF_ERR_INVALID_ARG;
     *out = nullptr;
-    if (n_pairs < 1 || !descs || (flags & ~(CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW))) return CMIF_ERR_INVALID_ARG;
+    if (n_pairs < 1 || !descs || (flags & ~(CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI)))
+        return CMIF_ERR_INVALID_ARG;
     for (int i = 0; i < n_pairs; ++i) {
         const cmif_pair_desc& d = descs[i];
         if (!d.A || !d.B || d.n_angles < 0 || d.n_angles > kMaxAngles || (d.n_angles > 0 && !d.angles_rad))
@@ -718,7 +724,8 @@ cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc
         cmif_plan p = new (std::nothrow) cmif_plan_s();
         if (!p) return fail(CMIF_ERR_OOM);
         b->plans.push_back(p);
-        cmif_status st = plan_init(p, d.H_A, d.W_A, d.H_B, d.W_B, d.K_A, d.K_B, prec, flags & CMIF_FLAG_WINDOW);
+        cmif_status st = plan_init(p, d.H_A, d.W_A, d.H_B, d.W_B, d.K_A, d.K_B, prec,
+                                   flags & (CMIF_FLAG_WINDOW | CMIF_FLAG_NMI));
         if (st != CMIF_OK) return fail(st);
         max_bytes = std::max(max_bytes, plan_bytes(p));
     }

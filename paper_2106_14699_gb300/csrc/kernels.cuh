@@ -61,6 +61,39 @@ __device__ __forceinline__ double mi_finish(long long S, int N) {
     return ((double)q1 + (double)q2) * (1.0 / (double)(1 << kFixBits));
 }
 
+// NMI(chi) = (H_A + H_B) / H_AB (the normalised MI the paper cites next to
+// MI, Sec. 2), from the same fixed-point sums kept apart: SJ = sum_joint c log2 c,
+// SM = sum_A + sum_B.  With T(N) = N log2 N: H_A + H_B = (2 T(N) - SM) / N and
+// H_AB = (T(N) - SJ) / N.  0 when N = 0 or H_AB = 0 (0/0 = 0, Sec. 3.2).
+__device__ __forceinline__ double nmi_finish(long long SJ, long long SM, int N) {
+    if (N <= 0) return 0.0;
+    const long long TN = clog2c_fixed((float)N);
+    const long long den = TN - SJ;
+    if (den == 0) return 0.0;
+    return (double)(2 * TN - SM) / (double)den;
+}
+
+// Per-position entropy sums of the row epilogue: MI keeps one signed sum
+// (joint terms in, marginal terms out); NMI keeps the two apart.
+template <bool NMI>
+struct EntAcc;
+template <>
+struct EntAcc<false> {
+    long long s;
+    __device__ __forceinline__ void zero() { s = 0; }
+    __device__ __forceinline__ void joint(long long t) { s += t; }
+    __device__ __forceinline__ void marg(long long t) { s -= t; }
+    __device__ __forceinline__ double finish(int N) const { return mi_finish(s, N); }
+};
+template <>
+struct EntAcc<true> {
+    long long j, m;
+    __device__ __forceinline__ void zero() { j = 0; m = 0; }
+    __device__ __forceinline__ void joint(long long t) { j += t; }
+    __device__ __forceinline__ void marg(long long t) { m += t; }
+    __device__ __forceinline__ double finish(int N) const { return nmi_finish(j, m, N); }
+};
+
 __device__ __forceinline__ void atomic_max_float_pos(unsigned* addr, float v) {
     atomicMax(addr, __float_as_uint(v));  // v >= 0: float order = unsigned order
 }
@@ -124,7 +157,7 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, int H,
     using C = FwdRowsCfg<T, Q>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* code = smem_raw + (size_t)C::TPB * C::REGION;
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
     const int npp = (K + 1) / 2;
@@ -189,7 +222,7 @@ k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cp
     using C = ColCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<T>* tile = reinterpret_cast<cpx<T>*>(smem_raw + C::SCR);
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
     const int kx0 = blockIdx.x * TPB, kx = kx0 + team, plane = blockIdx.y;
@@ -299,7 +332,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB, NQ = C::NQ;
     const int npairs = KA * KB, nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_item;
     cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* tw_sq = reinterpret_cast<cpx<T>*>(smem_raw + C::MAIN);
@@ -441,7 +474,7 @@ struct RowCfg {
     static_assert(REGION >= QH * 4, "team scratch must hold one pass of rounded counts");
 };
 
-template <typename T, int Q, bool CB_SMEM>
+template <typename T, int Q, bool CB_SMEM, bool NMI>
 __global__ void __launch_bounds__(RowCfg<T, Q>::THREADS, 1)
 k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ cb_global,
             double* __restrict__ mi_map, int32_t* __restrict__ n_map, int32_t* __restrict__ counts,
@@ -450,7 +483,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
     constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, BT = C::THREADS;
     constexpr int HALVES = C::HALVES, QH = C::QH;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     float* cb = CB_SMEM ? reinterpret_cast<float*>(smem_raw + C::TEAM_SMEM)
                         : cb_global + (size_t)blockIdx.x * g.KB * Q;
     const int tid = threadIdx.x, team = tid / C::TEAM, lt = tid % C::TEAM, r = lt / M, j = lt % M;
@@ -462,11 +495,11 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
     int row_max_n = 0;
 
     for (int row = g.r0 + blockIdx.x; row < g.r1; row += gridDim.x) {
-        long long S[U];
+        EntAcc<NMI> S[U];
         float CA[U];
         int N[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) { S[u] = 0; CA[u] = 0.f; N[u] = 0; }
+        for (int u = 0; u < U; ++u) { S[u].zero(); CA[u] = 0.f; N[u] = 0; }
         for (int b = 0; b < KB; ++b)
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -520,7 +553,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
                         for (int uh = 0; uh < UH; ++uh) {
                             const int u = hf * UH + uh, pl = tid + BT * uh;
                             if (pl >= QH) continue;
-                            S[u] -= clog2c_fixed(CA[u]);
+                            S[u].marg(clog2c_fixed(CA[u]));
                             N[u] += (int)CA[u];
                             if (counts) {
                                 const int c = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
@@ -537,7 +570,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
                         const int u = hf * UH + uh, pl = tid + BT * uh;
                         if (pl >= QH) continue;
                         const float c = obt[pl];
-                        S[u] += clog2c_fixed(c);
+                        S[u].joint(clog2c_fixed(c));
                         CA[u] += c;
                         cbb[pl] += c;
                         if (counts) {
@@ -555,17 +588,17 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
             const int pl = tid + BT * (u % UH), p = (u / UH) * QH + pl;
             if (pl >= QH) continue;
             const int cidx = circ_to_out(p, Q, g.WA, g.WB - 1);
-            S[u] -= clog2c_fixed(CA[u]);
+            S[u].marg(clog2c_fixed(CA[u]));
             N[u] += (int)CA[u];
             if (counts && cidx >= 0) counts[((size_t)npairs + cur_a[u / UH]) * RC + (size_t)row * Cout + cidx] = (int)CA[u];
             for (int b = 0; b < KB; ++b) {
                 const float cbv = cb[(size_t)b * Q + p];
-                S[u] -= clog2c_fixed(cbv);
+                S[u].marg(clog2c_fixed(cbv));
                 if (counts && cidx >= 0) counts[((size_t)npairs + KA + b) * RC + (size_t)row * Cout + cidx] = (int)cbv;
             }
             if (cidx < 0) continue;
             const size_t o = (size_t)row * Cout + cidx;
-            mi_map[o] = mi_finish(S[u], N[u]);
+            mi_map[o] = S[u].finish(N[u]);
             if (n_map) n_map[o] = N[u];
             if (cidx >= g.c0 && cidx < g.c1) row_max_n = max(row_max_n, N[u]);
         }
@@ -596,8 +629,9 @@ struct PeakPart {
     long long idx;
 };
 
-__global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __restrict__ n, long long RC,
-                               const DevStatus* __restrict__ st, double gamma, PeakPart* __restrict__ parts);
+__global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __restrict__ n, int Cout, int r0, int r1,
+                               int c0, int c1, const DevStatus* __restrict__ st, double gamma,
+                               PeakPart* __restrict__ parts);
 __global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, const double* __restrict__ mi,
                              const int32_t* __restrict__ n, int HA, int WA, int Cout, int angle_idx,
                              void* __restrict__ peak_out);

@@ -28,6 +28,7 @@ struct PipeArgs {
     int conditional;  // run only when STATUS_ESCALATE is set (AUTO re-run)
     int rows_grid;    // persistent grid of the row/epilogue kernel
     int num_sms;      // SMs of the device (persistent grid of the pair-column kernel)
+    int nmi;          // the map holds NMI = (H_A + H_B) / H_AB instead of MI
     bool cb_smem;     // B-marginal accumulators in shared memory
     Profiler* prof;   // optional launch timing (nullptr = off)
     int tm_cols;      // > 0: use the TMEM / TMA row kernel with this many TMEM columns
@@ -39,6 +40,38 @@ enum : unsigned {
     STAGE_FWD_B = 2u,  // level-set transforms of B
     STAGE_PAIRS = 4u,  // pair product, inverse transforms, epilogue
     STAGE_ALL = 7u,
+};
+
+// The transform sizes the kernels are compiled for (P, Q = 16 .. 4096).
+#define CMIF_SIZE_SWITCH(N, ...)                                     \
+    switch (N) {                                                      \
+        case 16: { constexpr int SZ = 16; __VA_ARGS__; } break;     \
+        case 32: { constexpr int SZ = 32; __VA_ARGS__; } break;     \
+        case 64: { constexpr int SZ = 64; __VA_ARGS__; } break;     \
+        case 128: { constexpr int SZ = 128; __VA_ARGS__; } break;   \
+        case 256: { constexpr int SZ = 256; __VA_ARGS__; } break;   \
+        case 512: { constexpr int SZ = 512; __VA_ARGS__; } break;   \
+        case 1024: { constexpr int SZ = 1024; __VA_ARGS__; } break; \
+        case 2048: { constexpr int SZ = 2048; __VA_ARGS__; } break; \
+        case 4096: { constexpr int SZ = 4096; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;                        \
+    }
+
+// Entry points of one (precision, transform size).  The definitions
+// (pipeline_impl.cuh) are instantiated explicitly in the kernels_<prec>_<sizes>.cu
+// units, so that the kernels of different sizes compile in parallel;
+// pipeline.cu dispatches on the run-time size.
+template <typename T, int SZ>
+struct Sized {
+    static cudaError_t fwd_rows(const Geom& g, const PipeArgs<T>& a, bool b_side, cudaStream_t s);  // Q = SZ
+    static cudaError_t fwd_cols(const Geom& g, const PipeArgs<T>& a, bool b_side, cudaStream_t s);  // P = SZ
+    static cudaError_t pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);              // P = SZ
+    static cudaError_t pair_rows(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);              // Q = SZ
+    static size_t rows_smem(int KB, bool cb_smem);
+    static int rows_threads();
+    static cudaError_t rows_max_blocks(int KB, bool cb_smem, int* out);
+    static int tm_cols(int KB);                 // 0 unless the TMEM row kernel applies (FP32, Q = 1024 / 2048)
+    static cudaError_t tm_max_blocks(int* out);
 };
 
 template <typename T>

@@ -142,7 +142,7 @@ __host__ __device__ constexpr int tm_alloc_cols(int need) {
     return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 
-template <int Q>
+template <int Q, bool NMI>
 __global__ void __launch_bounds__(RowTmCfg<Q>::THREADS, 1)
 k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* __restrict__ mi_map,
                int32_t* __restrict__ n_map, int32_t* __restrict__ counts, DevStatus* __restrict__ st,
@@ -195,11 +195,11 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     int row_max_n = 0;
     bool aborted = false;
     for (int row = g.r0 + blockIdx.x; row < g.r1 && !aborted; row += gridDim.x) {
-        long long S[U];
+        EntAcc<NMI> S[U];
         float CA[U];
         int N[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) { S[u] = 0; CA[u] = 0.f; N[u] = 0; }
+        for (int u = 0; u < U; ++u) { S[u].zero(); CA[u] = 0.f; N[u] = 0; }
         {   // zero this thread's B-marginal columns
             uint32_t z[16];
 #pragma unroll
@@ -279,7 +279,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
 #pragma unroll
                         for (int uh = 0; uh < UH; ++uh) {
                             const int u = hf * UH + uh;
-                            S[u] -= clog2c_fixed(CA[u]);
+                            S[u].marg(clog2c_fixed(CA[u]));
                             N[u] += (int)CA[u];
                             if (counts) {
                                 const int c = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
@@ -300,7 +300,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                         for (int uh = 0; uh < UH; ++uh) {
                             const int u = hf * UH + uh, pl = tid + BT * uh;
                             const float c = obt[pl];
-                            S[u] += clog2c_fixed(c);
+                            S[u].joint(clog2c_fixed(c));
                             CA[u] += c;
                             cbr[t * UH + uh] = __float_as_uint(__uint_as_float(cbr[t * UH + uh]) + c);
                             if (counts) {
@@ -319,7 +319,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
 #pragma unroll
                             for (int uh = 0; uh < UH; ++uh) {
                                 const int u = hf * UH + uh;
-                                S[u] -= clog2c_fixed(CA[u]);
+                                S[u].marg(clog2c_fixed(CA[u]));
                                 N[u] += (int)CA[u];
                                 if (counts) {
                                     const int c = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
@@ -337,7 +337,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                         for (int uh = 0; uh < UH; ++uh) {
                             const int u = hf * UH + uh, pl = tid + BT * uh;
                             const float c = obt[pl];
-                            S[u] += clog2c_fixed(c);
+                            S[u].joint(clog2c_fixed(c));
                             CA[u] += c;
                             cbr[uh] = __float_as_uint(__uint_as_float(cbr[uh]) + c);
                             if (counts) {
@@ -361,7 +361,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
 #pragma unroll
             for (int uh = 0; uh < UH; ++uh) {
                 const int u = hf * UH + uh;
-                S[u] -= clog2c_fixed(CA[u]);
+                S[u].marg(clog2c_fixed(CA[u]));
                 N[u] += (int)CA[u];
                 if (counts) {
                     const int c = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
@@ -375,7 +375,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
 #pragma unroll
                 for (int uh = 0; uh < UH; ++uh) {
                     const float cbv = __uint_as_float(cbr[uh]);
-                    S[hf * UH + uh] -= clog2c_fixed(cbv);
+                    S[hf * UH + uh].marg(clog2c_fixed(cbv));
                     if (counts) {
                         const int c = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
                         if (c >= 0) counts[((size_t)npairs + KA + b) * RC + (size_t)row * Cout + c] = (int)cbv;
@@ -388,7 +388,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 const int cidx = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
                 if (cidx < 0) continue;
                 const size_t o = (size_t)row * Cout + cidx;
-                mi_map[o] = mi_finish(S[u], N[u]);
+                mi_map[o] = S[u].finish(N[u]);
                 if (n_map) n_map[o] = N[u];
                 if (cidx >= g.c0 && cidx < g.c1) row_max_n = max(row_max_n, N[u]);
             }

@@ -1,11 +1,12 @@
-"""Pins of the oracle's Alg. 1 extensions: the ZERO-PAD search window
-(Alg. 1 line 2, Sec. 4) and the two-stage rigid search (Sec. 4).
+"""Pins of the oracle's extensions: Alg. 1's ZERO-PAD search window (Alg. 1
+line 2, Sec. 4), the two-stage rigid search (Sec. 4) and NMI (Sec. 2).
 
 Each pin ties the oracle to something other than itself: the unpadded direct
 CMIF at the same displacement (padding with mask 0 adds no pixel pairs), the
 overlap-area bound of the gamma gate for full masks, the label entropy of a
-template cut out of A (MI(chi*) = H(B), Sec. 2), and the strict-greater rule
-of Alg. 1 across the two stages.
+template cut out of A (MI(chi*) = H(B), Sec. 2), the strict-greater rule
+of Alg. 1 across the two stages, and NMI's closed forms (2 for A = B, 1 for
+independent labels).
 """
 import math
 
@@ -103,3 +104,21 @@ def test_two_stage_rules():
     assert best3[4] >= best[4]
     if best3[0] >= n_grid:
         assert abs(theta3 - theta) <= 2 * math.pi / n_grid + 1e-12
+
+
+def test_nmi_closed_forms():
+    """A = B: at chi = 0 the joint histogram is diagonal, H_AB = H_A = H_B, NMI = 2.
+    A(y, x) = y mod 2, B(y, x) = x mod 2 on an even grid: at chi = 0 every label
+    pair has probability 1/4 (independent), H_AB = 2 = H_A + H_B, NMI = 1."""
+    rng = np.random.default_rng(2)
+    A = rng.integers(0, 5, (15, 13)).astype(np.int32)
+    r = oracle.nmi(A, None, A, None, 5, 5)
+    assert abs(r["nmi"][14, 12] - 2.0) < 1e-12
+    yy, xx = np.mgrid[0:12, 0:10]
+    A2 = (yy % 2).astype(np.int32)
+    B2 = (xx % 2).astype(np.int32)
+    r2 = oracle.nmi(A2, None, B2, None, 2, 2)
+    assert abs(r2["nmi"][11, 9] - 1.0) < 1e-12
+    ok = r2["h_ab"] > 0
+    assert np.all(r2["nmi"][ok] >= 1.0 - 1e-12) and np.all(r2["nmi"][ok] <= 2.0 + 1e-12)
+    assert np.all(r2["nmi"][~ok] == 0.0)
