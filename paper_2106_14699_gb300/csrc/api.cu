@@ -100,7 +100,9 @@ cmif_status choose_rows(cmif_plan p, Workspace<T>& w) {
         }
     }
     if (w.args.tm_cols > 0) {
-        w.cb_smem = true;
+        // the TMEM kernel keeps the B-marginals in TMEM; calls that ask for the debug
+        // count maps run the generic kernel, whose B-marginals may need the global slice
+        w.cb_smem = !(p->flags & CMIF_FLAG_DEBUG_COUNTS) || rows_smem_bytes<T>(g.Q, g.KB, true) <= 200 * 1024;
     } else {
         const size_t smem_cb = rows_smem_bytes<T>(g.Q, g.KB, true);
         w.cb_smem = smem_cb <= 200 * 1024;

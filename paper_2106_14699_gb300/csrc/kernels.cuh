@@ -34,9 +34,11 @@ __device__ __forceinline__ long long clog2c_fixed(float c) {
     const float m = __int_as_float((bits & 0x7FFFFF) | 0x3F800000);
     const float lm = __log2f(m);
     // (e << F) + round(lm * 2^F), e = exponent of c, with the constants folded
-    int L = ((bits >> 23) << kFixBits) + __float_as_int(fmaf(lm, (float)(1 << kFixBits), 12582912.0f)) -
-            (0x4B400000 + (127 << kFixBits));
-    L = bits <= 0x3F800000 ? 0 : L;  // c in {0, 1}: c log c = 0 (Sec. 3.2: 0 log 0 = 0)
+    const int L = ((bits >> 23) << kFixBits) + __float_as_int(fmaf(lm, (float)(1 << kFixBits), 12582912.0f)) -
+                  (0x4B400000 + (127 << kFixBits));
+    // c = 0: ci = 0, so the term is 0 (Sec. 3.2: 0 log 0 = 0) whatever L is.  c = 1:
+    // m = 1 and e = 0, so L = round(log2(1) * 2^F) = 0.  T stays one fixed function
+    // of c, so equal counts still cancel exactly between joint and marginal sums.
     return (long long)ci * (long long)L;
 }
 

@@ -67,11 +67,11 @@ template <typename T, int Q, bool NMI>
 static cudaError_t launch_pair_rows_v(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     using C = RowCfg<T, Q>;
     if constexpr (sizeof(T) == 4 && (Q == 1024 || Q == 2048)) {
-        if (a.tm_cols > 0) {
+        if (a.tm_cols > 0 && !a.counts) {  // debug count maps: the generic kernel below
             auto kern = k_pair_rows_tm<Q, NMI>;
             cudaError_t e = ensure_smem(kern, RowTmCfg<Q>::SMEM);
             if (e != cudaSuccess) return e;
-            kern<<<a.rows_grid, RowTmCfg<Q>::THREADS, RowTmCfg<Q>::SMEM, s>>>(a.Y, g, a.tw, a.mi, a.n, a.counts, a.st,
+            kern<<<a.rows_grid, RowTmCfg<Q>::THREADS, RowTmCfg<Q>::SMEM, s>>>(a.Y, g, a.tw, a.mi, a.n, a.st,
                                                                              a.tm_cols);
             return cudaGetLastError();
         }

@@ -5,7 +5,8 @@
 //     owning thread, and
 //   * each team's next Y row fetched into shared memory by a TMA bulk copy
 //     (cp.async.bulk + mbarrier) while the current round computes.
-// Same arithmetic and outputs as k_pair_rows (kernels.cuh).
+// Same arithmetic and outputs as k_pair_rows (kernels.cuh), except the debug
+// count maps: a call that asks for them runs k_pair_rows.
 #pragma once
 #include "kernels.cuh"
 
@@ -145,7 +146,7 @@ __host__ __device__ constexpr int tm_alloc_cols(int need) {
 template <int Q, bool NMI>
 __global__ void __launch_bounds__(RowTmCfg<Q>::THREADS, 1)
 k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* __restrict__ mi_map,
-               int32_t* __restrict__ n_map, int32_t* __restrict__ counts, DevStatus* __restrict__ st,
+               int32_t* __restrict__ n_map, DevStatus* __restrict__ st,
                int tm_cols) {
     using C = RowTmCfg<Q>;
     constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, BT = C::THREADS, QH = C::QH;
@@ -159,7 +160,6 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     __shared__ int s_abort;
 
     const int KA = g.KA, KB = g.KB, npairs = KA * KB, Rout = g.R, Cout = g.C, Qs = g.Qs;
-    const size_t RC = (size_t)Rout * Cout;
     cpx<float>* tw_sq = reinterpret_cast<cpx<float>*>(smem_raw + C::OFF_TW);
     cpx<float>* twq_c2r = tw_sq + C::NQ;
     cpx<float>* tw_pre = twq_c2r + L;
@@ -281,10 +281,6 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                             const int u = hf * UH + uh;
                             S[u].marg(clog2c_fixed(CA[u]));
                             N[u] += (int)CA[u];
-                            if (counts) {
-                                const int c = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
-                                if (c >= 0) counts[((size_t)npairs + cur_a[hf]) * RC + (size_t)row * Cout + c] = (int)CA[u];
-                            }
                             CA[u] = 0.f;
                         }
                         cur_a[hf] = a0;
@@ -303,10 +299,6 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                             S[u].joint(clog2c_fixed(c));
                             CA[u] += c;
                             cbr[t * UH + uh] = __float_as_uint(__uint_as_float(cbr[t * UH + uh]) + c);
-                            if (counts) {
-                                const int cc = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
-                                if (cc >= 0) counts[(size_t)(base + t) * RC + (size_t)row * Cout + cc] = (int)c;
-                            }
                         }
                     }
                     if constexpr (UH == 2) tmem_st<32>(tcol, cbr);
@@ -321,10 +313,6 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                                 const int u = hf * UH + uh;
                                 S[u].marg(clog2c_fixed(CA[u]));
                                 N[u] += (int)CA[u];
-                                if (counts) {
-                                    const int c = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
-                                    if (c >= 0) counts[((size_t)npairs + cur_a[hf]) * RC + (size_t)row * Cout + c] = (int)CA[u];
-                                }
                                 CA[u] = 0.f;
                             }
                             cur_a[hf] = a;
@@ -340,10 +328,6 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                             S[u].joint(clog2c_fixed(c));
                             CA[u] += c;
                             cbr[uh] = __float_as_uint(__uint_as_float(cbr[uh]) + c);
-                            if (counts) {
-                                const int cc = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
-                                if (cc >= 0) counts[(size_t)(base + t) * RC + (size_t)row * Cout + cc] = (int)c;
-                            }
                         }
                         tmem_st<UH>(tcol + (uint32_t)(b * UH), cbr);
                         tmem_wait_st();
@@ -363,10 +347,6 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 const int u = hf * UH + uh;
                 S[u].marg(clog2c_fixed(CA[u]));
                 N[u] += (int)CA[u];
-                if (counts) {
-                    const int c = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
-                    if (c >= 0) counts[((size_t)npairs + cur_a[hf]) * RC + (size_t)row * Cout + c] = (int)CA[u];
-                }
             }
             for (int b = 0; b < KB; ++b) {
                 uint32_t cbr[UH];
@@ -376,10 +356,6 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 for (int uh = 0; uh < UH; ++uh) {
                     const float cbv = __uint_as_float(cbr[uh]);
                     S[hf * UH + uh].marg(clog2c_fixed(cbv));
-                    if (counts) {
-                        const int c = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
-                        if (c >= 0) counts[((size_t)npairs + KA + b) * RC + (size_t)row * Cout + c] = (int)cbv;
-                    }
                 }
             }
 #pragma unroll
