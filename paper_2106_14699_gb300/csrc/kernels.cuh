@@ -17,6 +17,7 @@
 //                K_A*K_B count maps never reach global memory.
 //   peak       : the gamma-gated argmax of Alg. 1 for one map.
 #pragma once
+#include <type_traits>
 #include <cstdint>
 #include "common.h"
 #include "fft.cuh"
@@ -307,7 +308,7 @@ struct PairColsCfg {
     static constexpr size_t XBUF = (size_t)TPB * P * sizeof(cpx<T>);
     static constexpr size_t FFT = (size_t)TPB * G::SCRATCH;
     static constexpr size_t MAIN = (XBUF > FFT ? XBUF : FFT);
-    static constexpr int TW_N = R > 1 ? P : 0;  // combine twiddles W_P^k
+    static constexpr int TW_N = R == 2 ? P / 2 : (R > 2 ? P : 0);  // combine twiddles W_P^k
     static constexpr size_t SMEM = MAIN + (size_t)(NQ + TW_N) * sizeof(cpx<T>);
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;
 };
@@ -387,7 +388,25 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
         team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
         if (threadIdx.x == 0) s_item = next;  // read by all after the tile barrier below
         cpx<T>* tx = xbuf + (size_t)team * P;  // this team's R sub-transforms
-        if constexpr (R > 1) {
+        if constexpr (R == 2) {
+            // X[k] = E_0[k] + W^k E_1[k], X[k + NQ] = E_0[k] - W^k E_1[k] (W = W_P, inverse
+            // direction, W^NQ = -1).  Lane j of both groups holds the same k = j + M k2:
+            // group 1 forms W^k E_1[k] once, the groups swap values through shared memory.
+            __syncthreads();  // every group is done with its transpose scratch (aliases xbuf)
+            if (r == 1) {
+#pragma unroll
+                for (int k2 = 0; k2 < M; ++k2)
+                    v[brev(k2, M)] = cmul(v[brev(k2, M)], twl<+1>(tw_n, j + M * k2));
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) tx[r * NQ + j + M * k2] = v[brev(k2, M)];
+            __syncthreads();
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const int k = j + M * k2;
+                v[brev(k2, M)] = r == 0 ? v[brev(k2, M)] + tx[NQ + k] : tx[k] - v[brev(k2, M)];
+            }
+        } else if constexpr (R > 2) {
             __syncthreads();  // every group is done with its transpose scratch (aliases xbuf)
 #pragma unroll
             for (int k2 = 0; k2 < M; ++k2) tx[r * NQ + j + M * k2] = v[brev(k2, M)];
@@ -548,40 +567,48 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
                     ob[m] = make_float2((float)z.x, (float)z.y);
                 }
                 __syncthreads();
-                int a = a0, b = b0;
-                for (int t = 0; t < nt; ++t) {
-                    if (a != cur_a[hf]) {  // uniform: the A-marginal of label cur_a is complete
+                // the round's accumulation, compiled twice: with the debug count maps
+                // and without (no per-count test of the counts pointer)
+                auto accumulate = [&](auto dbg) {
+                    constexpr bool DBG = decltype(dbg)::value;
+                    int a = a0, b = b0;
+                    for (int t = 0; t < nt; ++t) {
+                        if (a != cur_a[hf]) {  // uniform: the A-marginal of label cur_a is complete
+#pragma unroll
+                            for (int uh = 0; uh < UH; ++uh) {
+                                const int u = hf * UH + uh, pl = tid + BT * uh;
+                                if (pl >= QH) continue;
+                                S[u].marg(clog2c_fixed(CA[u]));
+                                N[u] += (int)CA[u];
+                                if constexpr (DBG) {
+                                    const int c = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
+                                    if (c >= 0)
+                                        counts[((size_t)npairs + cur_a[hf]) * RC + (size_t)row * Cout + c] = (int)CA[u];
+                                }
+                                CA[u] = 0.f;
+                            }
+                            cur_a[hf] = a;
+                        }
+                        const float* obt = reinterpret_cast<const float*>(smem_raw + (size_t)t * C::REGION);
+                        float* cbb = cb + (size_t)b * Q + hf * QH;
 #pragma unroll
                         for (int uh = 0; uh < UH; ++uh) {
                             const int u = hf * UH + uh, pl = tid + BT * uh;
                             if (pl >= QH) continue;
-                            S[u].marg(clog2c_fixed(CA[u]));
-                            N[u] += (int)CA[u];
-                            if (counts) {
-                                const int c = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
-                                if (c >= 0) counts[((size_t)npairs + cur_a[hf]) * RC + (size_t)row * Cout + c] = (int)CA[u];
+                            const float c = obt[pl];
+                            S[u].joint(clog2c_fixed(c));
+                            CA[u] += c;
+                            cbb[pl] += c;
+                            if constexpr (DBG) {
+                                const int cc = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
+                                if (cc >= 0) counts[(size_t)(base + t) * RC + (size_t)row * Cout + cc] = (int)c;
                             }
-                            CA[u] = 0.f;
                         }
-                        cur_a[hf] = a;
+                        if (++b == KB) { b = 0; ++a; }
                     }
-                    const float* obt = reinterpret_cast<const float*>(smem_raw + (size_t)t * C::REGION);
-                    float* cbb = cb + (size_t)b * Q + hf * QH;
-#pragma unroll
-                    for (int uh = 0; uh < UH; ++uh) {
-                        const int u = hf * UH + uh, pl = tid + BT * uh;
-                        if (pl >= QH) continue;
-                        const float c = obt[pl];
-                        S[u].joint(clog2c_fixed(c));
-                        CA[u] += c;
-                        cbb[pl] += c;
-                        if (counts) {
-                            const int cc = circ_to_out(hf * QH + pl, Q, g.WA, g.WB - 1);
-                            if (cc >= 0) counts[(size_t)(base + t) * RC + (size_t)row * Cout + cc] = (int)c;
-                        }
-                    }
-                    if (++b == KB) { b = 0; ++a; }
-                }
+                };
+                if (counts) accumulate(std::true_type{});
+                else accumulate(std::false_type{});
             }
             __syncthreads();  // the next round's transforms overwrite the scratch read above
         }
