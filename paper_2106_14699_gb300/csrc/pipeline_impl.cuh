@@ -8,9 +8,13 @@
 
 namespace cmif {
 
+// Opt the kernel in to `bytes` of dynamic shared memory.  Without the attribute,
+// static plus dynamic shared memory must stay within 48 KB, so a kernel with a
+// little static memory (a work index, an abort flag) fails to launch just below
+// 48 KB of dynamic memory: set it from 32 KB up.
 template <typename K>
 static cudaError_t ensure_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes <= 32 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
