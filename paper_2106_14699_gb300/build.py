@@ -54,6 +54,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     objdir = os.path.join(LIBDIR, "obj")
     os.makedirs(objdir, exist_ok=True)
     srcs = _sources()
+    keep = {os.path.basename(src) + ".o" for src in srcs}
+    for name in os.listdir(objdir):  # objects of sources that no longer exist
+        if name.endswith(".o") and name not in keep:
+            os.remove(os.path.join(objdir, name))
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")

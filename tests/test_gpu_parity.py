@@ -224,3 +224,54 @@ def test_host_buffer_entry_point(cm):
     assert float(np.abs(mi - ref["mi"]).max()) <= MI_TOL
     assert (pk.dy, pk.dx) == tuple(cfg["shift"])
     plan.close()
+
+
+def test_max_label_count_exact(cm):
+    """K_A = K_B = 64 (the largest accepted): 4096 label pairs; exact counts on the
+    whole map, FP32 and FP64."""
+    rng = np.random.default_rng(64)
+    A, MA, B, MB = _rand(rng, 23, 31, 19, 27, 64, 64, p0=0.1)
+    for prec in (cm.FP32, cm.FP64):
+        check_exact(cm, A, MA, B, MB, 64, 64, prec, gamma=0.3)
+
+
+def test_max_k_wide_rows_global_b_marginals(cm):
+    """K_B = 64 at Q = 2048: the B-marginals (64 x 2048 floats) fit neither TMEM
+    nor shared memory, so the row kernel keeps them in its global slice."""
+    rng = np.random.default_rng(65)
+    A, MA, B, MB = _rand(rng, 9, 600, 7, 610, 5, 64, p0=0.05)
+    g = run_gpu(cm, A, MA, B, MB, 5, 64, cm.FP32, counts=False, gamma=0.2)
+    ref = oracle.cmif(A, MA, B, MB, 5, 64)
+    assert g["status"][0] == "OK", g["status"]
+    np.testing.assert_array_equal(g["n"], ref["n"])
+    assert float(np.abs(g["mi"] - ref["mi"]).max()) <= MI_TOL
+
+
+def test_extreme_aspect_max_row_transform(cm):
+    """1 x 2048 rows: P = 16 (the smallest transform), Q = 4096 (the largest)."""
+    rng = np.random.default_rng(66)
+    A, MA, B, MB = _rand(rng, 1, 2048, 1, 2048, 3, 3, p0=0.1)
+    check_exact(cm, A, MA, B, MB, 3, 3, cm.FP32, gamma=0.5)
+
+
+def test_max_transform_size_sampled(cm):
+    """2048^2 pair (the largest plan: P = Q = 4096), K = 4, AUTO precision: N
+    exact on the whole map (all-ones masks: closed form), MI and N at sampled
+    shifts vs the oracle, residual guard satisfied after any escalation."""
+    rng = np.random.default_rng(67)
+    H = 2048
+    A = rng.integers(0, 4, (H, H)).astype(np.int32)
+    A[: H // 2, : H // 3] = 1
+    B = np.roll(A, (37, -101), axis=(0, 1))
+    B[rng.random(B.shape) < 0.1] = 2
+    g = run_gpu(cm, A, None, B, None, 4, 4, cm.AUTO, counts=False, gamma=0.5)
+    assert g["status"][0] == "OK", g["status"]
+    d = np.arange(2 * H - 1) - (H - 1)
+    np.testing.assert_array_equal(g["n"], np.outer(H - np.abs(d), H - np.abs(d)))
+    dys, dxs = _sample_shifts(rng, H, H, H, H, 40, extra=[(37, -101)])
+    ref = oracle.cmif_at(A, None, B, None, 4, 4, dys, dxs)
+    np.testing.assert_array_equal(g["n"][dys + H - 1, dxs + H - 1], ref["n"])
+    err = float(np.abs(g["mi"][dys + H - 1, dxs + H - 1] - ref["mi"]).max())
+    print(f"[mi-error] 2048^2 K=4 AUTO sampled max|dMI|={err:.3e} status={g['status']}")
+    assert err <= MI_TOL, err
+    assert tuple(g["peak"][1:3]) == (37, -101)
