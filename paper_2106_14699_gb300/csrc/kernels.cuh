@@ -439,15 +439,34 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             // h ^ (sw >> 1), swapped when sw is odd.  Qs and kx0 are even, so a
             // piece is either wholly inside the row (kx0 + 2h < Qs) or wholly out;
             // for TPB <= 4 always inside (Qs is a multiple of 4).
-            constexpr int PPR = TPB / 2;
-            for (int q = threadIdx.x; q < P * PPR; q += C::THREADS) {
-                const int row = q / PPR, h = q % PPR;
-                const int orow = circ_to_out(row, P, HA, HB - 1);
-                if (orow < r0 || orow >= r1 || (TPB > 4 && kx0 + 2 * h >= Qs)) continue;
-                const int sw = (row >> C::SWZ) & (TPB - 1);
-                float4 pv = reinterpret_cast<const float4*>(xbuf)[row * PPR + (h ^ (sw >> 1))];
-                if (sw & 1) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
-                reinterpret_cast<float4*>(yp + (size_t)orow * Qs + kx0)[h] = pv;
+            constexpr int PPR = TPB / 2, ROWS = C::THREADS / PPR;
+            if constexpr (ROWS % (TPB << C::SWZ) == 0) {
+                // A thread keeps its piece h and visits rows row0 + i * ROWS; ROWS is a
+                // multiple of the swizzle period, so the swizzle is fixed per thread.
+                const int h = threadIdx.x % PPR, row0 = threadIdx.x / PPR;
+                const int sw = (row0 >> C::SWZ) & (TPB - 1);
+                const bool swap_halves = sw & 1;
+                if (TPB <= 4 || kx0 + 2 * h < Qs) {
+                    const float4* src = reinterpret_cast<const float4*>(xbuf) + row0 * PPR + (h ^ (sw >> 1));
+                    float4* dst = reinterpret_cast<float4*>(yp + kx0) + h;
+                    for (int row = row0; row < P; row += ROWS, src += ROWS * PPR) {
+                        const int orow = circ_to_out(row, P, HA, HB - 1);
+                        if (orow < r0 || orow >= r1) continue;
+                        float4 pv = *src;
+                        if (swap_halves) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
+                        dst[(size_t)orow * (Qs / 2)] = pv;
+                    }
+                }
+            } else {
+                for (int q = threadIdx.x; q < P * PPR; q += C::THREADS) {
+                    const int row = q / PPR, h = q % PPR;
+                    const int orow = circ_to_out(row, P, HA, HB - 1);
+                    if (orow < r0 || orow >= r1 || kx0 + 2 * h >= Qs) continue;
+                    const int sw = (row >> C::SWZ) & (TPB - 1);
+                    float4 pv = reinterpret_cast<const float4*>(xbuf)[row * PPR + (h ^ (sw >> 1))];
+                    if (sw & 1) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
+                    reinterpret_cast<float4*>(yp + (size_t)orow * Qs + kx0)[h] = pv;
+                }
             }
         } else {
             // one complex per lane, adjacent lanes on adjacent columns of a row
