@@ -502,7 +502,9 @@ struct RowCfg {
     static constexpr int L = Q / 2;
     using G = TeamGeom<T, L>;
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
-    static constexpr int BT_TARGET = sizeof(T) == 4 ? 512 : 256;
+    // FP32: one thread per position of a pass (Q / 2), between one warp and 512
+    // threads, so that no thread idles in the epilogue; smaller blocks share an SM.
+    static constexpr int BT_TARGET = sizeof(T) == 4 ? (Q / 2 >= 512 ? 512 : (Q / 2 >= 32 ? Q / 2 : 32)) : 256;
     static constexpr int NT = TEAM >= BT_TARGET ? 1 : BT_TARGET / TEAM;
     static constexpr int THREADS = NT * TEAM;
     static constexpr int HALVES = sizeof(T) == 4 ? 2 : 1;
@@ -511,11 +513,12 @@ struct RowCfg {
     static constexpr int U = HALVES * UH;
     static constexpr int REGION = G::SCRATCH;                  // >= QH floats
     static constexpr size_t TEAM_SMEM = (size_t)NT * REGION;
+    static constexpr int MIN_BLOCKS = sizeof(T) == 4 && THREADS < 512 ? 512 / THREADS : 1;  // <= 128 registers
     static_assert(REGION >= QH * 4, "team scratch must hold one pass of rounded counts");
 };
 
 template <typename T, int Q, bool CB_SMEM, bool NMI>
-__global__ void __launch_bounds__(RowCfg<T, Q>::THREADS, 1)
+__global__ void __launch_bounds__(RowCfg<T, Q>::THREADS, RowCfg<T, Q>::MIN_BLOCKS)
 k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ cb_global,
             double* __restrict__ mi_map, int32_t* __restrict__ n_map, int32_t* __restrict__ counts,
             DevStatus* __restrict__ st, int prec_slot, int conditional) {
