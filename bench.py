@@ -221,7 +221,21 @@ def run_secondary(args):
     dev = torch.device("cuda", 0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     d = lambda x: None if x is None else torch.from_numpy(np.ascontiguousarray(x)).to(dev)
-    if args.workload == "nmi":
+    if args.workload == "swmi":
+        cfg = synth.make_config(2)
+        H, W = cfg["A"].shape
+        plan = cm.Plan(H, W, H, W, 16, 16, cm.FP64, graph=True, weighted=True)
+        R, C = 2 * H - 1, 2 * W - 1
+        rng = np.random.default_rng(12)
+        wa = d(rng.random((H, W)) * cfg["M_A"])
+        wb = d(rng.random((H, W)) * cfg["M_B"])
+        mi = torch.empty((R, C), dtype=torch.float64, device=dev)
+        nw = torch.empty((R, C), dtype=torch.float64, device=dev)
+        pk = torch.empty(24, dtype=torch.uint8, device=dev)
+        A, B = d(cfg["A"]), d(cfg["B"])
+        step = lambda: plan.compute_weighted(A, wa, B, wb, mi, nw, 0.5, pk)
+        units, name = R * C, cfg["name"] + " SWMI FP64"
+    elif args.workload == "nmi":
         cfg = synth.make_config(3)
         H, W = cfg["A"].shape
         plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True, nmi=True)
@@ -319,7 +333,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single1024",
                     choices=["single1024", "rotation", "rotation-window", "two-stage", "batch", "single256",
-                             "plain64", "nmi"],
+                             "plain64", "nmi", "swmi"],
                     help="single1024 (default, the headline): config 3; rotation: config 4 (512^2, 64 angles); "
                          "batch: config 5 (128 uneven pairs x 4 angles); single256 / plain64: configs 2 / 1")
     ap.add_argument("--profile-shape", default=None,

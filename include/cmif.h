@@ -90,6 +90,8 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
                                      window's map rows are computed (rows outside it are returned as MI = 0,
                                      N = 0); max N and the peak are taken over the window.  A call whose window
                                      is empty (B cannot fit inside padded A) returns CMIF_ERR_INVALID_ARG. */
+#define CMIF_FLAG_WEIGHTED 16u    /* the plan computes spatially weighted MI with cmif_compute_weighted (needs
+                                     CMIF_FP64; not with CMIF_FLAG_NMI or CMIF_FLAG_DEBUG_COUNTS) */
 #define CMIF_FLAG_NMI 8u          /* the map (mi_map, mi_maps) holds the normalised MI the paper cites next to MI
                                      (Sec. 2), NMI = (H_A + H_B) / H_AB, from the same counts and fixed-point
                                      entropy sums; 0 where N = 0 or H_AB = 0 (0/0 = 0, Sec. 3.2).  Alg. 1's
@@ -181,6 +183,27 @@ cmif_status cmif_rotate_nn(const int32_t* B, const uint8_t* M_B, int H, int W, d
 cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
                                  const uint8_t* M_B, const double* angles_rad_host, int n_angles, double gamma,
                                  int top_k, cmif_peak* topk_dev, double* mi_maps, void* stream);
+
+/* Spatially weighted MI (SWMI, Sec. 3 "Generalization to spatially weighted MI"):
+ * the level sets carry the weights, L_a^W[A](x) = W_A(x) where A(x) = a, else 0
+ * (likewise B with W_B), so every count becomes a weighted sum,
+ * C_AB^{a,b}(chi) = sum_x W_A(x) W_B(x + chi) [A(x) = a][B(x + chi) = b], and
+ * N(chi) = sum of the joint counts.  MI(chi) follows Eq. finalentropy with
+ * these real counts (no rounding: the counts are not integers), computed with
+ * FP64 transforms and FP64 sums; c log2 c = 0 for c <= 0; MI = 0 where N = 0.
+ *   plan   : created with CMIF_FP64 and CMIF_FLAG_WEIGHTED (else INVALID_ARG)
+ *   W_A    : device double[H_A][W_A] weights >= 0, or NULL for all ones; a
+ *            weight of 0 acts as mask 0 (the label there is ignored); where the
+ *            weight is > 0 the label must lie in [0, K_A) (device status
+ *            LABEL_RANGE otherwise).  Likewise W_B.
+ *   mi_map : device double[R][C] (as cmif_compute)
+ *   nw_map : device double[R][C] weighted N, or NULL
+ *   peak_dev: device cmif_peak or NULL: Alg. 1's gamma-gated argmax, with
+ *            N >= gamma max N on the weighted N (its n field: N rounded)
+ * The window flag and graph replay apply as for cmif_compute. */
+cmif_status cmif_compute_weighted(cmif_plan plan, const int32_t* A, const double* W_A, const int32_t* B,
+                                  const double* W_B, double* mi_map, double* nw_map, double gamma, cmif_peak* peak_dev,
+                                  void* stream);
 
 /* Two-stage rigid alignment (Sec. 4, the paragraph after Alg. 1): (i) Alg. 1
  * over the grid theta_t = 2 pi t / n_grid, t < n_grid; (ii) Alg. 1 over

@@ -28,6 +28,12 @@ Functions and the passages they follow:
 * ``nmi``         -- the normalised MI the paper cites next to MI (Sec. 2),
                      (H_A + H_B) / H_AB from the direct method's entropies, 0/0 = 0.
                      Pinned by closed forms (A = B: 2; independent labels: 1).
+* ``swmi``        -- spatially weighted MI (Sec. 3): the direct weighted histogram
+                     per displacement (each overlapping pixel pair adds W_A W_B to its
+                     joint bin), MI by Eq. mi on the weighted relative frequencies.
+                     numpy, small inputs.  Pinned by tests/test_oracle_alg1.py (unit
+                     weights = MI, 0/1 weights = masked MI, scale invariance, and the
+                     weighted label entropy for A = B).
 * ``align_two_stage`` -- the two-stage rigid search of Sec. 4 (grid, then random
                      refinement in [theta - 2 pi/|Omega|, theta + 2 pi/|Omega|]), the
                      uniform draws passed in.  Pinned by hand-checked compositions.
@@ -295,3 +301,47 @@ def nmi(A, M_A, B, M_B, K_A, K_B):
     ok = hab > 0
     out[ok] = (ha[ok] + hb[ok]) / hab[ok]
     return dict(nmi=out, n=ref["n"], h_ab=hab)
+
+
+def swmi(A, W_A, B, W_B, K_A, K_B):
+    """Spatially weighted MI over the full shift range (Sec. 3), by the direct
+    weighted histogram: at each chi every pixel pair (x, x + chi) with both weights
+    > 0 adds W_A(x) W_B(x + chi) to bin (A(x), B(x + chi)); p = bins / N with N the
+    total; MI = sum p log2(p / (p_a p_b)) (Eq. mi), 0 where N = 0.  W_* = None means
+    all ones.  Returns dict(mi, nw) of shape (H_A + H_B - 1, W_A + W_B - 1)."""
+    A = np.asarray(A, np.int64)
+    B = np.asarray(B, np.int64)
+    HA, WA = A.shape
+    HB, WB = B.shape
+    wa = np.ones(A.shape) if W_A is None else np.asarray(W_A, np.float64)
+    wb = np.ones(B.shape) if W_B is None else np.asarray(W_B, np.float64)
+    R, C = HA + HB - 1, WA + WB - 1
+    mi = np.zeros((R, C))
+    nw = np.zeros((R, C))
+    for r in range(R):
+        dy = r - (HA - 1)
+        ya0, ya1 = max(0, -dy), min(HA, HB - dy)
+        for c in range(C):
+            dx = c - (WA - 1)
+            xa0, xa1 = max(0, -dx), min(WA, WB - dx)
+            if ya1 <= ya0 or xa1 <= xa0:
+                continue
+            a = A[ya0:ya1, xa0:xa1]
+            b = B[ya0 + dy:ya1 + dy, xa0 + dx:xa1 + dx]
+            w = wa[ya0:ya1, xa0:xa1] * wb[ya0 + dy:ya1 + dy, xa0 + dx:xa1 + dx]
+            keep = (wa[ya0:ya1, xa0:xa1] > 0) & (wb[ya0 + dy:ya1 + dy, xa0 + dx:xa1 + dx] > 0)
+            if not keep.any():
+                continue
+            if (a[keep] < 0).any() or (a[keep] >= K_A).any() or (b[keep] < 0).any() or (b[keep] >= K_B).any():
+                raise OracleError("label outside [0, K) under a positive weight")
+            joint = np.bincount(a[keep] * K_B + b[keep], weights=w[keep], minlength=K_A * K_B).reshape(K_A, K_B)
+            n = joint.sum()
+            nw[r, c] = n
+            if n <= 0:
+                continue
+            p = joint / n
+            pa = p.sum(axis=1, keepdims=True)
+            pb = p.sum(axis=0, keepdims=True)
+            nz = p > 0
+            mi[r, c] = float((p[nz] * np.log2(p[nz] / (pa @ pb)[nz])).sum())
+    return dict(mi=mi, nw=nw)

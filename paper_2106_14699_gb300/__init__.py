@@ -24,6 +24,7 @@ FLAG_DEBUG_COUNTS = 1
 FLAG_GRAPH = 2
 FLAG_WINDOW = 4
 FLAG_NMI = 8
+FLAG_WEIGHTED = 16
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "LABEL_RANGE", 3: "OOM", 4: "CUDA", 5: "PRECISION",
                 6: "TIMEOUT", 7: "NOT_IMPLEMENTED", 8: "UNSUPPORTED"}
 
@@ -49,7 +50,7 @@ class Peak(ctypes.Structure):
 EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_destroy", "cmif_plan_workspace_bytes",
            "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
            "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_rotate_nn", "cmif_align_rotations",
-           "cmif_align_two_stage", "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status",
+           "cmif_align_two_stage", "cmif_compute_weighted", "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status",
            "cmif_batch_destroy", "cmif_status_string"]
 
 _lib = None
@@ -76,6 +77,7 @@ def lib():
         L.cmif_compute_noalloc.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, D, P, P, P]
         L.cmif_rotate_nn.argtypes = [P, P, I, I, D, P, P, P]
         L.cmif_align_rotations.argtypes = [P, P, P, P, P, P, I, D, I, P, P, P]
+        L.cmif_compute_weighted.argtypes = [P, P, P, P, P, P, P, D, P, P]
         L.cmif_align_two_stage.argtypes = [P, P, P, P, P, I, P, I, D, ctypes.POINTER(Peak), ctypes.POINTER(D), P]
         L.cmif_batch_create.argtypes = [ctypes.POINTER(P), I, P, I, U]
         L.cmif_compute_batch.argtypes = [P, P, P, P]
@@ -119,10 +121,10 @@ class Plan:
     """A CMIF plan for images H_A x W_A and H_B x W_B with K_A, K_B labels."""
 
     def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False, graph=False, window=False,
-                 nmi=False):
+                 nmi=False, weighted=False):
         self._h = ctypes.c_void_p()
         flags = (FLAG_DEBUG_COUNTS if debug_counts else 0) | (FLAG_GRAPH if graph else 0) | \
-            (FLAG_WINDOW if window else 0) | (FLAG_NMI if nmi else 0)
+            (FLAG_WINDOW if window else 0) | (FLAG_NMI if nmi else 0) | (FLAG_WEIGHTED if weighted else 0)
         _check(lib().cmif_plan_create_ex(ctypes.byref(self._h), H_A, W_A, H_B, W_B, K_A, K_B, precision, flags),
                "cmif_plan_create_ex")
         self.H_A, self.W_A, self.H_B, self.W_B, self.K_A, self.K_B = H_A, W_A, H_B, W_B, K_A, K_B
@@ -142,6 +144,12 @@ class Plan:
         """Device-pointer call (torch CUDA tensors or raw addresses); asynchronous."""
         _check(lib().cmif_compute(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), _ptr(mi_map), _ptr(n_map),
                                   _ptr(counts), float(gamma), _ptr(peak), _stream(stream)), "cmif_compute")
+
+    def compute_weighted(self, A, W_A, B, W_B, mi_map, nw_map=None, gamma=0.0, peak=None, stream=None):
+        """Spatially weighted MI map (device tensors; weights float64 or None); asynchronous."""
+        _check(lib().cmif_compute_weighted(self._h, _ptr(A), _ptr(W_A), _ptr(B), _ptr(W_B), _ptr(mi_map),
+                                           _ptr(nw_map), float(gamma), _ptr(peak), _stream(stream)),
+               "cmif_compute_weighted")
 
     def compute_host(self, A, M_A, B, M_B, mi_map, n_map=None, gamma=0.0, peak=None, stream=None):
         """Host-buffer call (numpy, ideally pinned); copies in and out, synchronises."""

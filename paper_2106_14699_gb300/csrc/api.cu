@@ -24,6 +24,7 @@ struct Workspace {
     PipeArgs<T> args{};  // pointer part filled at create time
     int rows_grid = 0;
     bool cb_smem = true;
+    int rows_grid_w = 0;  // > 0: the plan computes weighted maps (FP64 workspace only)
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -129,6 +130,10 @@ size_t workspace_bytes(const Geom& g, const Workspace<T>& w) {
     off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);  // Y
     off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);  // CB
     off = align_up(off + sizeof(int), 256);  // work counter
+    if (w.rows_grid_w > 0) {
+        off = align_up(off + (size_t)w.rows_grid_w * g.KB * g.Q * sizeof(double), 256);  // weighted B-marginals
+        off = align_up(off + (size_t)g.R * g.C * sizeof(double), 256);                   // weighted N map
+    }
     return off;
 }
 
@@ -145,6 +150,12 @@ void carve_workspace(const Geom& g, Workspace<T>& w, char* base) {
     w.args.cb_global = w.cb_smem ? nullptr : (float*)(base + off);
     off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);
     w.args.work_ctr = (int*)(base + off);
+    off = align_up(off + sizeof(int), 256);
+    w.args.rows_grid_w = w.rows_grid_w;
+    if (w.rows_grid_w > 0) {
+        w.args.cbw = (double*)(base + off); off = align_up(off + (size_t)w.rows_grid_w * g.KB * g.Q * sizeof(double), 256);
+        w.args.nw = (double*)(base + off);
+    }
 }
 
 template <typename T>
@@ -282,8 +293,11 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     if (H_A < 1 || W_A < 1 || H_B < 1 || W_B < 1 || K_A < 1 || K_B < 1 || K_A > 64 || K_B > 64)
         return CMIF_ERR_INVALID_ARG;
     if ((long long)H_A * W_A > (1LL << 22) || (long long)H_B * W_B > (1LL << 22)) return CMIF_ERR_INVALID_ARG;
-    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI))
+    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI | CMIF_FLAG_WEIGHTED))
         return CMIF_ERR_INVALID_ARG;
+    // weighted maps: FP64 transforms (real counts, no rounding), MI only
+    if ((flags & CMIF_FLAG_WEIGHTED) && (prec != CMIF_FP64 || (flags & (CMIF_FLAG_NMI | CMIF_FLAG_DEBUG_COUNTS))))
+        return CMIF_ERR_UNSUPPORTED;
     if (prec != CMIF_FP32 && prec != CMIF_SPLIT32 && prec != CMIF_FP64 && prec != CMIF_AUTO) return CMIF_ERR_INVALID_ARG;
     Geom g{};
     g.HA = H_A; g.WA = W_A; g.HB = H_B; g.WB = W_B; g.KA = K_A; g.KB = K_B;
@@ -313,6 +327,12 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     if (st == CMIF_OK && (prec == CMIF_FP64 || (prec == CMIF_AUTO && p->tier2 == CMIF_FP64))) {
         st = choose_rows<double>(p, p->w64);
         p->has64 = (st == CMIF_OK);
+        if (st == CMIF_OK && (flags & CMIF_FLAG_WEIGHTED)) {
+            int bps = 0;
+            if (rows_w_max_blocks_per_sm(g.Q, &bps) != cudaSuccess) return CMIF_ERR_CUDA;
+            if (bps < 1) return CMIF_ERR_UNSUPPORTED;
+            p->w64.rows_grid_w = std::min(g.R, bps * p->num_sms);
+        }
     }
     if (st == CMIF_OK && (prec == CMIF_SPLIT32 || (prec == CMIF_AUTO && p->tier2 == CMIF_SPLIT32))) {
         st = choose_rows<df32>(p, p->ws32);
@@ -547,6 +567,52 @@ cmif_status cmif_compute(cmif_plan plan, const int32_t* A, const uint8_t* M_A, c
             if (e != cudaSuccess) return from_cuda(e);
         }
         return CMIF_OK;
+    });
+}
+
+cmif_status cmif_compute_weighted(cmif_plan plan, const int32_t* A, const double* W_A, const int32_t* B,
+                                  const double* W_B, double* mi_map, double* nw_map, double gamma, cmif_peak* peak_dev,
+                                  void* stream) {
+    if (!plan || !A || !B || !mi_map) return CMIF_ERR_INVALID_ARG;
+    if (!(plan->flags & CMIF_FLAG_WEIGHTED) || plan->w64.rows_grid_w <= 0) return CMIF_ERR_INVALID_ARG;
+    if (!(gamma >= 0.0 && gamma <= 1.0)) return CMIF_ERR_INVALID_ARG;
+    DeviceGuard dg(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->last_stream = s;
+    plan->prof.reset();
+    Geom g;
+    if (!call_geom(plan, gamma, &g)) return CMIF_ERR_INVALID_ARG;
+    double* nw = nw_map ? nw_map : plan->w64.args.nw;
+    std::vector<unsigned char> key;
+    key_add(key, 4);
+    key_add(key, A); key_add(key, W_A); key_add(key, B); key_add(key, W_B);
+    key_add(key, mi_map); key_add(key, nw); key_add(key, gamma); key_add(key, peak_dev);
+    return run_graph(plan, s, key, [&](cudaStream_t cs) -> cmif_status {
+        cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(plan->st, 0, sizeof(DevStatus), cs);
+        if (e == cudaSuccess && (g.r0 > 0 || g.r1 < g.R)) {  // rows outside the window are not computed: zero
+            const size_t RC = (size_t)g.R * g.C;
+            e = cudaMemsetAsync(mi_map, 0, RC * sizeof(double), cs);
+            if (e == cudaSuccess) e = cudaMemsetAsync(nw, 0, RC * sizeof(double), cs);
+        }
+        if (e != cudaSuccess) return from_cuda(e);
+        PipeArgs<double> a = plan->w64.args;
+        a.A = A; a.MA = nullptr; a.B = B; a.MB = nullptr;
+        a.WA = W_A; a.WB = W_B; a.weighted = 1;
+        a.mi = mi_map; a.nw = nw; a.n = nullptr; a.counts = nullptr; a.st = plan->st;
+        a.prof = plan->prof.enabled ? &plan->prof : nullptr;
+        a.stages = STAGE_ALL;
+        a.prec_slot = 1;
+        a.conditional = 0;
+        e = run_pipeline<double>(g, a, cs);
+        if (e != cudaSuccess) return from_cuda(e);
+        e = launch_merge_status(plan->st, plan->st_total, 1, cs);
+        if (e == cudaSuccess && peak_dev) {
+            plan->prof.begin("peak", cs);
+            e = launch_peak_w(mi_map, nw, g, plan->st, gamma, plan->parts, plan->nparts, peak_dev, cs);
+            plan->prof.end(cs);
+        }
+        return from_cuda(e);
     });
 }
 

@@ -11,6 +11,7 @@ struct DevStatus {
     int max_n;             // max_chi N(chi) of the last map (for the gamma gate of Alg. 1)
     int escalations;       // number of FP32 -> FP64 re-runs
     int pad[3];
+    unsigned long long max_nw_bits;  // weighted maps (SWMI): max N(chi) as double bits (N >= 0)
 };
 enum : unsigned {
     STATUS_LABEL_RANGE = 1u,  // a label under mask 1 lies outside [0, K)

@@ -140,7 +140,9 @@ struct TeamGeom {
 // plane pair pp = blockIdx.y * TPB + t (planes 2pp, 2pp+1).  The block first
 // stages the row as one byte per pixel (the label, or kMaskedOut where the
 // mask is 0; the label range is checked here), then every team builds its two
-// level sets from shared memory.
+// level sets from shared memory.  With a weight image WX (spatially weighted
+// MI, Sec. 3) the level sets carry the weight W(x) instead of 1 (weight 0 plays
+// the mask's 0) and the row's weights are staged too.
 constexpr unsigned char kMaskedOut = 255;
 
 template <typename T, int Q>
@@ -150,18 +152,21 @@ struct FwdRowsCfg {
     static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
     static constexpr int THREADS = TPB * TEAM;
     static constexpr int REGION = (int)(Q * sizeof(cpx<T>)) > G::SCRATCH ? (int)(Q * sizeof(cpx<T>)) : G::SCRATCH;
-    static constexpr size_t smem(int W) { return (size_t)TPB * REGION + (((size_t)W + 15) & ~(size_t)15); }
+    static constexpr size_t smem(int W, bool weighted) {
+        return (size_t)TPB * REGION + (((size_t)W + 15) & ~(size_t)15) + (weighted ? (size_t)W * sizeof(double) : 0);
+    }
 };
 
 template <typename T, int Q>
 __global__ void __launch_bounds__(FwdRowsCfg<T, Q>::THREADS)
-k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, int H, int W, int K, int Qs,
-           cpx<T>* __restrict__ T1, Tw<T> tw, DevStatus* __restrict__ st, int conditional) {
+k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const double* __restrict__ WX, int H, int W,
+           int K, int Qs, cpx<T>* __restrict__ T1, Tw<T> tw, DevStatus* __restrict__ st, int conditional) {
     using C = FwdRowsCfg<T, Q>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* code = smem_raw + (size_t)C::TPB * C::REGION;
+    double* wts = reinterpret_cast<double*>(code + (((size_t)W + 15) & ~(size_t)15));
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
     const int npp = (K + 1) / 2;
     const int y = blockIdx.x, pp = blockIdx.y * C::TPB + team;
@@ -170,9 +175,15 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, int H,
     const int32_t* xr = X + (size_t)y * W;
     const uint8_t* mr = MX ? MX + (size_t)y * W : nullptr;
     bool bad = false;
+    const double* wr = WX ? WX + (size_t)y * W : nullptr;
     for (int x = threadIdx.x; x < W; x += C::THREADS) {
         const int lab = __ldg(xr + x);
-        const bool m = mr ? (__ldg(mr + x) != 0) : true;
+        bool m = mr ? (__ldg(mr + x) != 0) : true;
+        if (wr) {
+            const double w = __ldg(wr + x);
+            m = w > 0.0;
+            wts[x] = w;
+        }
         if (m && (lab < 0 || lab >= K)) bad = true;
         code[x] = m && lab >= 0 && lab < K ? (unsigned char)lab : kMaskedOut;
     }
@@ -183,7 +194,8 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, int H,
     auto load = [&](int x) -> cpx<T> {
         if (!active || x >= W) return {T(0), T(0)};
         const int c = code[x];
-        return {c == la ? T(1) : T(0), c == lb ? T(1) : T(0)};
+        const T one = wr ? T(wts[x]) : T(1);
+        return {c == la ? one : T(0), c == lb ? one : T(0)};
     };
     cpx<T> v[M];
     team_fft<M, R, -1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)], tw.n[ilog2c(Q)]);
@@ -667,6 +679,125 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Spatially weighted MI (Sec. 3): the inverse row transform of weighted
+// correlations (FP64 transforms) and the MI of their real-valued counts.  The
+// counts are not integers, so nothing is rounded: each position accumulates
+// sum c log2 c over joint, A- and B-marginal counts in FP64, with c log2 c = 0
+// for c <= 0 (a count that the transform's rounding error takes below 0).
+// MI = (S_joint - S_A - S_B + N log2 N) / N, N = sum_a C_A^a; 0 when N <= 0.
+// One block per output row (grid-stride), NT teams transform NT pairs per round
+// (a-major order); the B-marginals live in the block's global slice cbw.
+template <int Q>
+struct RowWCfg {
+    static constexpr int L = Q / 2;
+    using G = TeamGeom<double, L>;
+    static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
+    static constexpr int NT = TEAM >= 256 ? 1 : 256 / TEAM;
+    static constexpr int THREADS = NT * TEAM;
+    static constexpr int U = (Q + THREADS - 1) / THREADS;  // positions per thread
+    static constexpr int REGION = G::SCRATCH;              // one row of Q doubles
+    static constexpr size_t SMEM = (size_t)NT * REGION;
+    static_assert(REGION >= Q * 8, "team scratch must hold one row of counts");
+};
+
+__device__ __forceinline__ double xlog2x(double c) { return c > 0.0 ? c * log2(c) : 0.0; }
+
+template <int Q>
+__global__ void __launch_bounds__(RowWCfg<Q>::THREADS, 1)
+k_pair_rows_w(const cpx<double>* __restrict__ Y, Geom g, Tw<double> tw, double* __restrict__ cbw,
+              double* __restrict__ mi_map, double* __restrict__ nw_map, DevStatus* __restrict__ st) {
+    using C = RowWCfg<Q>;
+    constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, BT = C::THREADS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tid = threadIdx.x, team = tid / C::TEAM, lt = tid % C::TEAM, r = lt / M, j = lt % M;
+    unsigned char* region = smem_raw + (size_t)team * C::REGION;
+    const int KB = g.KB, npairs = g.KA * g.KB, Rout = g.R, Cout = g.C, Qs = g.Qs;
+    double* cb = cbw + (size_t)blockIdx.x * KB * Q;
+    const cpx<double>* twq_c2r = tw.n[ilog2c(Q)];
+    double row_max_n = 0.0;
+    for (int row = g.r0 + blockIdx.x; row < g.r1; row += gridDim.x) {
+        double S[U], CA[U], N[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) { S[u] = 0.0; CA[u] = 0.0; N[u] = 0.0; }
+        for (int b = 0; b < KB; ++b)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = tid + BT * u;
+                if (p < Q) cb[(size_t)b * Q + p] = 0.0;
+            }
+        int cur_a = 0;
+        for (int base = 0; base < npairs; base += NT) {
+            const int pair = base + team;
+            const bool act = pair < npairs;
+            const cpx<double>* yr = Y + ((size_t)(act ? pair : 0) * Rout + row) * Qs;
+            // Hermitian split: z = IDFT_L(E + iO), z[m] = x[2m] + i x[2m+1]
+            auto load = [&](int k) -> cpx<double> {
+                if (!act) return {0.0, 0.0};
+                const cpx<double> yk = yr[k], ym = yr[L - k];
+                const cpx<double> e = {yk.x + ym.x, yk.y - ym.y};
+                const cpx<double> d = {yk.x - ym.x, yk.y + ym.y};
+                const cpx<double> o = cmul(d, twl<+1>(twq_c2r, k));
+                return {e.x - o.y, e.y + o.x};
+            };
+            cpx<double> v[M];
+            team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<double, M>(), tw.sq[ilog2c(M)],
+                               tw.n[ilog2c(L)]);
+            __syncthreads();  // all transforms done with their scratch
+            double2* ob = reinterpret_cast<double2*>(region);
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const cpx<double> z = v[brev(k2, M)];
+                ob[R * (j + M * k2) + r] = make_double2(z.x, z.y);  // positions 2m, 2m + 1
+            }
+            __syncthreads();
+            const int nt = min(NT, npairs - base);
+            int a = base / KB, b = base - (base / KB) * KB;
+            for (int t = 0; t < nt; ++t) {
+                if (a != cur_a) {  // uniform: the A-marginal of label cur_a is complete
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        S[u] -= xlog2x(CA[u]);
+                        N[u] += CA[u];
+                        CA[u] = 0.0;
+                    }
+                    cur_a = a;
+                }
+                const double* obt = reinterpret_cast<const double*>(smem_raw + (size_t)t * C::REGION);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int p = tid + BT * u;
+                    if (p >= Q) continue;
+                    const double c = fmax(obt[p], 0.0);
+                    S[u] += xlog2x(c);
+                    CA[u] += c;
+                    cb[(size_t)b * Q + p] += c;
+                }
+                if (++b == KB) { b = 0; ++a; }
+            }
+            __syncthreads();  // the next round's transforms overwrite the scratch read above
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = tid + BT * u;
+            if (p >= Q) continue;
+            S[u] -= xlog2x(CA[u]);
+            N[u] += CA[u];
+            for (int b = 0; b < KB; ++b) S[u] -= xlog2x(cb[(size_t)b * Q + p]);
+            const int cidx = circ_to_out(p, Q, g.WA, g.WB - 1);
+            if (cidx < 0) continue;
+            const size_t o = (size_t)row * Cout + cidx;
+            mi_map[o] = N[u] > 0.0 ? (S[u] + xlog2x(N[u])) / N[u] : 0.0;
+            nw_map[o] = N[u];
+            if (cidx >= g.c0 && cidx < g.c1) row_max_n = fmax(row_max_n, N[u]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) row_max_n = fmax(row_max_n, __shfl_xor_sync(0xffffffffu, row_max_n, off));
+    if ((tid & 31) == 0) atomicMax(&st->max_nw_bits, (unsigned long long)__double_as_longlong(row_max_n));
+}
+
 template <typename T, int Q>
 constexpr size_t pair_rows_smem(int KB, bool cb_smem) {
     return RowCfg<T, Q>::TEAM_SMEM + (cb_smem ? (size_t)KB * Q * sizeof(float) : 0);
@@ -680,11 +811,6 @@ struct PeakPart {
     long long idx;
 };
 
-__global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __restrict__ n, int Cout, int r0, int r1,
-                               int c0, int c1, const DevStatus* __restrict__ st, double gamma,
-                               PeakPart* __restrict__ parts);
-__global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, const double* __restrict__ mi,
-                             const int32_t* __restrict__ n, int HA, int WA, int Cout, int angle_idx,
-                             void* __restrict__ peak_out);
+
 
 }  // namespace cmif

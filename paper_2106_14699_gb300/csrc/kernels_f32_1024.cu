@@ -1,4 +1,4 @@
-// FP32 forward, column and pair-product kernels for transform size 1024.
+// FP32 forward, column, pair-product and weighted-row kernels for transform size 1024.
 #include "pipeline_impl.cuh"
 namespace cmif {
 template cudaError_t Sized<float, 1024>::fwd_rows(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
@@ -6,4 +6,7 @@ template cudaError_t Sized<float, 1024>::fwd_cols(const Geom&, const PipeArgs<fl
 template cudaError_t Sized<float, 1024>::pair_cols(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template int Sized<float, 1024>::tm_cols(int);
 template cudaError_t Sized<float, 1024>::tm_max_blocks(int*);
+template cudaError_t Sized<float, 1024>::pair_rows_w(const Geom&, const PipeArgs<float>&, cudaStream_t);
+template size_t Sized<float, 1024>::rows_w_smem();
+template cudaError_t Sized<float, 1024>::rows_w_max_blocks(int*);
 }

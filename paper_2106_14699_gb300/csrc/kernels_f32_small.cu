@@ -1,4 +1,4 @@
-// FP32 forward, column and pair-product kernels for transform sizes 16, 32, 64, 128, 256.
+// FP32 forward, column, pair-product and weighted-row kernels for transform sizes 16, 32, 64, 128, 256.
 #include "pipeline_impl.cuh"
 namespace cmif {
 template cudaError_t Sized<float, 16>::fwd_rows(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
@@ -6,24 +6,39 @@ template cudaError_t Sized<float, 16>::fwd_cols(const Geom&, const PipeArgs<floa
 template cudaError_t Sized<float, 16>::pair_cols(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template int Sized<float, 16>::tm_cols(int);
 template cudaError_t Sized<float, 16>::tm_max_blocks(int*);
+template cudaError_t Sized<float, 16>::pair_rows_w(const Geom&, const PipeArgs<float>&, cudaStream_t);
+template size_t Sized<float, 16>::rows_w_smem();
+template cudaError_t Sized<float, 16>::rows_w_max_blocks(int*);
 template cudaError_t Sized<float, 32>::fwd_rows(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
 template cudaError_t Sized<float, 32>::fwd_cols(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
 template cudaError_t Sized<float, 32>::pair_cols(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template int Sized<float, 32>::tm_cols(int);
 template cudaError_t Sized<float, 32>::tm_max_blocks(int*);
+template cudaError_t Sized<float, 32>::pair_rows_w(const Geom&, const PipeArgs<float>&, cudaStream_t);
+template size_t Sized<float, 32>::rows_w_smem();
+template cudaError_t Sized<float, 32>::rows_w_max_blocks(int*);
 template cudaError_t Sized<float, 64>::fwd_rows(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
 template cudaError_t Sized<float, 64>::fwd_cols(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
 template cudaError_t Sized<float, 64>::pair_cols(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template int Sized<float, 64>::tm_cols(int);
 template cudaError_t Sized<float, 64>::tm_max_blocks(int*);
+template cudaError_t Sized<float, 64>::pair_rows_w(const Geom&, const PipeArgs<float>&, cudaStream_t);
+template size_t Sized<float, 64>::rows_w_smem();
+template cudaError_t Sized<float, 64>::rows_w_max_blocks(int*);
 template cudaError_t Sized<float, 128>::fwd_rows(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
 template cudaError_t Sized<float, 128>::fwd_cols(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
 template cudaError_t Sized<float, 128>::pair_cols(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template int Sized<float, 128>::tm_cols(int);
 template cudaError_t Sized<float, 128>::tm_max_blocks(int*);
+template cudaError_t Sized<float, 128>::pair_rows_w(const Geom&, const PipeArgs<float>&, cudaStream_t);
+template size_t Sized<float, 128>::rows_w_smem();
+template cudaError_t Sized<float, 128>::rows_w_max_blocks(int*);
 template cudaError_t Sized<float, 256>::fwd_rows(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
 template cudaError_t Sized<float, 256>::fwd_cols(const Geom&, const PipeArgs<float>&, bool, cudaStream_t);
 template cudaError_t Sized<float, 256>::pair_cols(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template int Sized<float, 256>::tm_cols(int);
 template cudaError_t Sized<float, 256>::tm_max_blocks(int*);
+template cudaError_t Sized<float, 256>::pair_rows_w(const Geom&, const PipeArgs<float>&, cudaStream_t);
+template size_t Sized<float, 256>::rows_w_smem();
+template cudaError_t Sized<float, 256>::rows_w_max_blocks(int*);
 }

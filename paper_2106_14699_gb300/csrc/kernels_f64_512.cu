@@ -1,4 +1,4 @@
-// FP64 forward, column and pair-product kernels for transform size 512.
+// FP64 forward, column, pair-product and weighted-row kernels for transform size 512.
 #include "pipeline_impl.cuh"
 namespace cmif {
 template cudaError_t Sized<double, 512>::fwd_rows(const Geom&, const PipeArgs<double>&, bool, cudaStream_t);
@@ -6,4 +6,7 @@ template cudaError_t Sized<double, 512>::fwd_cols(const Geom&, const PipeArgs<do
 template cudaError_t Sized<double, 512>::pair_cols(const Geom&, const PipeArgs<double>&, cudaStream_t);
 template int Sized<double, 512>::tm_cols(int);
 template cudaError_t Sized<double, 512>::tm_max_blocks(int*);
+template cudaError_t Sized<double, 512>::pair_rows_w(const Geom&, const PipeArgs<double>&, cudaStream_t);
+template size_t Sized<double, 512>::rows_w_smem();
+template cudaError_t Sized<double, 512>::rows_w_max_blocks(int*);
 }

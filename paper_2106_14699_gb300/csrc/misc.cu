@@ -18,11 +18,20 @@ __device__ __forceinline__ bool better(double m1, long long i1, double m2, long 
 }
 
 // Scans the search window rows [r0, r1) x columns [c0, c1) of the (R x Cout) maps;
-// indices stay row-major map indices (ties: lowest).
-__global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __restrict__ n, int Cout, int r0, int r1,
+// indices stay row-major map indices (ties: lowest).  NT: int32_t N (counts) or
+// double N (weighted maps, max N from max_nw_bits).
+__device__ __forceinline__ double max_n_of(const DevStatus* st, const int32_t*) { return (double)st->max_n; }
+__device__ __forceinline__ double max_n_of(const DevStatus* st, const double*) {
+    return __longlong_as_double((long long)st->max_nw_bits);
+}
+__device__ __forceinline__ int32_t n_record(int32_t n) { return n; }
+__device__ __forceinline__ int32_t n_record(double n) { return (int32_t)fmin(rint(n), 2147483647.0); }
+
+template <typename NT>
+__global__ void k_peak_partial(const double* __restrict__ mi, const NT* __restrict__ n, int Cout, int r0, int r1,
                                int c0, int c1, const DevStatus* __restrict__ st, double gamma,
                                PeakPart* __restrict__ parts) {
-    const double thr = gamma * (double)st->max_n;
+    const double thr = gamma * max_n_of(st, n);
     const int wc = c1 - c0;
     const long long cnt = (long long)(r1 - r0) * wc;
     double bm = -INFINITY;
@@ -51,8 +60,9 @@ __global__ void k_peak_partial(const double* __restrict__ mi, const int32_t* __r
     }
 }
 
+template <typename NT>
 __global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, const double* __restrict__ mi,
-                             const int32_t* __restrict__ n, int HA, int WA, int Cout, int angle_idx,
+                             const NT* __restrict__ n, int HA, int WA, int Cout, int angle_idx,
                              void* __restrict__ peak_out) {
     double bm = -INFINITY;
     long long bi = -1;
@@ -76,7 +86,7 @@ __global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, con
     p->angle_idx = angle_idx;
     p->dy = (int)(bi / Cout) - (HA - 1);
     p->dx = (int)(bi % Cout) - (WA - 1);
-    p->n = n[bi];
+    p->n = n_record(n[bi]);  // weighted maps: N rounded to an integer
     p->mi = bm;
 }
 
@@ -197,12 +207,23 @@ __global__ void k_finalize(DevStatus* st, int slot_if_escalated, int slot_defaul
     }
 }
 
+template <typename NT>
+static cudaError_t launch_peak_t(const double* mi, const NT* n, const Geom& g, const DevStatus* st, double gamma,
+                                 PeakPart* parts, int nparts, int angle_idx, void* peak_out, cudaStream_t s) {
+    const int HA = g.HA, WA = g.WA, Cout = g.C;
+    k_peak_partial<NT><<<nparts, 256, 0, s>>>(mi, n, Cout, g.r0, g.r1, g.c0, g.c1, st, gamma, parts);
+    k_peak_final<NT><<<1, 256, 0, s>>>(parts, nparts, mi, n, HA, WA, Cout, angle_idx, peak_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_peak(const double* mi, const int32_t* n, const Geom& g, const DevStatus* st, double gamma,
                         PeakPart* parts, int nparts, int angle_idx, void* peak_out, cudaStream_t s) {
-    const int HA = g.HA, WA = g.WA, Cout = g.C;
-    k_peak_partial<<<nparts, 256, 0, s>>>(mi, n, Cout, g.r0, g.r1, g.c0, g.c1, st, gamma, parts);
-    k_peak_final<<<1, 256, 0, s>>>(parts, nparts, mi, n, HA, WA, Cout, angle_idx, peak_out);
-    return cudaGetLastError();
+    return launch_peak_t(mi, n, g, st, gamma, parts, nparts, angle_idx, peak_out, s);
+}
+
+cudaError_t launch_peak_w(const double* mi, const double* nw, const Geom& g, const DevStatus* st, double gamma,
+                          PeakPart* parts, int nparts, void* peak_out, cudaStream_t s) {
+    return launch_peak_t(mi, nw, g, st, gamma, parts, nparts, 0, peak_out, s);
 }
 
 cudaError_t launch_check_escalate(DevStatus* st, cudaStream_t s) {

@@ -18,6 +18,9 @@ struct PeakRec {
 // Alg. 1's gamma-gated argmax over the call's search window (g.r0..g.r1, g.c0..g.c1).
 cudaError_t launch_peak(const double* mi, const int32_t* n, const Geom& g, const DevStatus* st, double gamma,
                         PeakPart* parts, int nparts, int angle_idx, void* peak_out, cudaStream_t s);
+// The same on a weighted map (real N, max N from the status word's max_nw_bits).
+cudaError_t launch_peak_w(const double* mi, const double* nw, const Geom& g, const DevStatus* st, double gamma,
+                          PeakPart* parts, int nparts, void* peak_out, cudaStream_t s);
 cudaError_t launch_check_escalate(DevStatus* st, cudaStream_t s);
 cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s);
 cudaError_t launch_warp_nn(const int32_t* B, const uint8_t* MB, int H, int W, double theta, int32_t* Bo, uint8_t* Mo,

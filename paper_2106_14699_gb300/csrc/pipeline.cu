@@ -45,10 +45,17 @@ cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
             ProfScope ps(a.prof, f32 ? "pair_cols_f32" : split ? "pair_cols_s32" : "pair_cols_f64", s);
             e = Sized<T, SZ>::pair_cols(g, a, s);
         } if (e != cudaSuccess) return e);
-        CMIF_SIZE_SWITCH(g.Q, {
-            ProfScope ps(a.prof, f32 ? "pair_rows_f32" : split ? "pair_rows_s32" : "pair_rows_f64", s);
-            e = Sized<T, SZ>::pair_rows(g, a, s);
-        } if (e != cudaSuccess) return e);
+        if (a.weighted) {
+            CMIF_SIZE_SWITCH(g.Q, {
+                ProfScope ps(a.prof, "pair_rows_weighted_f64", s);
+                e = Sized<T, SZ>::pair_rows_w(g, a, s);
+            } if (e != cudaSuccess) return e);
+        } else {
+            CMIF_SIZE_SWITCH(g.Q, {
+                ProfScope ps(a.prof, f32 ? "pair_rows_f32" : split ? "pair_rows_s32" : "pair_rows_f64", s);
+                e = Sized<T, SZ>::pair_rows(g, a, s);
+            } if (e != cudaSuccess) return e);
+        }
     }
     return cudaSuccess;
 }
@@ -89,6 +96,12 @@ int rows_tm_cols(int Q, int KB) {
     };
     f();
     return out;
+}
+
+cudaError_t rows_w_max_blocks_per_sm(int Q, int* out) {
+    *out = 0;
+    CMIF_SIZE_SWITCH(Q, return Sized<double, SZ>::rows_w_max_blocks(out));
+    return cudaSuccess;
 }
 
 cudaError_t rows_tm_max_blocks_per_sm(int Q, int* out) {

@@ -29,6 +29,13 @@ struct PipeArgs {
     int rows_grid;    // persistent grid of the row/epilogue kernel
     int num_sms;      // SMs of the device (persistent grid of the pair-column kernel)
     int nmi;          // the map holds NMI = (H_A + H_B) / H_AB instead of MI
+    // spatially weighted MI (FP64 plans): weight images replace the masks
+    const double* WA;  // [H_A][W_A] or nullptr
+    const double* WB;  // [H_B][W_B] or nullptr
+    int weighted;      // run the weighted row kernel (real counts, no rounding)
+    double* cbw;       // [rows_grid_w][K_B][Q] B-marginals of the weighted row kernel
+    double* nw;        // weighted N map [R][C]
+    int rows_grid_w;   // persistent grid of the weighted row kernel
     bool cb_smem;     // B-marginal accumulators in shared memory
     Profiler* prof;   // optional launch timing (nullptr = off)
     int tm_cols;      // > 0: use the TMEM / TMA row kernel with this many TMEM columns
@@ -72,6 +79,9 @@ struct Sized {
     static cudaError_t rows_max_blocks(int KB, bool cb_smem, int* out);
     static int tm_cols(int KB);                 // 0 unless the TMEM row kernel applies (FP32, Q = 1024 / 2048)
     static cudaError_t tm_max_blocks(int* out);
+    static cudaError_t pair_rows_w(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);  // FP64 only
+    static size_t rows_w_smem();
+    static cudaError_t rows_w_max_blocks(int* out);
 };
 
 template <typename T>
@@ -87,5 +97,7 @@ cudaError_t rows_max_blocks_per_sm(int Q, int KB, bool cb_smem, int* out);
 // TMEM columns the TMEM / TMA row kernel needs for (Q, K_B), or 0 when it does not apply.
 int rows_tm_cols(int Q, int KB);
 cudaError_t rows_tm_max_blocks_per_sm(int Q, int* out);
+// The weighted (SWMI) row kernel: its occupancy (FP64).
+cudaError_t rows_w_max_blocks_per_sm(int Q, int* out);
 
 }  // namespace cmif

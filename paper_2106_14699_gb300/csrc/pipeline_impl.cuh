@@ -19,14 +19,14 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
 }
 
 template <typename T, int Q>
-static cudaError_t launch_fwd_rows(const int32_t* X, const uint8_t* MX, int H, int W, int K, int Qs, cpx<T>* T1,
-                                   const Tw<T>& tw, DevStatus* st, int conditional, cudaStream_t s) {
+static cudaError_t launch_fwd_rows(const int32_t* X, const uint8_t* MX, const double* WX, int H, int W, int K, int Qs,
+                                   cpx<T>* T1, const Tw<T>& tw, DevStatus* st, int conditional, cudaStream_t s) {
     using C = FwdRowsCfg<T, Q>;
     auto kern = k_fwd_rows<T, Q>;
-    cudaError_t e = ensure_smem(kern, C::smem(Q));
+    cudaError_t e = ensure_smem(kern, C::smem(Q, true));
     if (e != cudaSuccess) return e;
     dim3 grid(H, ((K + 1) / 2 + C::TPB - 1) / C::TPB);
-    kern<<<grid, C::THREADS, C::smem(W), s>>>(X, MX, H, W, K, Qs, T1, tw, st, conditional);
+    kern<<<grid, C::THREADS, C::smem(W, WX != nullptr), s>>>(X, MX, WX, H, W, K, Qs, T1, tw, st, conditional);
     return cudaGetLastError();
 }
 
@@ -107,8 +107,10 @@ static cudaError_t launch_pair_rows(const Geom& g, const PipeArgs<T>& a, cudaStr
 
 template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::fwd_rows(const Geom& g, const PipeArgs<T>& a, bool b_side, cudaStream_t s) {
-    return b_side ? launch_fwd_rows<T, SZ>(a.B, a.MB, g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st, a.conditional, s)
-                  : launch_fwd_rows<T, SZ>(a.A, a.MA, g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st, a.conditional, s);
+    const double* wb = a.weighted ? a.WB : nullptr;
+    const double* wa = a.weighted ? a.WA : nullptr;
+    return b_side ? launch_fwd_rows<T, SZ>(a.B, a.MB, wb, g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st, a.conditional, s)
+                  : launch_fwd_rows<T, SZ>(a.A, a.MA, wa, g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st, a.conditional, s);
 }
 
 template <typename T, int SZ>
@@ -155,6 +157,39 @@ cudaError_t Sized<T, SZ>::rows_max_blocks(int KB, bool cb_smem, int* out) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, RowCfg<T, SZ>::THREADS, smem);
     } else {
         return cudaErrorInvalidValue;  // not reached: the B-marginals always fit in shared memory
+    }
+}
+
+template <typename T, int SZ>
+cudaError_t Sized<T, SZ>::pair_rows_w(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
+    if constexpr (std::is_same<T, double>::value) {
+        using C = RowWCfg<SZ>;
+        cudaError_t e = ensure_smem(k_pair_rows_w<SZ>, C::SMEM);
+        if (e != cudaSuccess) return e;
+        k_pair_rows_w<SZ><<<a.rows_grid_w, C::THREADS, C::SMEM, s>>>(a.Y, g, a.tw, a.cbw, a.mi, a.nw, a.st);
+        return cudaGetLastError();
+    } else {
+        (void)g; (void)a; (void)s;
+        return cudaErrorNotSupported;  // weighted maps need FP64 transforms
+    }
+}
+
+template <typename T, int SZ>
+size_t Sized<T, SZ>::rows_w_smem() {
+    if constexpr (std::is_same<T, double>::value) return RowWCfg<SZ>::SMEM;
+    else return 0;
+}
+
+template <typename T, int SZ>
+cudaError_t Sized<T, SZ>::rows_w_max_blocks(int* out) {
+    if constexpr (std::is_same<T, double>::value) {
+        using C = RowWCfg<SZ>;
+        cudaError_t e = ensure_smem(k_pair_rows_w<SZ>, C::SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pair_rows_w<SZ>, C::THREADS, C::SMEM);
+    } else {
+        *out = 0;
+        return cudaSuccess;
     }
 }
 

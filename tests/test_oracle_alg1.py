@@ -122,3 +122,32 @@ def test_nmi_closed_forms():
     ok = r2["h_ab"] > 0
     assert np.all(r2["nmi"][ok] >= 1.0 - 1e-12) and np.all(r2["nmi"][ok] <= 2.0 + 1e-12)
     assert np.all(r2["nmi"][~ok] == 0.0)
+
+
+def test_swmi_pins():
+    """SWMI (Sec. 3): unit weights give the binary CMIF; 0/1 weights give the
+    masked CMIF; scaling a weight image leaves MI unchanged (the relative
+    frequencies do not change); for A = B at chi = 0 the weighted joint
+    histogram is diagonal with weights w^2, so MI = the entropy of the labels
+    weighted by w^2 (scipy)."""
+    rng = np.random.default_rng(8)
+    A = rng.integers(0, 4, (9, 11)).astype(np.int32)
+    B = rng.integers(0, 3, (7, 10)).astype(np.int32)
+    ref = oracle.cmif(A, None, B, None, 4, 3)
+    r = oracle.swmi(A, None, B, None, 4, 3)
+    assert np.abs(r["mi"] - ref["mi"]).max() < 1e-12 and np.array_equal(r["nw"], ref["n"])
+    MA = (rng.random(A.shape) > 0.3).astype(np.uint8)
+    MB = (rng.random(B.shape) > 0.3).astype(np.uint8)
+    refm = oracle.cmif(A, MA, B, MB, 4, 3)
+    rm = oracle.swmi(A, MA.astype(float), B, MB.astype(float), 4, 3)
+    assert np.abs(rm["mi"] - refm["mi"]).max() < 1e-12 and np.array_equal(rm["nw"], refm["n"])
+    WA = rng.random(A.shape)
+    WB = rng.random(B.shape)
+    r1 = oracle.swmi(A, WA, B, WB, 4, 3)
+    r2 = oracle.swmi(A, 3.7 * WA, B, WB, 4, 3)
+    assert np.abs(r1["mi"] - r2["mi"]).max() < 1e-12
+    assert np.allclose(r2["nw"], 3.7 * r1["nw"])
+    w = rng.random(A.shape) + 0.1
+    rs = oracle.swmi(A, w, A, w, 4, 4)
+    hw = scipy_stats.entropy(np.bincount(A.ravel(), weights=(w * w).ravel(), minlength=4), base=2)
+    assert abs(rs["mi"][8, 10] - hw) < 1e-12
