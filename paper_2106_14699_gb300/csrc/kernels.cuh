@@ -175,7 +175,8 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const 
     const int32_t* xr = X + (size_t)y * W;
     const uint8_t* mr = MX ? MX + (size_t)y * W : nullptr;
     bool bad = false;
-    const double* wr = WX ? WX + (size_t)y * W : nullptr;
+    // weighted maps run with FP64 transforms only: the other precisions never read weights
+    const double* wr = std::is_same<T, double>::value && WX ? WX + (size_t)y * W : nullptr;
     for (int x = threadIdx.x; x < W; x += C::THREADS) {
         const int lab = __ldg(xr + x);
         bool m = mr ? (__ldg(mr + x) != 0) : true;
@@ -194,7 +195,10 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const 
     auto load = [&](int x) -> cpx<T> {
         if (!active || x >= W) return {T(0), T(0)};
         const int c = code[x];
-        const T one = wr ? T(wts[x]) : T(1);
+        T one = T(1);
+        if constexpr (std::is_same<T, double>::value) {
+            if (wr) one = wts[x];
+        }
         return {c == la ? one : T(0), c == lb ? one : T(0)};
     };
     cpx<T> v[M];

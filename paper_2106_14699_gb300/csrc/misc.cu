@@ -36,24 +36,11 @@ __global__ void k_peak_partial(const double* __restrict__ mi, const NT* __restri
     const long long cnt = (long long)(r1 - r0) * wc;
     double bm = -INFINITY;
     long long bi = -1;
-    // four independent (coalesced) elements per thread and iteration, so that the
-    // loads of an iteration are in flight together
-    const long long S = (long long)gridDim.x * blockDim.x;
-    for (long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; t0 < cnt; t0 += 4 * S) {
-        long long idx[4];
-        double nv[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long t = t0 + k * S;
-            idx[k] = t < cnt ? (long long)(r0 + t / wc) * Cout + c0 + t % wc : -1;
-            nv[k] = idx[k] >= 0 ? (double)n[idx[k]] : -1.0;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (idx[k] >= 0 && nv[k] >= thr) {
-                const double m = mi[idx[k]];
-                if (bi < 0 || better(m, idx[k], bm, bi)) { bm = m; bi = idx[k]; }
-            }
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x) {
+        const long long i = (long long)(r0 + t / wc) * Cout + c0 + t % wc;
+        if ((double)n[i] >= thr) {
+            const double m = mi[i];
+            if (bi < 0 || better(m, i, bm, bi)) { bm = m; bi = i; }
         }
     }
     __shared__ double sm_m[32];
