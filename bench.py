@@ -213,6 +213,54 @@ def run_profile_shape(args):
                       "workspace_gb": plan.workspace_bytes() / 1e9}), flush=True)
 
 
+class TorchFFTPlain:
+    """Comparison baseline, not this library: the plain frequency-domain form of
+    the same CMIF map with cuFFT through torch.fft and torch elementwise ops (the
+    paper's own PyTorch approach): one-hot level sets, rfft2, per-pair product
+    conj(F_a) F_b, irfft2, rounding, c log2 c sums (FP64 accumulation), MI."""
+
+    def __init__(self, torch, A, MA, B, MB, KA, KB, dev):
+        self.t = torch
+        HA, WA = A.shape
+        HB, WB = B.shape
+        self.R, self.C = HA + HB - 1, WA + WB - 1
+        self.P = 1 << max(4, math.ceil(math.log2(self.R)))
+        self.Q = 1 << max(4, math.ceil(math.log2(self.C)))
+        self.HA, self.WA, self.KA, self.KB = HA, WA, KA, KB
+
+        def planes(X, MX, K):
+            x = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+            m = torch.ones_like(x, dtype=torch.bool) if MX is None else torch.from_numpy(MX).to(dev).bool()
+            out = torch.zeros((K, self.P, self.Q), dtype=torch.float32, device=dev)
+            for k in range(K):
+                out[k, :x.shape[0], :x.shape[1]] = ((x == k) & m).float()
+            return out
+        self.la, self.lb = planes(A, MA, KA), planes(B, MB, KB)
+
+    def __call__(self):
+        t = self.t
+        FA = t.fft.rfft2(self.la)
+        FB = t.fft.rfft2(self.lb)
+        S = t.zeros((self.P, self.Q), dtype=t.float64, device=FA.device)
+        N = t.zeros_like(S)
+        CB = t.zeros((self.KB, self.P, self.Q), dtype=t.float32, device=FA.device)
+        for a in range(self.KA):
+            c = t.round(t.fft.irfft2(t.conj(FA[a])[None] * FB, s=(self.P, self.Q)))  # c[s] = sum_x a(x) b(x + s)
+            ca = c.sum(0)
+            S += (c * t.log2(c.clamp_min(1.0))).sum(0, dtype=t.float64)
+            S -= (ca * t.log2(ca.clamp_min(1.0))).double()
+            CB += c
+            N += ca.double()
+        S -= (CB * t.log2(CB.clamp_min(1.0))).sum(0, dtype=t.float64)
+        mi = t.where(N > 0, (S + N * t.log2(N.clamp_min(1.0))) / N.clamp_min(1.0), t.zeros_like(S))
+        # circular shift index -> map row / column (chi + H_A - 1, chi + W_A - 1)
+        self.out = t.roll(mi, shifts=(self.HA - 1, self.WA - 1), dims=(0, 1))[:self.R, :self.C]
+        return self.out
+
+    def status(self):
+        return ("OK", None, 0)
+
+
 def run_secondary(args):
     """The other configurations as bench lines of the same metric (device-timed, graph replay)."""
     import torch
@@ -221,7 +269,18 @@ def run_secondary(args):
     dev = torch.device("cuda", 0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     d = lambda x: None if x is None else torch.from_numpy(np.ascontiguousarray(x)).to(dev)
-    if args.workload == "swmi":
+    if args.workload == "torchfft":
+        cfg = synth.make_config(3)
+        H, W = cfg["A"].shape
+        plan = TorchFFTPlain(torch, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 16, 16, dev)
+        step = plan
+        units, name = (2 * H - 1) * (2 * W - 1), cfg["name"] + " torch.fft (cuFFT) plain form FP32"
+        # sanity: the same map as this library's, at a few shifts
+        ref = cm.cmif(d(cfg["A"]), d(cfg["M_A"]), d(cfg["B"]), d(cfg["M_B"]), 16, 16, precision=cm.FP32)["mi"]
+        got = plan()
+        torch.cuda.synchronize()
+        print(json.dumps({"torchfft_vs_library_max_abs_mi_diff": float((got - ref).abs().max())}), flush=True)
+    elif args.workload == "swmi":
         cfg = synth.make_config(2)
         H, W = cfg["A"].shape
         plan = cm.Plan(H, W, H, W, 16, 16, cm.FP64, graph=True, weighted=True)
@@ -319,7 +378,9 @@ def run_secondary(args):
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "FP32" in name else "f64",
                       "data": "synthetic", "config": {"workload": name, "units_per_step": units,
                                                        "l2": "flushed between steps (256 MB write)"},
-                      "clocks": clocks, "device_status": {"status": st[0], "max_residual": st[1], "escalations": st[2]}}),
+                      "clocks": clocks, "device_status": {"status": st[0], "max_residual": st[1], "escalations": st[2]},
+                      **({"impl": "torch.fft (cuFFT) plain form: comparison baseline, not this library"}
+                         if args.workload == "torchfft" else {})}),
           flush=True)
 
 
@@ -333,7 +394,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single1024",
                     choices=["single1024", "rotation", "rotation-window", "two-stage", "batch", "single256",
-                             "plain64", "nmi", "swmi"],
+                             "plain64", "nmi", "swmi", "torchfft"],
                     help="single1024 (default, the headline): config 3; rotation: config 4 (512^2, 64 angles); "
                          "batch: config 5 (128 uneven pairs x 4 angles); single256 / plain64: configs 2 / 1")
     ap.add_argument("--profile-shape", default=None,
