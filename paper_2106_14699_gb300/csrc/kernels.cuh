@@ -307,12 +307,10 @@ __device__ __forceinline__ void stage_table(cpx<T>* dst, const cpx<T>* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Pair product + inverse column transform.  Block = (pair, kx block): pairs
-// vary fastest so that the blocks resident at one time read the same few
-// spectrum columns (L2 reuse).  The transformed columns are transposed
-// through shared memory, one half of the rows at a time, into per-group
-// sub-tiles whose column slot is XOR-swizzled by the row (conflict-free
-// writes), and leave as row chunks of TPB adjacent kx.
+// Configuration of the pair-product + inverse column kernel (k_pair_cols below):
+// TPB columns per block, one team of R x M lanes per column; the block's shared
+// memory holds one buffer (the teams' exchange, then the P x TPB output tile,
+// with the transpose scratch aliased on it) and the twiddle tables.
 template <typename T, int P>
 struct PairColsCfg {
     using G = TeamGeom<T, P>;
