@@ -90,12 +90,12 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
                                      window's map rows are computed (rows outside it are returned as MI = 0,
                                      N = 0); max N and the peak are taken over the window.  A call whose window
                                      is empty (B cannot fit inside padded A) returns CMIF_ERR_INVALID_ARG. */
-#define CMIF_FLAG_WEIGHTED 16u    /* the plan computes spatially weighted MI with cmif_compute_weighted (needs
-                                     CMIF_FP64; not with CMIF_FLAG_NMI or CMIF_FLAG_DEBUG_COUNTS) */
 #define CMIF_FLAG_NMI 8u          /* the map (mi_map, mi_maps) holds the normalised MI the paper cites next to MI
                                      (Sec. 2), NMI = (H_A + H_B) / H_AB, from the same counts and fixed-point
                                      entropy sums; 0 where N = 0 or H_AB = 0 (0/0 = 0, Sec. 3.2).  Alg. 1's
                                      argmax and the peaks then maximise NMI. */
+#define CMIF_FLAG_WEIGHTED 16u    /* the plan computes spatially weighted MI with cmif_compute_weighted (needs
+                                     CMIF_FP64; not with CMIF_FLAG_NMI or CMIF_FLAG_DEBUG_COUNTS) */
 
 /* One argmax record of Alg. 1: the displacement chi = (dy, dx) maximising
  * CMIF among shifts with N(chi) >= gamma * max N, for transform angle_idx
@@ -264,8 +264,8 @@ cmif_status cmif_batch_destroy(cmif_batch batch);
 /* Device status of the last call on this plan (synchronises the plan's
  * last stream).  device_side: CMIF_OK, or the first device problem in the
  * order LABEL_RANGE, PRECISION, TIMEOUT.  max_residual: the largest
- * pre-rounding residual of the authoritative precision.  escalations: FP64
- * re-runs done by CMIF_AUTO.  Any output pointer may be NULL. */
+ * pre-rounding residual of the authoritative precision.  escalations:
+ * second-precision re-runs done by CMIF_AUTO.  Any output pointer may be NULL. */
 cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* max_residual, int* escalations);
 
 /* Launch timing (instrumentation, off by default).  When enabled, each
