@@ -212,7 +212,7 @@ class Batch:
     """cmif_batch over pairs given as dicts with device tensors A, M_A, B, M_B, K_A, K_B,
     host angle lists `angles` (radians) and `gamma`."""
 
-    def __init__(self, pairs, precision=FP32, graph=True, window=False):
+    def __init__(self, pairs, precision=FP32, graph=True, window=False, nmi=False):
         self._keep = []
         descs = (PairDesc * len(pairs))()
         for i, p in enumerate(pairs):
@@ -226,7 +226,8 @@ class Batch:
         self._descs = descs
         self._h = ctypes.c_void_p()
         _check(lib().cmif_batch_create(ctypes.byref(self._h), len(pairs), ctypes.cast(descs, ctypes.c_void_p),
-                                       precision, (FLAG_GRAPH if graph else 0) | (FLAG_WINDOW if window else 0)),
+                                       precision, (FLAG_GRAPH if graph else 0) | (FLAG_WINDOW if window else 0) |
+                                       (FLAG_NMI if nmi else 0)),
                "cmif_batch_create")
         self.n = len(pairs)
 

@@ -125,3 +125,51 @@ def test_batch_vs_oracle(cm, graph):
                      p0["K_B"], gamma=0.5)
     assert got[-1][1:4] == direct["peak"][1:4] and abs(got[-1][4] - direct["peak"][4]) <= MI_TOL
     batch.close()
+
+
+@pytest.mark.parametrize("flag", ["window", "nmi"])
+def test_batch_with_window_or_nmi(cm, flag):
+    """Batch plans inherit CMIF_FLAG_WINDOW / CMIF_FLAG_NMI: each pair's result
+    equals a single-pair plan with the same flag."""
+    cfg = synth.make_config(5, scale=0.08)
+    pairs = cfg["pairs"][:4]
+    dev_pairs = [dict(A=_dev(p["A"]), M_A=_dev(p["M_A"]), B=_dev(p["B"]), M_B=_dev(p["M_B"]), K_A=p["K_A"],
+                      K_B=p["K_B"], angles=p["angles"][:2], gamma=0.5) for p in pairs]
+    kw = {flag: True}
+    batch = cm.Batch(dev_pairs, cm.FP32, graph=True, **kw)
+    res = torch.empty(24 * len(dev_pairs), dtype=torch.uint8, device="cuda:0")
+    batch.run(res)
+    torch.cuda.synchronize()
+    assert batch.status()[0] == "OK"
+    got = cm.peaks_from_bytes(res, len(dev_pairs))
+    for i, (p, dp) in enumerate(zip(pairs, dev_pairs)):
+        HA, WA = p["A"].shape
+        HB, WB = p["B"].shape
+        plan = cm.Plan(HA, WA, HB, WB, p["K_A"], p["K_B"], cm.FP32, **kw)
+        top = torch.empty(24, dtype=torch.uint8, device="cuda:0")
+        plan.align_rotations(dp["A"], dp["M_A"], dp["B"], dp["M_B"], dp["angles"], 0.5, 1, top)
+        ref = cm.peaks_from_bytes(top, 1)[0]
+        assert got[i] == ref, (i, got[i], ref)
+        plan.close()
+    batch.close()
+
+
+def test_weighted_graph_replay(cm):
+    """cmif_compute_weighted under graph replay: replays equal the direct call."""
+    rng = np.random.default_rng(4)
+    A = rng.integers(0, 5, (30, 26)).astype(np.int32)
+    B = rng.integers(0, 5, (28, 24)).astype(np.int32)
+    WA, WB = _dev(rng.random(A.shape)), _dev(rng.random(B.shape))
+    R, C = 57, 49
+    outs = []
+    for graph in (False, True):
+        plan = cm.Plan(30, 26, 28, 24, 5, 5, cm.FP64, graph=graph, weighted=True)
+        mi = torch.empty((R, C), dtype=torch.float64, device="cuda:0")
+        for _ in range(2 if graph else 1):
+            mi.fill_(float("nan"))
+            plan.compute_weighted(_dev(A), WA, _dev(B), WB, mi, None, 0.3)
+            torch.cuda.synchronize()
+        outs.append(mi.clone())
+        assert plan.status()[0] == "OK"
+        plan.close()
+    assert torch.equal(outs[0], outs[1])
