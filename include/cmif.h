@@ -118,7 +118,9 @@ cmif_status cmif_plan_create(cmif_plan* out, int H, int W, int K_A, int K_B, cmi
  *   must not exceed 4096 (else CMIF_ERR_UNSUPPORTED).
  *   prec: see cmif_precision.  flags: CMIF_FLAG_*.
  * Allocates the workspace on the current CUDA device, which becomes the
- * plan's device.  On error *out is NULL. */
+ * plan's device.  On error *out is NULL.  The environment variable
+ * CMIF_DISABLE_TMEM=1 at creation makes FP32 plans use the shared-memory row
+ * kernel instead of the Tensor-Memory one (same results; for comparison). */
 cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B,
                                 cmif_precision prec, unsigned flags);
 
