@@ -474,7 +474,7 @@ def main():
         ev1[i].record(stream)
         for name, ms in plan.stage_times():  # synchronises; between steps
             stage.setdefault(name, []).append(ms)
-            launches += 2 if name == "peak" else 1
+            launches += 2 if name in ("peak", "finalize") else 1  # peak: partial + final; finalize: + merge
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
