@@ -124,6 +124,22 @@ cmif_status cmif_plan_create(cmif_plan* out, int H, int W, int K_A, int K_B, cmi
 cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B,
                                 cmif_precision prec, unsigned flags);
 
+/* Create a plan for VOLUMES (Sec. 3.1 with n = 3: the domains are boxes):
+ * A is D_A x H_A x W_A, B is D_B x H_B x W_B (slice-major int32; masks uint8
+ * of the same shape or NULL).  cmif_compute then returns the CMIF over every
+ * displacement chi = (dz, dy, dx), dz in [-(D_A-1), D_B-1] (dy, dx as for
+ * images), as maps of (D_A + D_B - 1) * (H_A + H_B - 1) rows by C columns,
+ * depth-offset major: map row (D_A - 1 + dz) * (H_A + H_B - 1) + (H_A - 1 + dy).
+ * The counts are the 3-D cross-correlations of the level sets: each slice is
+ * transformed as an image, and for every depth offset the products of the
+ * slice spectra are summed over the overlapping slices before the inverse
+ * transform.  The peak record's angle_idx field holds dz.  Limits as
+ * cmif_plan_create_ex with D * H * W <= 2^22 per volume and D <= 1024;
+ * CMIF_FLAG_WINDOW and CMIF_FLAG_WEIGHTED are not supported (UNSUPPORTED), and
+ * cmif_align_rotations / cmif_align_two_stage reject volume plans. */
+cmif_status cmif_plan_create_3d(cmif_plan* out, int D_A, int H_A, int W_A, int D_B, int H_B, int W_B, int K_A,
+                                int K_B, cmif_precision prec, unsigned flags);
+
 /* Free the plan and its workspace (synchronises the plan's device). NULL is ignored. */
 cmif_status cmif_plan_destroy(cmif_plan plan);
 

@@ -34,6 +34,11 @@ Functions and the passages they follow:
                      numpy, small inputs.  Pinned by tests/test_oracle_alg1.py (unit
                      weights = MI, 0/1 weights = masked MI, scale invariance, and the
                      weighted label entropy for A = B).
+* ``cmif3``       -- the CMIF of two label VOLUMES (Sec. 3.1 with n = 3) by the
+                     direct method: at every displacement (dz, dy, dx) the joint
+                     histogram of the overlapping voxels, MI by Eq. mi.  numpy, small
+                     inputs.  Pinned by tests/test_oracle_alg1.py (depth 1 = the C
+                     oracle, N closed form, MI(0) = H(A), swap symmetry).
 * ``align_two_stage`` -- the two-stage rigid search of Sec. 4 (grid, then random
                      refinement in [theta - 2 pi/|Omega|, theta + 2 pi/|Omega|]), the
                      uniform draws passed in.  Pinned by hand-checked compositions.
@@ -345,3 +350,49 @@ def swmi(A, W_A, B, W_B, K_A, K_B):
             nz = p > 0
             mi[r, c] = float((p[nz] * np.log2(p[nz] / (pa @ pb)[nz])).sum())
     return dict(mi=mi, nw=nw)
+
+
+def cmif3(A, M_A, B, M_B, K_A, K_B):
+    """CMIF of label volumes A (D_A x H_A x W_A) and B over every displacement
+    chi = (dz, dy, dx) of the full linear range, by the direct method: the joint
+    histogram of the voxel pairs (A(x), B(x + chi)) where both masks are 1, MI =
+    sum p log2(p / (p_a p_b)) (Eq. mi), 0 where N = 0.  Returns dict(mi, n) as maps
+    of (D_A + D_B - 1) * (H_A + H_B - 1) rows (depth-offset major) by W_A + W_B - 1."""
+    A = np.asarray(A, np.int64)
+    B = np.asarray(B, np.int64)
+    DA, HA, WA = A.shape
+    DB, HB, WB = B.shape
+    ma = np.ones(A.shape, bool) if M_A is None else np.asarray(M_A) != 0
+    mb = np.ones(B.shape, bool) if M_B is None else np.asarray(M_B) != 0
+    R2, C = HA + HB - 1, WA + WB - 1
+    Dz = DA + DB - 1
+    mi = np.zeros((Dz * R2, C))
+    n = np.zeros((Dz * R2, C), np.int64)
+
+    def span(d, la, lb):
+        return max(0, -d), min(la, lb - d)
+    for zi in range(Dz):
+        dz = zi - (DA - 1)
+        z0, z1 = span(dz, DA, DB)
+        for r in range(R2):
+            dy = r - (HA - 1)
+            y0, y1 = span(dy, HA, HB)
+            for c in range(C):
+                dx = c - (WA - 1)
+                x0, x1 = span(dx, WA, WB)
+                if z1 <= z0 or y1 <= y0 or x1 <= x0:
+                    continue
+                a = A[z0:z1, y0:y1, x0:x1]
+                b = B[z0 + dz:z1 + dz, y0 + dy:y1 + dy, x0 + dx:x1 + dx]
+                keep = ma[z0:z1, y0:y1, x0:x1] & mb[z0 + dz:z1 + dz, y0 + dy:y1 + dy, x0 + dx:x1 + dx]
+                if not keep.any():
+                    continue
+                joint = np.bincount(a[keep] * K_B + b[keep], minlength=K_A * K_B).reshape(K_A, K_B)
+                tot = int(joint.sum())
+                n[zi * R2 + r, c] = tot
+                p = joint / tot
+                pa = p.sum(axis=1, keepdims=True)
+                pb = p.sum(axis=0, keepdims=True)
+                nz = p > 0
+                mi[zi * R2 + r, c] = float((p[nz] * np.log2(p[nz] / (pa @ pb)[nz])).sum())
+    return dict(mi=mi, n=n)

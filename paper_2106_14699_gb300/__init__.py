@@ -47,7 +47,7 @@ class Peak(ctypes.Structure):
                 ("n", ctypes.c_int32), ("mi", ctypes.c_double)]
 
 
-EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_destroy", "cmif_plan_workspace_bytes",
+EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_create_3d", "cmif_plan_destroy", "cmif_plan_workspace_bytes",
            "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
            "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_rotate_nn", "cmif_align_rotations",
            "cmif_align_two_stage", "cmif_compute_weighted", "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status",
@@ -67,6 +67,7 @@ def lib():
         P, I, D, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint
         L.cmif_plan_create.argtypes = [ctypes.POINTER(P), I, I, I, I, I]
         L.cmif_plan_create_ex.argtypes = [ctypes.POINTER(P), I, I, I, I, I, I, I, U]
+        L.cmif_plan_create_3d.argtypes = [ctypes.POINTER(P), I, I, I, I, I, I, I, I, I, U]
         L.cmif_plan_destroy.argtypes = [P]
         L.cmif_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         L.cmif_compute.argtypes = [P, P, P, P, P, P, P, P, D, P, P]
@@ -206,6 +207,23 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class VolumePlan(Plan):
+    """A CMIF plan for volumes D_A x H_A x W_A and D_B x H_B x W_B (cmif_plan_create_3d);
+    compute() then fills maps of (D_A + D_B - 1) * (H_A + H_B - 1) rows by W_A + W_B - 1
+    columns (depth-offset major), and the peak's first field is dz."""
+
+    def __init__(self, D_A, H_A, W_A, D_B, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False, graph=False,
+                 nmi=False):
+        self._h = ctypes.c_void_p()
+        flags = (FLAG_DEBUG_COUNTS if debug_counts else 0) | (FLAG_GRAPH if graph else 0) | (FLAG_NMI if nmi else 0)
+        _check(lib().cmif_plan_create_3d(ctypes.byref(self._h), D_A, H_A, W_A, D_B, H_B, W_B, K_A, K_B, precision,
+                                         flags), "cmif_plan_create_3d")
+        self.D_A, self.D_B = D_A, D_B
+        self.H_A, self.W_A, self.H_B, self.W_B, self.K_A, self.K_B = H_A, W_A, H_B, W_B, K_A, K_B
+        self.precision = precision
+        self.R, self.C = (D_A + D_B - 1) * (H_A + H_B - 1), W_A + W_B - 1
 
 
 class Batch:

@@ -123,10 +123,10 @@ template <typename T>
 size_t workspace_bytes(const Geom& g, const Workspace<T>& w) {
     const size_t cs = sizeof(cpx<T>);
     size_t off = 0;
-    off = align_up(off + (size_t)g.KA * g.HA * g.Qs * cs, 256);  // T1A
-    off = align_up(off + (size_t)g.KB * g.HB * g.Qs * cs, 256);  // T1B
-    off = align_up(off + (size_t)g.KA * g.Qh * g.P * cs, 256);   // FA
-    off = align_up(off + (size_t)g.KB * g.Qh * g.P * cs, 256);   // FB
+    off = align_up(off + (size_t)g.KA * g.DA * g.HA * g.Qs * cs, 256);  // T1A
+    off = align_up(off + (size_t)g.KB * g.DB * g.HB * g.Qs * cs, 256);  // T1B
+    off = align_up(off + (size_t)g.KA * g.DA * g.Qh * g.P * cs, 256);   // FA
+    off = align_up(off + (size_t)g.KB * g.DB * g.Qh * g.P * cs, 256);   // FB
     off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);  // Y
     off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);  // CB
     off = align_up(off + sizeof(int), 256);  // work counter
@@ -142,10 +142,10 @@ template <typename T>
 void carve_workspace(const Geom& g, Workspace<T>& w, char* base) {
     const size_t cs = sizeof(cpx<T>);
     size_t off = 0;
-    w.args.T1A = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.HA * g.Qs * cs, 256);
-    w.args.T1B = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.HB * g.Qs * cs, 256);
-    w.args.FA = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.Qh * g.P * cs, 256);
-    w.args.FB = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.Qh * g.P * cs, 256);
+    w.args.T1A = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.DA * g.HA * g.Qs * cs, 256);
+    w.args.T1B = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.DB * g.HB * g.Qs * cs, 256);
+    w.args.FA = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.DA * g.Qh * g.P * cs, 256);
+    w.args.FB = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.DB * g.Qh * g.P * cs, 256);
     w.args.Y = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);
     w.args.cb_global = w.cb_smem ? nullptr : (float*)(base + off);
     off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);
@@ -289,10 +289,14 @@ cmif_status compute_map(cmif_plan p, const Geom& g, const int32_t* A, const uint
 // Validate sizes and flags, set the geometry, pick kernels; allocates nothing
 // (except the per-device twiddle tables on first use).
 cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B, cmif_precision prec,
-                      unsigned flags) {
+                      unsigned flags, int D_A = 1, int D_B = 1) {
     if (H_A < 1 || W_A < 1 || H_B < 1 || W_B < 1 || K_A < 1 || K_B < 1 || K_A > 64 || K_B > 64)
         return CMIF_ERR_INVALID_ARG;
-    if ((long long)H_A * W_A > (1LL << 22) || (long long)H_B * W_B > (1LL << 22)) return CMIF_ERR_INVALID_ARG;
+    if (D_A < 1 || D_B < 1 || D_A > 1024 || D_B > 1024) return CMIF_ERR_INVALID_ARG;
+    if ((long long)D_A * H_A * W_A > (1LL << 22) || (long long)D_B * H_B * W_B > (1LL << 22))
+        return CMIF_ERR_INVALID_ARG;
+    const bool volume = D_A > 1 || D_B > 1;
+    if (volume && (flags & (CMIF_FLAG_WINDOW | CMIF_FLAG_WEIGHTED))) return CMIF_ERR_UNSUPPORTED;
     if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI | CMIF_FLAG_WEIGHTED))
         return CMIF_ERR_INVALID_ARG;
     // weighted maps: FP64 transforms (real counts, no rounding), MI only
@@ -301,9 +305,11 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     if (prec != CMIF_FP32 && prec != CMIF_SPLIT32 && prec != CMIF_FP64 && prec != CMIF_AUTO) return CMIF_ERR_INVALID_ARG;
     Geom g{};
     g.HA = H_A; g.WA = W_A; g.HB = H_B; g.WB = W_B; g.KA = K_A; g.KB = K_B;
-    g.R = H_A + H_B - 1;
+    g.DA = D_A; g.DB = D_B; g.Dz = D_A + D_B - 1;
+    g.R2 = H_A + H_B - 1;
+    g.R = g.Dz * g.R2;
     g.C = W_A + W_B - 1;
-    g.P = pow2_at_least(g.R, 16);
+    g.P = pow2_at_least(g.R2, 16);
     g.Q = pow2_at_least(g.C, 16);
     if (g.P > 4096 || g.Q > 4096) return CMIF_ERR_UNSUPPORTED;
     g.Qh = g.Q / 2 + 1;
@@ -491,13 +497,14 @@ struct cmif_batch_s {
 
 extern "C" {
 
-cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B,
-                                cmif_precision prec, unsigned flags) {
+namespace {
+cmif_status plan_create(cmif_plan* out, int D_A, int H_A, int W_A, int D_B, int H_B, int W_B, int K_A, int K_B,
+                        cmif_precision prec, unsigned flags) {
     if (!out) return CMIF_ERR_INVALID_ARG;
     *out = nullptr;
     cmif_plan p = new (std::nothrow) cmif_plan_s();
     if (!p) return CMIF_ERR_OOM;
-    cmif_status st = plan_init(p, H_A, W_A, H_B, W_B, K_A, K_B, prec, flags);
+    cmif_status st = plan_init(p, H_A, W_A, H_B, W_B, K_A, K_B, prec, flags, D_A, D_B);
     if (st == CMIF_OK) {
         const size_t bytes = plan_bytes(p);
         cudaError_t e = cudaMalloc(&p->mem, bytes);
@@ -513,6 +520,17 @@ cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W
     }
     *out = p;
     return CMIF_OK;
+}
+}  // namespace
+
+cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B,
+                                cmif_precision prec, unsigned flags) {
+    return plan_create(out, 1, H_A, W_A, 1, H_B, W_B, K_A, K_B, prec, flags);
+}
+
+cmif_status cmif_plan_create_3d(cmif_plan* out, int D_A, int H_A, int W_A, int D_B, int H_B, int W_B, int K_A,
+                                int K_B, cmif_precision prec, unsigned flags) {
+    return plan_create(out, D_A, H_A, W_A, D_B, H_B, W_B, K_A, K_B, prec, flags);
 }
 
 cmif_status cmif_plan_create(cmif_plan* out, int H, int W, int K_A, int K_B, cmif_precision prec) {
@@ -623,7 +641,7 @@ cmif_status cmif_compute_host(cmif_plan plan, const int32_t* A, const uint8_t* M
     if (!(gamma >= 0.0 && gamma <= 1.0)) return CMIF_ERR_INVALID_ARG;
     DeviceGuard dg(plan->device);
     const Geom& g = plan->g;
-    const size_t nA = (size_t)g.HA * g.WA, nB = (size_t)g.HB * g.WB, RC = (size_t)g.R * g.C;
+    const size_t nA = (size_t)g.DA * g.HA * g.WA, nB = (size_t)g.DB * g.HB * g.WB, RC = (size_t)g.R * g.C;
     size_t off = 0;
     const size_t oA = off; off = align_up(off + nA * 4, 256);
     const size_t oB = off; off = align_up(off + nB * 4, 256);
@@ -690,7 +708,7 @@ cmif_status cmif_rotate_nn(const int32_t* B, const uint8_t* M_B, int H, int W, d
 cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
                                  const uint8_t* M_B, const double* angles_rad_host, int n_angles, double gamma,
                                  int top_k, cmif_peak* topk_dev, double* mi_maps, void* stream) {
-    if (!plan || !A || !B || !angles_rad_host || !topk_dev) return CMIF_ERR_INVALID_ARG;
+    if (!plan || !A || !B || !angles_rad_host || !topk_dev || plan->g.Dz > 1) return CMIF_ERR_INVALID_ARG;
     if (n_angles < 1 || n_angles > kMaxAngles || top_k < 1 || top_k > n_angles) return CMIF_ERR_INVALID_ARG;
     if (!(gamma >= 0.0 && gamma <= 1.0)) return CMIF_ERR_INVALID_ARG;
     for (int i = 0; i < n_angles; ++i)
@@ -712,7 +730,7 @@ cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t
 cmif_status cmif_align_two_stage(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
                                  const uint8_t* M_B, int n_grid, const double* refine_u_host, int n_refine,
                                  double gamma, cmif_peak* best_host, double* best_angle_rad, void* stream) {
-    if (!plan || !A || !B || !best_host || !best_angle_rad) return CMIF_ERR_INVALID_ARG;
+    if (!plan || !A || !B || !best_host || !best_angle_rad || plan->g.Dz > 1) return CMIF_ERR_INVALID_ARG;
     if (n_grid < 1 || n_grid > kMaxAngles || n_refine < 0 || n_refine > kMaxAngles || (n_refine > 0 && !refine_u_host))
         return CMIF_ERR_INVALID_ARG;
     for (int i = 0; i < n_refine; ++i)

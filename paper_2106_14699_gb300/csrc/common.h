@@ -32,6 +32,11 @@ struct Geom {
     // rows [r0, r1) x columns [c0, c1) (max N and the peak are taken over it).
     // The whole map unless Alg. 1's padded window is on.
     int r0, r1, c0, c1;
+    // Volumes (D_A x H_A x W_A and D_B x H_B x W_B, Sec. 3.1 for n = 3): the
+    // slices are transformed as images; Dz = D_A + D_B - 1 depth offsets, R2 =
+    // H_A + H_B - 1 rows per depth offset, and the maps have R = Dz * R2 rows
+    // (depth-offset major).  Images: DA = DB = Dz = 1, R2 = R.
+    int DA, DB, Dz, R2;
 };
 
 constexpr float kResidualGuard = 0.25f;  // a count whose pre-rounding residual reaches this is not trusted

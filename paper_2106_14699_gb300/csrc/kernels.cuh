@@ -340,15 +340,20 @@ struct PairColsCfg {
 // block's next item are already in flight, and items at the head of a kx
 // block ask L2 for the spectrum columns two kx blocks ahead.  work_ctr must
 // be zero at launch.
-template <typename T, int P>
+// VOL (volumes): items are (pair, depth offset dz, kx block); the product is
+// the sum over the slices z of conj(F_a,z) F_b,z+dz (the 3-D correlation's
+// depth sum, taken before the inverse transform, which is linear), and the
+// output row of depth offset index dzo is dzo * R2 + (the image's output row).
+template <typename T, int P, bool VOL>
 __global__ void __launch_bounds__(PairColsCfg<T, P>::THREADS, PairColsCfg<T, P>::MIN_BLOCKS)
 k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA, int KB, int Qh, int HA, int HB,
             int Rout, int Qs, int r0, int r1, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st,
-            int conditional, int* __restrict__ work_ctr) {
+            int conditional, int* __restrict__ work_ctr, int DA, int DB, int R2) {
     using C = PairColsCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB, NQ = C::NQ;
-    const int npairs = KA * KB, nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb;
+    const int Dz = VOL ? DA + DB - 1 : 1;
+    const int npairs = KA * KB, nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb * Dz;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_item;
     cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -368,6 +373,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     // carrying the 1/(P Q) of the inverse.
     cpx<T> v[M];
     auto load_fa = [&](int it) {
+        if constexpr (VOL) return;  // volumes sum over slices in the item itself
         const int kx = (it / npairs) * TPB + team, a = (it % npairs) / KB;
         if (kx < Qh) {
             const cpx<T>* ga = FA + ((size_t)a * Qh + kx) * P + r * NQ + j;
@@ -382,14 +388,29 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     while (true) {
         int next = 0;
         if (threadIdx.x == 0) next = atomicAdd(work_ctr, 1);
-        const int pair = item % npairs, kxb = item / npairs;
+        const int pair = item % npairs;
+        const int kxb = VOL ? item / npairs / Dz : item / npairs;
+        const int dzo = VOL ? (item / npairs) % Dz : 0;
         const int kx0 = kxb * TPB, kx = kx0 + team, b = pair % KB;
-        if (kx < Qh) {
+        if constexpr (VOL) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) v[i] = {T(0), T(0)};
+            if (kx < Qh) {
+                const int a = pair / KB, dz = dzo - (DA - 1);
+                const int z0 = dz < 0 ? -dz : 0, z1 = DA < DB - dz ? DA : DB - dz;
+                for (int z = z0; z < z1; ++z) {
+                    const cpx<T>* ga = FA + ((size_t)(a * DA + z) * Qh + kx) * P + r * NQ + j;
+                    const cpx<T>* gb = FB + ((size_t)(b * DB + z + dz) * Qh + kx) * P + r * NQ + j;
+#pragma unroll
+                    for (int i = 0; i < M; ++i) v[i] = v[i] + cmulc(__ldg(gb + M * i), __ldg(ga + M * i));
+                }
+            }
+        } else if (kx < Qh) {
             const cpx<T>* gb = FB + ((size_t)b * Qh + kx) * P + r * NQ + j;
 #pragma unroll
             for (int i = 0; i < M; ++i) v[i] = cmulc(__ldg(gb + M * i), v[i]);
         }
-        if (pair < KA + KB && (int)threadIdx.x < TPB && kxb + 2 < nkxb) {
+        if (!VOL && pair < KA + KB && (int)threadIdx.x < TPB && kxb + 2 < nkxb) {
             // the items of this kx block with pair < K_A + K_B each prefetch one
             // spectrum's columns of kx block kxb + 2 into L2 (one bulk request per column)
             const int kf = (kxb + 2) * TPB + threadIdx.x;
@@ -464,7 +485,11 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                     const float4* src = reinterpret_cast<const float4*>(xbuf) + row0 * PPR + (h ^ (sw >> 1));
                     float4* dst = reinterpret_cast<float4*>(yp + kx0) + h;
                     for (int row = row0; row < P; row += ROWS, src += ROWS * PPR) {
-                        const int orow = circ_to_out(row, P, HA, HB - 1);
+                        int orow = circ_to_out(row, P, HA, HB - 1);
+                        if constexpr (VOL) {
+                            if (orow < 0) continue;
+                            orow += dzo * R2;
+                        }
                         if (orow < r0 || orow >= r1) continue;
                         float4 pv = *src;
                         if (swap_halves) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
@@ -474,7 +499,11 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             } else {
                 for (int q = threadIdx.x; q < P * PPR; q += C::THREADS) {
                     const int row = q / PPR, h = q % PPR;
-                    const int orow = circ_to_out(row, P, HA, HB - 1);
+                    int orow = circ_to_out(row, P, HA, HB - 1);
+                    if constexpr (VOL) {
+                        if (orow < 0) continue;
+                        orow += dzo * R2;
+                    }
                     if (orow < r0 || orow >= r1 || kx0 + 2 * h >= Qs) continue;
                     const int sw = (row >> C::SWZ) & (TPB - 1);
                     float4 pv = reinterpret_cast<const float4*>(xbuf)[row * PPR + (h ^ (sw >> 1))];
@@ -486,7 +515,11 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             // one complex per lane, adjacent lanes on adjacent columns of a row
             for (int q = threadIdx.x; q < P * TPB; q += C::THREADS) {
                 const int row = q / TPB, c = q % TPB;
-                const int orow = circ_to_out(row, P, HA, HB - 1);
+                int orow = circ_to_out(row, P, HA, HB - 1);
+                if constexpr (VOL) {
+                    if (orow < 0) continue;
+                    orow += dzo * R2;
+                }
                 if (orow < r0 || orow >= r1 || kx0 + c >= Qs) continue;
                 const int sw = (row >> C::SWZ) & (TPB - 1);
                 yp[(size_t)orow * Qs + kx0 + c] = xbuf[(size_t)row * TPB + (c ^ sw)];

@@ -60,9 +60,11 @@ __global__ void k_peak_partial(const double* __restrict__ mi, const NT* __restri
     }
 }
 
+// R2 > 0 (volumes): the map rows are (depth offset, row) pairs, depth-offset
+// major; the record's first field then holds the depth offset dz.
 template <typename NT>
 __global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, const double* __restrict__ mi,
-                             const NT* __restrict__ n, int HA, int WA, int Cout, int angle_idx,
+                             const NT* __restrict__ n, int HA, int WA, int Cout, int angle_idx, int R2, int DA,
                              void* __restrict__ peak_out) {
     double bm = -INFINITY;
     long long bi = -1;
@@ -83,8 +85,9 @@ __global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, con
         if (sm_i[k] >= 0 && (bi < 0 || better(sm_m[k], sm_i[k], bm, bi))) { bm = sm_m[k]; bi = sm_i[k]; }
     PeakRec* p = reinterpret_cast<PeakRec*>(peak_out);
     if (bi < 0) { *p = {-1, 0, 0, 0, 0.0}; return; }
-    p->angle_idx = angle_idx;
-    p->dy = (int)(bi / Cout) - (HA - 1);
+    const long long row = bi / Cout;
+    p->angle_idx = R2 > 0 ? (int)(row / R2) - (DA - 1) : angle_idx;
+    p->dy = (int)(R2 > 0 ? row % R2 : row) - (HA - 1);
     p->dx = (int)(bi % Cout) - (WA - 1);
     p->n = n_record(n[bi]);  // weighted maps: N rounded to an integer
     p->mi = bm;
@@ -212,7 +215,8 @@ static cudaError_t launch_peak_t(const double* mi, const NT* n, const Geom& g, c
                                  PeakPart* parts, int nparts, int angle_idx, void* peak_out, cudaStream_t s) {
     const int HA = g.HA, WA = g.WA, Cout = g.C;
     k_peak_partial<NT><<<nparts, 256, 0, s>>>(mi, n, Cout, g.r0, g.r1, g.c0, g.c1, st, gamma, parts);
-    k_peak_final<NT><<<1, 256, 0, s>>>(parts, nparts, mi, n, HA, WA, Cout, angle_idx, peak_out);
+    k_peak_final<NT><<<1, 256, 0, s>>>(parts, nparts, mi, n, HA, WA, Cout, angle_idx, g.Dz > 1 ? g.R2 : 0, g.DA,
+                                         peak_out);
     return cudaGetLastError();
 }
 

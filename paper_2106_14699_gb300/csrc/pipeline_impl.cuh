@@ -42,10 +42,10 @@ static cudaError_t launch_fwd_cols(const cpx<T>* T1, int H, int K, int Qh, int Q
     return cudaGetLastError();
 }
 
-template <typename T, int P>
+template <typename T, int P, bool VOL>
 static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     using C = PairColsCfg<T, P>;
-    auto kern = k_pair_cols<T, P>;
+    auto kern = k_pair_cols<T, P, VOL>;
     const size_t smem = pair_cols_smem<T, P>();
     cudaError_t e = ensure_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -57,13 +57,13 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
         if (e != cudaSuccess) return e;
         per_sm = n > 0 ? n : 1;
     }
-    const long long items = (long long)g.KA * g.KB * ((g.Qh + C::TPB - 1) / C::TPB);
+    const long long items = (long long)g.KA * g.KB * ((g.Qh + C::TPB - 1) / C::TPB) * (VOL ? g.Dz : 1);
     const long long slots = a.num_sms > 0 ? (long long)per_sm * a.num_sms : items;
     const int grid = (int)(items < slots ? items : slots);
     e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KA, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, g.r0, g.r1, a.Y, a.tw,
-                                        a.st, a.conditional, a.work_ctr);
+                                        a.st, a.conditional, a.work_ctr, g.DA, g.DB, g.R2);
     return cudaGetLastError();
 }
 
@@ -109,21 +109,26 @@ template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::fwd_rows(const Geom& g, const PipeArgs<T>& a, bool b_side, cudaStream_t s) {
     const double* wb = a.weighted ? a.WB : nullptr;
     const double* wa = a.weighted ? a.WA : nullptr;
-    return b_side ? launch_fwd_rows<T, SZ>(a.B, a.MB, wb, g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st, a.conditional, s)
-                  : launch_fwd_rows<T, SZ>(a.A, a.MA, wa, g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st, a.conditional, s);
+    // volumes: the D slices of H rows are D * H rows of one image
+    return b_side ? launch_fwd_rows<T, SZ>(a.B, a.MB, wb, g.DB * g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st,
+                                           a.conditional, s)
+                  : launch_fwd_rows<T, SZ>(a.A, a.MA, wa, g.DA * g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st,
+                                           a.conditional, s);
 }
 
 template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::fwd_cols(const Geom& g, const PipeArgs<T>& a, bool b_side, cudaStream_t s) {
     // B's spectra carry the 1/(P Q) of the unnormalised inverse transform (a power of two: exact)
-    return b_side ? launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional,
+    // volumes: K * D slice planes of H rows each (plane index label * D + z)
+    return b_side ? launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB * g.DB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional,
                                            T(1.0 / ((double)g.P * (double)g.Q)), s)
-                  : launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional, T(1), s);
+                  : launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA * g.DA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional,
+                                           T(1), s);
 }
 
 template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
-    return launch_pair_cols<T, SZ>(g, a, s);
+    return g.Dz > 1 ? launch_pair_cols<T, SZ, true>(g, a, s) : launch_pair_cols<T, SZ, false>(g, a, s);
 }
 
 template <typename T, int SZ>

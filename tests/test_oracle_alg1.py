@@ -151,3 +151,29 @@ def test_swmi_pins():
     rs = oracle.swmi(A, w, A, w, 4, 4)
     hw = scipy_stats.entropy(np.bincount(A.ravel(), weights=(w * w).ravel(), minlength=4), base=2)
     assert abs(rs["mi"][8, 10] - hw) < 1e-12
+
+
+def test_cmif3_pins():
+    """Volumes: depth 1 reproduces the 2-D C oracle; full masks give
+    N = (D - |dz|)(H - |dy|)(W - |dx|) for equal sizes; A = B at chi = 0 gives
+    MI = H(A) (scipy); CMIF3(chi; A, B) = CMIF3(-chi; B, A)."""
+    rng = np.random.default_rng(13)
+    A2 = rng.integers(0, 3, (7, 8)).astype(np.int32)
+    B2 = rng.integers(0, 3, (6, 9)).astype(np.int32)
+    r3 = oracle.cmif3(A2[None], None, B2[None], None, 3, 3)
+    r2 = oracle.cmif(A2, None, B2, None, 3, 3)
+    assert np.abs(r3["mi"] - r2["mi"]).max() < 1e-12 and np.array_equal(r3["n"], r2["n"])
+    A = rng.integers(0, 4, (3, 5, 6)).astype(np.int32)
+    r = oracle.cmif3(A, None, A, None, 4, 4)
+    D, H, W = A.shape
+    dz = np.arange(2 * D - 1) - (D - 1)
+    dy = np.arange(2 * H - 1) - (H - 1)
+    dx = np.arange(2 * W - 1) - (W - 1)
+    nn = ((D - np.abs(dz))[:, None, None] * (H - np.abs(dy))[None, :, None] * (W - np.abs(dx))[None, None, :])
+    assert np.array_equal(r["n"], nn.reshape((2 * D - 1) * (2 * H - 1), 2 * W - 1))
+    ha = scipy_stats.entropy(np.bincount(A.ravel(), minlength=4), base=2)
+    assert abs(r["mi"][(D - 1) * (2 * H - 1) + H - 1, W - 1] - ha) < 1e-12
+    B = rng.integers(0, 4, (2, 4, 7)).astype(np.int32)
+    rab = oracle.cmif3(A, None, B, None, 4, 4)["mi"].reshape(D + 2 - 1, H + 4 - 1, W + 7 - 1)
+    rba = oracle.cmif3(B, None, A, None, 4, 4)["mi"].reshape(2 + D - 1, 4 + H - 1, 7 + W - 1)
+    assert np.abs(rab - rba[::-1, ::-1, ::-1]).max() < 1e-12
