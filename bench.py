@@ -269,7 +269,21 @@ def run_secondary(args):
     dev = torch.device("cuda", 0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     d = lambda x: None if x is None else torch.from_numpy(np.ascontiguousarray(x)).to(dev)
-    if args.workload == "torchfft":
+    if args.workload == "volume":
+        rng = np.random.default_rng(33)
+        D = H = W = 64
+        Av = rng.integers(0, 8, (D, H, W)).astype(np.int32)
+        Av[:, : H // 2, : W // 3] = 3                      # some structure, then a planted 3-D shift
+        Bv = np.roll(Av, (3, -5, 7), axis=(0, 1, 2))
+        Bv[rng.random(Bv.shape) < 0.1] = 0
+        plan = cm.VolumePlan(D, H, W, D, H, W, 8, 8, cm.FP32, graph=True)
+        mi = torch.empty((plan.R, plan.C), dtype=torch.float64, device=dev)
+        n = torch.empty((plan.R, plan.C), dtype=torch.int32, device=dev)
+        pk = torch.empty(24, dtype=torch.uint8, device=dev)
+        A, B = d(Av), d(Bv)
+        step = lambda: plan.compute(A, None, B, None, mi, n, None, 0.5, pk)
+        units, name = plan.R * plan.C, "volume-64^3-K8 FP32"
+    elif args.workload == "torchfft":
         cfg = synth.make_config(3)
         H, W = cfg["A"].shape
         plan = TorchFFTPlain(torch, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 16, 16, dev)
@@ -394,7 +408,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single1024",
                     choices=["single1024", "rotation", "rotation-window", "two-stage", "batch", "single256",
-                             "plain64", "nmi", "swmi", "torchfft"],
+                             "plain64", "nmi", "swmi", "torchfft", "volume"],
                     help="single1024 (default, the headline): config 3; rotation: config 4 (512^2, 64 angles); "
                          "batch: config 5 (128 uneven pairs x 4 angles); single256 / plain64: configs 2 / 1")
     ap.add_argument("--profile-shape", default=None,
