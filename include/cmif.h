@@ -236,8 +236,9 @@ cmif_status cmif_compute_weighted(cmif_plan plan, const int32_t* A, const double
  *                   refinement angle i, -1 for the identity
  *   best_angle_rad: host; the winning rotation angle (0 for the identity)
  * Synchronous: waits for stage (i) to choose the refinement interval and for
- * stage (ii) to finish.  The plan's flags (CMIF_FLAG_WINDOW, CMIF_FLAG_GRAPH)
- * apply to both stages. */
+ * stage (ii) to finish.  The plan's flags apply to both stages; with
+ * CMIF_FLAG_GRAPH the two stages' different angle lists make every call
+ * capture its graphs anew, so a plan without graph replay is the better fit. */
 cmif_status cmif_align_two_stage(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
                                  const uint8_t* M_B, int n_grid, const double* refine_u_host, int n_refine,
                                  double gamma, cmif_peak* best_host, double* best_angle_rad, void* stream);
