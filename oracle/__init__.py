@@ -356,8 +356,10 @@ def cmif3(A, M_A, B, M_B, K_A, K_B):
     """CMIF of label volumes A (D_A x H_A x W_A) and B over every displacement
     chi = (dz, dy, dx) of the full linear range, by the direct method: the joint
     histogram of the voxel pairs (A(x), B(x + chi)) where both masks are 1, MI =
-    sum p log2(p / (p_a p_b)) (Eq. mi), 0 where N = 0.  Returns dict(mi, n) as maps
-    of (D_A + D_B - 1) * (H_A + H_B - 1) rows (depth-offset major) by W_A + W_B - 1."""
+    sum p log2(p / (p_a p_b)) (Eq. mi), 0 where N = 0; and NMI = (H_A + H_B) / H_AB
+    from the same histogram's entropies (Sec. 2), 0 where N = 0 or H_AB = 0.
+    Returns dict(mi, n, nmi, h_ab) as maps of (D_A + D_B - 1) * (H_A + H_B - 1) rows
+    (depth-offset major) by W_A + W_B - 1."""
     A = np.asarray(A, np.int64)
     B = np.asarray(B, np.int64)
     DA, HA, WA = A.shape
@@ -367,7 +369,13 @@ def cmif3(A, M_A, B, M_B, K_A, K_B):
     R2, C = HA + HB - 1, WA + WB - 1
     Dz = DA + DB - 1
     mi = np.zeros((Dz * R2, C))
+    nmi_map = np.zeros((Dz * R2, C))
+    hab_map = np.zeros((Dz * R2, C))
     n = np.zeros((Dz * R2, C), np.int64)
+
+    def entropy(q):
+        q = q[q > 0]
+        return float(-(q * np.log2(q)).sum())
 
     def span(d, la, lb):
         return max(0, -d), min(la, lb - d)
@@ -395,4 +403,8 @@ def cmif3(A, M_A, B, M_B, K_A, K_B):
                 pb = p.sum(axis=0, keepdims=True)
                 nz = p > 0
                 mi[zi * R2 + r, c] = float((p[nz] * np.log2(p[nz] / (pa @ pb)[nz])).sum())
-    return dict(mi=mi, n=n)
+                h_ab = entropy(p.ravel())
+                hab_map[zi * R2 + r, c] = h_ab
+                if h_ab > 0:
+                    nmi_map[zi * R2 + r, c] = (entropy(pa.ravel()) + entropy(pb.ravel())) / h_ab
+    return dict(mi=mi, n=n, nmi=nmi_map, h_ab=hab_map)

@@ -154,15 +154,17 @@ def test_swmi_pins():
 
 
 def test_cmif3_pins():
-    """Volumes: depth 1 reproduces the 2-D C oracle; full masks give
+    """Volumes: depth 1 reproduces the 2-D C oracle (MI, N and NMI); full masks give
     N = (D - |dz|)(H - |dy|)(W - |dx|) for equal sizes; A = B at chi = 0 gives
-    MI = H(A) (scipy); CMIF3(chi; A, B) = CMIF3(-chi; B, A)."""
+    MI = H(A) (scipy) and NMI = 2; labels that vary along different axes are
+    independent at chi = 0 (NMI = 1, MI = 0); CMIF3(chi; A, B) = CMIF3(-chi; B, A)."""
     rng = np.random.default_rng(13)
     A2 = rng.integers(0, 3, (7, 8)).astype(np.int32)
     B2 = rng.integers(0, 3, (6, 9)).astype(np.int32)
     r3 = oracle.cmif3(A2[None], None, B2[None], None, 3, 3)
     r2 = oracle.cmif(A2, None, B2, None, 3, 3)
     assert np.abs(r3["mi"] - r2["mi"]).max() < 1e-12 and np.array_equal(r3["n"], r2["n"])
+    assert np.abs(r3["nmi"] - oracle.nmi(A2, None, B2, None, 3, 3)["nmi"]).max() < 1e-12
     A = rng.integers(0, 4, (3, 5, 6)).astype(np.int32)
     r = oracle.cmif3(A, None, A, None, 4, 4)
     D, H, W = A.shape
@@ -173,6 +175,16 @@ def test_cmif3_pins():
     assert np.array_equal(r["n"], nn.reshape((2 * D - 1) * (2 * H - 1), 2 * W - 1))
     ha = scipy_stats.entropy(np.bincount(A.ravel(), minlength=4), base=2)
     assert abs(r["mi"][(D - 1) * (2 * H - 1) + H - 1, W - 1] - ha) < 1e-12
+    assert abs(r["nmi"][(D - 1) * (2 * H - 1) + H - 1, W - 1] - 2.0) < 1e-12
+    zz, yy, xx = np.mgrid[0:4, 0:3, 0:6]
+    Az = (zz % 2).astype(np.int32)           # varies along depth only
+    Bx = (xx % 2).astype(np.int32)           # varies along width only
+    ri = oracle.cmif3(Az, None, Bx, None, 2, 2)
+    c0 = (4 - 1) * (2 * 3 - 1) + 3 - 1
+    assert abs(ri["nmi"][c0, 6 - 1] - 1.0) < 1e-12 and abs(ri["mi"][c0, 6 - 1]) < 1e-12
+    pos = ri["nmi"] > 0                      # H_AB > 0; elsewhere one label only on each side: MI = 0
+    assert np.all(ri["nmi"][pos] >= 1.0 - 1e-12) and np.all(ri["nmi"] <= 2.0 + 1e-12)
+    assert np.all(np.abs(ri["mi"][~pos]) < 1e-12)
     B = rng.integers(0, 4, (2, 4, 7)).astype(np.int32)
     rab = oracle.cmif3(A, None, B, None, 4, 4)["mi"].reshape(D + 2 - 1, H + 4 - 1, W + 7 - 1)
     rba = oracle.cmif3(B, None, A, None, 4, 4)["mi"].reshape(2 + D - 1, 4 + H - 1, 7 + W - 1)
