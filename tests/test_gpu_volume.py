@@ -76,3 +76,44 @@ def test_volume_planted_shift_and_depth1(cm):
     mi1, n1, pk1, _ = _run(cm, A2[None], None, B2[None], None, 6, cm.FP32)
     ref = cm.cmif(_dev(A2), None, _dev(B2), None, 6, 6, precision=cm.FP32, gamma=0.5)
     assert np.array_equal(mi1, ref["mi"].cpu().numpy()) and np.array_equal(n1, ref["n"].cpu().numpy())
+
+
+
+def test_volume_host_entry_auto_and_nmi(cm):
+    """Volume plans through the host-buffer entry point (copies of D*H*W voxels)
+    with AUTO precision, and NMI maps of a volume plan against the oracle's
+    (H_A + H_B) / H_AB: each entropy is within ~1.1e-6 bits, so the NMI error is
+    at most 4.4e-6 / H_AB (5e-6 / H_AB allowed), exact 0 where H_AB = 0."""
+    rng = np.random.default_rng(31)
+    A = rng.integers(0, 4, (3, 10, 12)).astype(np.int32)
+    A[:2, :5] = 2
+    B = rng.integers(0, 4, (4, 9, 11)).astype(np.int32)
+    MB = (rng.random(B.shape) > 0.1).astype(np.uint8)
+    ref = oracle.cmif3(A, None, B, MB, 4, 4)
+    plan = cm.VolumePlan(3, 10, 12, 4, 9, 11, 4, 4, cm.AUTO)
+    mi = np.full((plan.R, plan.C), np.nan)
+    n = np.full((plan.R, plan.C), -1, np.int32)
+    pk = cm.Peak()
+    plan.compute_host(A, None, B, MB, mi, n, 0.5, pk)
+    assert plan.status()[0] == "OK"
+    plan.close()
+    np.testing.assert_array_equal(n, ref["n"])
+    assert float(np.abs(mi - ref["mi"]).max()) <= MI_TOL
+    _, best, _ = oracle.gamma_argmax(ref["mi"], ref["n"], 0.5)
+    row = (pk.angle_idx + 3 - 1) * (10 + 9 - 1) + pk.dy + 10 - 1
+    col = pk.dx + 12 - 1
+    assert abs(pk.mi - best) <= MI_TOL and abs(ref["mi"][row, col] - best) <= MI_TOL
+    assert pk.n == ref["n"][row, col]
+
+    nplan = cm.VolumePlan(3, 10, 12, 4, 9, 11, 4, 4, cm.FP32, nmi=True)
+    m = torch.full((nplan.R, nplan.C), float("nan"), dtype=torch.float64, device="cuda:0")
+    nplan.compute(_dev(A), None, _dev(B), _dev(MB), m)
+    torch.cuda.synchronize()
+    assert nplan.status()[0] == "OK"
+    nplan.close()
+    got = m.cpu().numpy()
+    hab = ref["h_ab"]
+    zero = hab == 0
+    assert np.all(got[zero] == 0.0)
+    err = np.abs(got[~zero] - ref["nmi"][~zero])
+    assert np.all(err <= 5e-6 / hab[~zero])
