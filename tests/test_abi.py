@@ -52,3 +52,32 @@ def test_host_side_argument_errors(libcmif):
     assert libcmif.cmif_compute(None, None, None, None, None, None, None, None, 0.0, None, None) == 1
     assert libcmif.cmif_plan_destroy(None) == 0
     assert libcmif.cmif_status_string(2) == b"label outside [0, K) under mask"
+
+
+def test_host_side_argument_errors_of_the_extensions(libcmif):
+    """Volume, weighted, rotation and batch entry points reject bad arguments on
+    the host, before any CUDA call (status codes of include/cmif.h)."""
+    h = ctypes.c_void_p()
+    P = ctypes.byref(h)
+    INVALID, UNSUPPORTED = 1, 8
+    c3 = libcmif.cmif_plan_create_3d
+    assert c3(P, 0, 4, 4, 2, 4, 4, 2, 2, cm.FP32, 0) == INVALID                          # D_A < 1
+    assert c3(P, 2, 4, 4, 1025, 4, 4, 2, 2, cm.FP32, 0) == INVALID                       # D_B > 1024
+    assert c3(P, 65, 256, 256, 2, 4, 4, 2, 2, cm.FP32, 0) == INVALID                     # D*H*W > 2^22
+    assert c3(P, 2, 4, 4, 2, 4, 4, 2, 2, cm.FP32, cm.FLAG_WINDOW) == UNSUPPORTED         # no window in 3-D
+    assert c3(P, 2, 4, 4, 1, 4, 4, 2, 2, cm.FP64, cm.FLAG_WEIGHTED) == UNSUPPORTED       # no weights in 3-D
+    assert not h.value
+    ce = libcmif.cmif_plan_create_ex
+    assert ce(P, 4, 4, 4, 4, 2, 2, cm.FP32, cm.FLAG_WEIGHTED) == UNSUPPORTED                   # SWMI is FP64
+    assert ce(P, 4, 4, 4, 4, 2, 2, cm.FP64, cm.FLAG_WEIGHTED | cm.FLAG_NMI) == UNSUPPORTED     # MI only
+    assert ce(P, 4, 4, 4, 4, 2, 2, cm.FP64, cm.FLAG_WEIGHTED | cm.FLAG_DEBUG_COUNTS) == UNSUPPORTED
+    assert libcmif.cmif_compute_weighted(None, None, None, None, None, None, None, 0.0, None, None) == INVALID
+    assert libcmif.cmif_align_rotations(None, None, None, None, None, None, 1, 0.5, 1, None, None, None) == INVALID
+    pk, th = cm.Peak(), ctypes.c_double()
+    assert libcmif.cmif_align_two_stage(None, None, None, None, None, 8, None, 0, 0.5, ctypes.byref(pk),
+                                        ctypes.byref(th), None) == INVALID
+    assert libcmif.cmif_rotate_nn(None, None, 4, 4, 0.1, None, None, None) == INVALID
+    b = ctypes.c_void_p()
+    assert libcmif.cmif_batch_create(ctypes.byref(b), 0, None, cm.FP32, 0) == INVALID          # no pairs
+    assert libcmif.cmif_batch_create(None, 1, None, cm.FP32, 0) == INVALID
+    assert not b.value
