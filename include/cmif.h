@@ -166,7 +166,10 @@ cmif_status cmif_compute(cmif_plan plan, const int32_t* A, const uint8_t* M_A, c
 
 /* cmif_compute with HOST buffers: copies the images in, computes, copies
  * mi_map (and n_map, peak when non-NULL) out, and synchronises the stream.
- * Host pointers; the device staging buffers belong to the plan. */
+ * Host pointers (pinned memory makes the copies asynchronous DMA).  The device
+ * staging buffer belongs to the plan: it is allocated by the first host call
+ * (the one exception to "compute calls allocate nothing"; CMIF_ERR_OOM when
+ * that fails), reused by later ones and freed by cmif_plan_destroy. */
 cmif_status cmif_compute_host(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
                               const uint8_t* M_B, double* mi_map, int32_t* n_map, double gamma,
                               cmif_peak* peak_host, void* stream);
