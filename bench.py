@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CMIF shift·angle evaluations/sec at 1024², K=16 (1 GB300); % HBM roofline"
 UNIT = "shift·angle evals/s"
-CONFIG_ID = 3
+WORKLOAD = "single-1024x1024-K16"
 GAMMA = 0.5
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
@@ -166,7 +166,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import synth
-    cfg = synth.make_config(CONFIG_ID)
+    cfg = synth.make_workload(WORKLOAD)
     per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
     rates = []
     n_tot, s_tot, thr = 0, 0.0, 1
@@ -182,7 +182,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * shifts / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "single-1024x1024-K16 (config 3)", "shifts_per_map": shifts},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "shifts_per_map": shifts},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                          "sample": f"{n_tot} random shifts of the 1024^2 K=16 map over {args.steps} steps "
                                    f"(direct method, FP64 entropies)"},
@@ -284,7 +284,7 @@ def run_secondary(args):
         step = lambda: plan.compute(A, None, B, None, mi, n, None, 0.5, pk)
         units, name = plan.R * plan.C, "volume-64^3-K8 FP32"
     elif args.workload == "torchfft":
-        cfg = synth.make_config(3)
+        cfg = synth.make_workload("single-1024x1024-K16")
         H, W = cfg["A"].shape
         plan = TorchFFTPlain(torch, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 16, 16, dev)
         step = plan
@@ -295,7 +295,7 @@ def run_secondary(args):
         torch.cuda.synchronize()
         print(json.dumps({"torchfft_vs_library_max_abs_mi_diff": float((got - ref).abs().max())}), flush=True)
     elif args.workload == "swmi":
-        cfg = synth.make_config(2)
+        cfg = synth.make_workload("single-256x256-K16")
         H, W = cfg["A"].shape
         plan = cm.Plan(H, W, H, W, 16, 16, cm.FP64, graph=True, weighted=True)
         R, C = 2 * H - 1, 2 * W - 1
@@ -309,7 +309,7 @@ def run_secondary(args):
         step = lambda: plan.compute_weighted(A, wa, B, wb, mi, nw, 0.5, pk)
         units, name = R * C, cfg["name"] + " SWMI FP64"
     elif args.workload == "nmi":
-        cfg = synth.make_config(3)
+        cfg = synth.make_workload("single-1024x1024-K16")
         H, W = cfg["A"].shape
         plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True, nmi=True)
         R, C = 2 * H - 1, 2 * W - 1
@@ -320,11 +320,11 @@ def run_secondary(args):
         step = lambda: plan.compute(ins[0], ins[1], ins[2], ins[3], mi, n, None, 0.5, pk)
         units, name = R * C, cfg["name"] + " NMI FP32"
     elif args.workload in ("single256", "plain64"):
-        cid = 2 if args.workload == "single256" else 1
-        cfg = synth.make_config(cid)
+        small = args.workload == "single256"
+        cfg = synth.make_workload("single-256x256-K16" if small else "plain-64x64-K8")
         H, W = cfg["A"].shape
         K = cfg["K_A"]
-        prec = cm.FP32 if cid == 2 else cm.FP64
+        prec = cm.FP32 if small else cm.FP64
         plan = cm.Plan(H, W, H, W, K, K, prec, graph=True)
         R, C = 2 * H - 1, 2 * W - 1
         mi = torch.empty((R, C), dtype=torch.float64, device=dev)
@@ -334,7 +334,7 @@ def run_secondary(args):
         step = lambda: plan.compute(ins[0], ins[1], ins[2], ins[3], mi, n, None, 0.5, pk)
         units, name = R * C, cfg["name"] + (" FP32" if prec == cm.FP32 else " FP64")
     elif args.workload in ("rotation", "rotation-window"):
-        cfg = synth.make_config(4)
+        cfg = synth.make_workload("rotation-512x512-K16-64angles")
         H, W = cfg["A"].shape
         win = args.workload == "rotation-window"
         plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True, window=win)
@@ -348,7 +348,7 @@ def run_secondary(args):
         else:
             units, name = (2 * H - 1) * (2 * W - 1) * len(cfg["angles"]), cfg["name"] + " FP32"
     elif args.workload == "two-stage":
-        cfg = synth.make_config(4)
+        cfg = synth.make_workload("rotation-512x512-K16-64angles")
         H, W = cfg["A"].shape
         # no graph: the two stages have different angle lists (one cached graph would be re-captured each call)
         plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=False, window=True)
@@ -359,7 +359,7 @@ def run_secondary(args):
         units = (2 * min(py, H - 1) + 1) * (2 * min(px, W - 1) + 1) * (64 + len(u))
         name = cfg["name"] + " two-stage 64+16 padded-window FP32"
     else:
-        cfg = synth.make_config(5)
+        cfg = synth.make_workload("uneven-batch-128pairs")
         pairs = [dict(A=d(p["A"]), M_A=d(p["M_A"]), B=d(p["B"]), M_B=d(p["M_B"]), K_A=p["K_A"], K_B=p["K_B"],
                       angles=p["angles"], gamma=0.5) for p in cfg["pairs"]]
         plan = cm.Batch(pairs, cm.FP32, graph=True)
@@ -409,8 +409,8 @@ def main():
     ap.add_argument("--workload", default="single1024",
                     choices=["single1024", "rotation", "rotation-window", "two-stage", "batch", "single256",
                              "plain64", "nmi", "swmi", "torchfft", "volume"],
-                    help="single1024 (default, the headline): config 3; rotation: config 4 (512^2, 64 angles); "
-                         "batch: config 5 (128 uneven pairs x 4 angles); single256 / plain64: configs 2 / 1")
+                    help="single1024 (default, the headline): 1024^2, K=16; rotation: 512^2, K=16, 64 angles; "
+                         "batch: 128 uneven pairs x 4 angles; single256 / plain64: 256^2, K=16 / 64^2, K=8")
     ap.add_argument("--profile-shape", default=None,
                     help="HxW: run only the device step loop on a planted pair of this size (for ncu captures)")
     args = ap.parse_args()
@@ -441,7 +441,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    cfg = synth.make_config(CONFIG_ID)
+    cfg = synth.make_workload(WORKLOAD)
     A_np, B_np, MA_np, MB_np = cfg["A"], cfg["B"], cfg["M_A"], cfg["M_B"]
     HA, WA = A_np.shape
     HB, WB = B_np.shape
@@ -559,7 +559,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "single-1024x1024-K16 (config 3)", "H": HA, "W": WA, "K_A": KA, "K_B": KB,
+        "config": {"workload": WORKLOAD, "H": HA, "W": WA, "K_A": KA, "K_B": KB,
                    "shifts_per_map": shifts, "angles": 1, "precision": "FP32 transforms, fixed-point entropy",
                    "gamma": GAMMA, "l2": "flushed between steps (256 MB write), per-step CUDA events",
                    "parallelism": f"replicas x{world}"},

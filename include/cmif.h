@@ -83,7 +83,7 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
 #define CMIF_FLAG_DEBUG_COUNTS 1u /* allow a non-NULL counts output in cmif_compute */
 #define CMIF_FLAG_GRAPH 2u        /* capture each call's launches in a CUDA graph once and replay it while the
                                      call's arguments (pointers, gamma, angles) are unchanged */
-#define CMIF_FLAG_WINDOW 4u       /* Alg. 1's padded search window (Sec. 4, Alg. 1 line 2: A and M_A zero-padded
+#define CMIF_FLAG_WINDOW 4u       /* Alg. 1's padded search window (Sec. 4, Alg. 1's ZERO-PAD step: A and M_A zero-padded
                                      by p_i = ceil(|X_B|_i (1 - gamma)) along each axis).  X_S becomes the shifts
                                      that keep B's domain inside padded A's: chi_i in [|X_B|_i - |X_A|_i - p_i, p_i]
                                      (|chi_i| <= p_i for equal sizes), intersected with the full range.  Only the

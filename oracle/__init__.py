@@ -19,8 +19,8 @@ Functions and the passages they follow:
 * ``gamma_argmax``, ``align`` -- the per-transform gamma-gated argmax and the
                      strict-greater update over transforms of Alg. 1.  Pinned by
                      hand-built cases.
-* ``alg1_padded`` -- one transform of Alg. 1 with its ZERO-PAD step (Alg. 1
-                     line 2, Sec. 4): A and M_A padded by ceil(|X_B|_i (1 - gamma))
+* ``alg1_padded`` -- one transform of Alg. 1 with its ZERO-PAD step (Alg. 1,
+                     Sec. 4): A and M_A padded by ceil(|X_B|_i (1 - gamma))
                      zeros along each axis, the direct CMIF of the padded pair, X_S
                      = the shifts that keep B's domain inside padded A's, and the
                      gated argmax over X_S.  Pinned by tests/test_oracle.py
@@ -222,7 +222,7 @@ def align(per_angle, gamma, top_k=1):
 
 
 def alg1_padded(A, M_A, B, M_B, K_A, K_B, gamma):
-    """One transform of Alg. 1 with the ZERO-PAD step (Alg. 1 line 2).
+    """One transform of Alg. 1 with the ZERO-PAD step of Alg. 1.
 
     Pads A and M_A by p_i = ceil(|X_B|_i (1 - gamma)) zeros on both sides of
     each axis, computes the direct CMIF of (padded A, B), restricts it to X_S =

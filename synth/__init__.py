@@ -12,7 +12,7 @@ labels with k-means (Sec. 3.6), which yields exactly such label maps with
 k in {8, 16, 32} (Sec. 5.1).  Masks follow the paper's ROI masks
 (Sec. 3.1) and the circular masks of its evaluation (Sec. 5.2).
 
-Every generator takes a ``numpy.random.Generator``; a whole configuration is
+Every generator takes a ``numpy.random.Generator``; a whole workload is
 reproducible from one integer seed.
 """
 from __future__ import annotations
@@ -25,7 +25,7 @@ from scipy.spatial import cKDTree
 
 __all__ = [
     "LabelField", "make_field", "permutation", "label_noise", "disc_mask",
-    "hole_mask", "ones_mask", "planted_pair", "make_config", "CONFIG_NAMES",
+    "hole_mask", "ones_mask", "planted_pair", "make_workload", "WORKLOADS",
 ]
 
 
@@ -143,24 +143,28 @@ def planted_pair(rng, H, W, n_cells, K_A, K_B, shift, noise, angle_deg=0.0,
     return A.astype(np.int32), B.astype(np.int32)
 
 
-CONFIG_NAMES = {
-    1: "plain-64x64-K8",
-    2: "single-256x256-K16",
-    3: "single-1024x1024-K16",
-    4: "rotation-512x512-K16-64angles",
-    5: "uneven-batch-128pairs",
+# The five workloads, by name, with the offset added to the seed for each (so
+# that every workload draws its own stream).
+WORKLOADS = {
+    "plain-64x64-K8": 1000,
+    "single-256x256-K16": 2000,
+    "single-1024x1024-K16": 3000,
+    "rotation-512x512-K16-64angles": 4000,
+    "uneven-batch-128pairs": 5000,
 }
 
 
-def make_config(i: int, seed: int = 2106_14699, scale: float = 1.0) -> dict:
-    """Inputs for the five workloads.  ``scale`` < 1 shrinks sides (test-sized variants).
+def make_workload(name: str, seed: int = 2106_14699, scale: float = 1.0) -> dict:
+    """Inputs for one of the WORKLOADS.  ``scale`` < 1 shrinks sides (test-sized variants).
 
     Returns a dict with A, M_A, B, M_B (numpy), K_A, K_B and the planted truth.
-    Config 5 returns {"pairs": [...]} with one dict per pair.
+    "uneven-batch-128pairs" returns {"pairs": [...]} with one dict per pair.
     """
-    rng = np.random.default_rng(seed + 1000 * i)
+    if name not in WORKLOADS:
+        raise ValueError(f"unknown workload {name!r}")
+    rng = np.random.default_rng(seed + WORKLOADS[name])
     s = lambda n: max(8, int(round(n * scale)))
-    if i == 1:
+    if name == "plain-64x64-K8":
         H = W = s(64)
         lim = max(1, int(round(12 * min(1.0, scale))))
         d = tuple(int(v) for v in rng.integers(-lim, lim + 1, 2))
@@ -170,20 +174,21 @@ def make_config(i: int, seed: int = 2106_14699, scale: float = 1.0) -> dict:
         perm = permutation(rng, K)
         B = label_noise(rng, np.roll(perm[A], d, axis=(0, 1)).astype(np.int32), 0.05, K)
         return dict(A=A, M_A=ones_mask(H, W), B=B, M_B=disc_mask(H, W, 28 * H / 64.0),
-                    K_A=K, K_B=K, shift=d, name=CONFIG_NAMES[1])
-    if i in (2, 3):
-        H = W = s(256 if i == 2 else 1024)
+                    K_A=K, K_B=K, shift=d, name=name)
+    if name in ("single-256x256-K16", "single-1024x1024-K16"):
+        small = name == "single-256x256-K16"
+        H = W = s(256 if small else 1024)
         K = 16
-        n_cells = 300 if i == 2 else 2000
+        n_cells = 300 if small else 2000
         lim = max(1, int(round(40 * min(1.0, scale))))
         d = tuple(int(v) for v in rng.integers(-lim, lim + 1, 2))
-        A, B = planted_pair(rng, H, W, n_cells, K, K, d, 0.10, jitter=(i == 3), same_labels=True)
-        if i == 2:
+        A, B = planted_pair(rng, H, W, n_cells, K, K, d, 0.10, jitter=not small, same_labels=True)
+        if small:
             MA, MB = hole_mask(rng, H, W), hole_mask(rng, H, W)
         else:
             MA, MB = ones_mask(H, W), ones_mask(H, W)
-        return dict(A=A, M_A=MA, B=B, M_B=MB, K_A=K, K_B=K, shift=d, name=CONFIG_NAMES[i])
-    if i == 4:
+        return dict(A=A, M_A=MA, B=B, M_B=MB, K_A=K, K_B=K, shift=d, name=name)
+    if name == "rotation-512x512-K16-64angles":
         H = W = s(512)
         K = 16
         shift = (int(round(-23 * scale)), int(round(61 * scale)))
@@ -192,23 +197,22 @@ def make_config(i: int, seed: int = 2106_14699, scale: float = 1.0) -> dict:
         n_angles = 64
         angles = np.arange(n_angles) * (2 * math.pi / n_angles)
         return dict(A=A, M_A=ones_mask(H, W), B=B, M_B=ones_mask(H, W), K_A=K, K_B=K,
-                    shift=shift, angle_deg=37.5, angles=angles, name=CONFIG_NAMES[4])
-    if i == 5:
-        pairs = []
-        n_pairs = 128 if scale >= 1.0 else max(2, int(round(128 * scale)))
-        lo, hi = math.log(s(96)), math.log(s(1536))
-        for p in range(n_pairs):
-            H = int(round(math.exp(rng.uniform(lo, hi))))
-            W = int(round(math.exp(rng.uniform(lo, hi))))
-            K_A = int(rng.choice([8, 16, 24]))
-            K_B = int(rng.choice([8, 16, 24]))
-            th = float(rng.uniform(0, 360))
-            lim = max(1, min(H, W) // 8)
-            d = tuple(int(v) for v in rng.integers(-lim, lim + 1, 2))
-            n_cells = max(20, int(H * W / 500))
-            A, B = planted_pair(rng, H, W, n_cells, K_A, K_B, d, 0.10, angle_deg=th)
-            angles = np.concatenate([[math.radians(th)], rng.uniform(0, 2 * math.pi, 3)])
-            pairs.append(dict(A=A, M_A=hole_mask(rng, H, W), B=B, M_B=hole_mask(rng, H, W),
-                              K_A=K_A, K_B=K_B, shift=d, angle_deg=th, angles=angles))
-        return dict(pairs=pairs, name=CONFIG_NAMES[5])
-    raise ValueError(f"unknown config {i}")
+                    shift=shift, angle_deg=37.5, angles=angles, name=name)
+    # uneven-batch-128pairs
+    pairs = []
+    n_pairs = 128 if scale >= 1.0 else max(2, int(round(128 * scale)))
+    lo, hi = math.log(s(96)), math.log(s(1536))
+    for p in range(n_pairs):
+        H = int(round(math.exp(rng.uniform(lo, hi))))
+        W = int(round(math.exp(rng.uniform(lo, hi))))
+        K_A = int(rng.choice([8, 16, 24]))
+        K_B = int(rng.choice([8, 16, 24]))
+        th = float(rng.uniform(0, 360))
+        lim = max(1, min(H, W) // 8)
+        d = tuple(int(v) for v in rng.integers(-lim, lim + 1, 2))
+        n_cells = max(20, int(H * W / 500))
+        A, B = planted_pair(rng, H, W, n_cells, K_A, K_B, d, 0.10, angle_deg=th)
+        angles = np.concatenate([[math.radians(th)], rng.uniform(0, 2 * math.pi, 3)])
+        pairs.append(dict(A=A, M_A=hole_mask(rng, H, W), B=B, M_B=hole_mask(rng, H, W),
+                          K_A=K_A, K_B=K_B, shift=d, angle_deg=th, angles=angles))
+    return dict(pairs=pairs, name=name)

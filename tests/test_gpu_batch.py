@@ -30,7 +30,7 @@ def _dev(x):
 
 
 def test_graph_replay_matches_direct(cm):
-    cfg = synth.make_config(2, scale=0.5)
+    cfg = synth.make_workload("single-256x256-K16", scale=0.5)
     A, B, MA, MB = (_dev(cfg[k]) for k in ("A", "B", "M_A", "M_B"))
     H, W = cfg["A"].shape
     R, C = 2 * H - 1, 2 * W - 1
@@ -56,7 +56,7 @@ def test_graph_replay_matches_direct(cm):
 
 
 def test_graph_align_rotations(cm):
-    cfg = synth.make_config(4, scale=64 / 512)
+    cfg = synth.make_workload("rotation-512x512-K16-64angles", scale=64 / 512)
     A, B = _dev(cfg["A"]), _dev(cfg["B"])
     H, W = cfg["A"].shape
     angles = cfg["angles"][::8]
@@ -92,7 +92,7 @@ def _pair_oracle(cm, p):
 
 @pytest.mark.parametrize("graph", [False, True])
 def test_batch_vs_oracle(cm, graph):
-    cfg = synth.make_config(5, scale=0.1)
+    cfg = synth.make_workload("uneven-batch-128pairs", scale=0.1)
     pairs = cfg["pairs"]
     dev_pairs = [dict(A=_dev(p["A"]), M_A=_dev(p["M_A"]), B=_dev(p["B"]), M_B=_dev(p["M_B"]), K_A=p["K_A"],
                       K_B=p["K_B"], angles=p["angles"], gamma=0.5) for p in pairs]
@@ -131,7 +131,7 @@ def test_batch_vs_oracle(cm, graph):
 def test_batch_with_window_or_nmi(cm, flag):
     """Batch plans inherit CMIF_FLAG_WINDOW / CMIF_FLAG_NMI: each pair's result
     equals a single-pair plan with the same flag."""
-    cfg = synth.make_config(5, scale=0.08)
+    cfg = synth.make_workload("uneven-batch-128pairs", scale=0.08)
     pairs = cfg["pairs"][:4]
     dev_pairs = [dict(A=_dev(p["A"]), M_A=_dev(p["M_A"]), B=_dev(p["B"]), M_B=_dev(p["M_B"]), K_A=p["K_A"],
                       K_B=p["K_B"], angles=p["angles"][:2], gamma=0.5) for p in pairs]

@@ -71,8 +71,8 @@ def test_nmi_map_vs_oracle(cm, shape, K, prec):
     plan.close()
 
 
-def test_nmi_config2_full_map(cm):
-    cfg = synth.make_config(2)
+def test_nmi_single256_full_map(cm):
+    cfg = synth.make_workload("single-256x256-K16")
     A, B, MA, MB = cfg["A"], cfg["B"], cfg["M_A"], cfg["M_B"]
     H, W = A.shape
     plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, nmi=True)

@@ -140,15 +140,15 @@ def test_label_range_reported(cm):
 
 
 @pytest.mark.parametrize("prec_name", ["FP64", "SPLIT32", "FP32"])
-def test_config1_full(cm, prec_name):
-    cfg = synth.make_config(1)
+def test_plain64_full(cm, prec_name):
+    cfg = synth.make_workload("plain-64x64-K8")
     g, ref = check_exact(cm, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 8, 8, getattr(cm, prec_name), gamma=0.5)
     _, dy, dx, _, _ = g["peak"]
     assert (dy, dx) == tuple(cfg["shift"])
 
 
-def test_config2_full(cm):
-    cfg = synth.make_config(2)
+def test_single256_full(cm):
+    cfg = synth.make_workload("single-256x256-K16")
     g, ref = check_exact(cm, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 16, 16, cm.FP32, gamma=0.5)
     _, dy, dx, _, _ = g["peak"]
     assert (dy, dx) == tuple(cfg["shift"])
@@ -164,11 +164,11 @@ def _sample_shifts(rng, HA, WA, HB, WB, n, extra=()):
     return np.array(dys, np.int32), np.array(dxs, np.int32)
 
 
-def test_config3_full_size_sampled(cm):
+def test_single1024_full_size_sampled(cm):
     """1024^2, K=16, FP32 path at the benchmark size: N exact on the whole map
     (closed form for all-ones masks), MI on sampled shifts vs the oracle,
     residual under the guard, planted shift found."""
-    cfg = synth.make_config(3)
+    cfg = synth.make_workload("single-1024x1024-K16")
     A, B = cfg["A"], cfg["B"]
     g = run_gpu(cm, A, cfg["M_A"], B, cfg["M_B"], 16, 16, cm.FP32, counts=False, gamma=0.5)
     assert g["status"][0] == "OK" and g["status"][1] < 0.25, g["status"]
@@ -181,7 +181,7 @@ def test_config3_full_size_sampled(cm):
     got = g["mi"][dys + H - 1, dxs + H - 1]
     np.testing.assert_array_equal(g["n"][dys + H - 1, dxs + H - 1], ref["n"])
     err = float(np.abs(got - ref["mi"]).max())
-    print(f"[mi-error] config3 sampled max|dMI|={err:.3e} residual={g['status'][1]:.3e}")
+    print(f"[mi-error] 1024^2 K=16 sampled max|dMI|={err:.3e} residual={g['status'][1]:.3e}")
     assert err <= MI_TOL, err
     _, dy, dx, _, _ = g["peak"]
     assert (dy, dx) == tuple(cfg["shift"])
@@ -212,7 +212,7 @@ def test_auto_escalates_unbalanced_labels(cm, tier2, monkeypatch):
 
 
 def test_host_buffer_entry_point(cm):
-    cfg = synth.make_config(1)
+    cfg = synth.make_workload("plain-64x64-K8")
     A, B = cfg["A"], cfg["B"]
     plan = cm.Plan(64, 64, 64, 64, 8, 8, cm.FP32)
     mi = np.empty((127, 127), np.float64)

@@ -26,8 +26,8 @@ def cm():
     return cm
 
 
-def test_config3_three_precisions(cm, capsys):
-    cfg = synth.make_config(3)
+def test_single1024_three_precisions(cm, capsys):
+    cfg = synth.make_workload("single-1024x1024-K16")
     A, B = cfg["A"], cfg["B"]
     H = 1024
     K = 16
@@ -72,7 +72,7 @@ def test_config3_three_precisions(cm, capsys):
             del counts
         plan.close()
     with capsys.disabled():
-        print("\n[precision] config 3, 1024^2, K=16: name, ms/map (debug counts off), max residual, "
+        print("\n[precision] 1024^2, K=16: name, ms/map (debug counts off), max residual, "
               "count mismatches vs oracle at 48 shifts x 256 pairs, count mismatches vs FP64 over the whole map, "
               "max |dMI| at the sampled shifts, status")
         for r in report:

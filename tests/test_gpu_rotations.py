@@ -58,7 +58,7 @@ def test_rotate_nn_matches_oracle(cm, theta):
 
 
 def test_align_rotations_vs_oracle(cm):
-    cfg = synth.make_config(4, scale=96 / 512)
+    cfg = synth.make_workload("rotation-512x512-K16-64angles", scale=96 / 512)
     A, B = cfg["A"], cfg["B"]
     H, W = A.shape
     K = 16
@@ -94,11 +94,11 @@ def test_align_rotations_vs_oracle(cm):
     plan.close()
 
 
-def test_config4_planted_rotation_and_shift(cm):
+def test_rotation512_planted_angle_and_shift(cm):
     """512^2, K = 16, 64 angles over 360 degrees; B is A rotated by 37.5 deg and
     shifted by (-23, 61).  37.5 deg is off the 5.625 deg grid: the best angle
     must be a grid neighbour and the shift within 3 px of the planted one."""
-    cfg = synth.make_config(4)
+    cfg = synth.make_workload("rotation-512x512-K16-64angles")
     A, B = cfg["A"], cfg["B"]
     H, W = A.shape
     plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32)
@@ -119,7 +119,7 @@ def test_sharded_entry_single_rank_equals_direct(cm):
     """shard.align_rotations_sharded without a process group = one rank holding
     every angle: its merged top-k equals cmif_align_rotations' device top-k."""
     from paper_2106_14699_gb300 import shard
-    cfg = synth.make_config(4, scale=64 / 512)
+    cfg = synth.make_workload("rotation-512x512-K16-64angles", scale=64 / 512)
     A, B = _dev(cfg["A"]), _dev(cfg["B"])
     H, W = cfg["A"].shape
     angles = list(cfg["angles"][::4])

@@ -1,7 +1,7 @@
 """GPU parity of Alg. 1's padded search window (CMIF_FLAG_WINDOW) and of the
 two-stage rigid search (cmif_align_two_stage) against the oracle.
 
-The oracle pads A literally (Alg. 1 line 2) and runs the direct method on the
+The oracle pads A literally (Alg. 1's ZERO-PAD step) and runs the direct method on the
 padded pair; the library computes only the window rows of the unpadded map.
 Count parity for rotations uses the device-warped B (see test_gpu_rotations).
 """
@@ -97,7 +97,7 @@ def _dev_warp(cm):
 
 
 def test_align_rotations_window_vs_oracle(cm):
-    cfg = synth.make_config(4, scale=80 / 512)
+    cfg = synth.make_workload("rotation-512x512-K16-64angles", scale=80 / 512)
     A, B = cfg["A"], cfg["B"]
     H, W = A.shape
     angles = cfg["angles"][::8]
@@ -120,7 +120,7 @@ def test_align_rotations_window_vs_oracle(cm):
 
 
 def test_two_stage_vs_oracle(cm):
-    cfg = synth.make_config(4, scale=64 / 512)
+    cfg = synth.make_workload("rotation-512x512-K16-64angles", scale=64 / 512)
     A, B = cfg["A"], cfg["B"]
     H, W = A.shape
     u = [0.11, 0.5, 0.73, 0.94, 0.28, 0.6]
@@ -135,11 +135,11 @@ def test_two_stage_vs_oracle(cm):
         plan.close()
 
 
-def test_config4_two_stage_refines_planted_angle(cm):
+def test_rotation512_two_stage_refines_planted_angle(cm):
     """512^2, B = A rotated by 37.5 deg (off the 5.625 deg grid) and shifted by
     (-23, 61): the refinement draws (evenly spaced here) bring the angle within
     2 deg of 37.5 deg and never lower I."""
-    cfg = synth.make_config(4)
+    cfg = synth.make_workload("rotation-512x512-K16-64angles")
     A, B = cfg["A"], cfg["B"]
     H, W = A.shape
     plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, window=True)

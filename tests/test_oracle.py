@@ -207,12 +207,12 @@ def test_label_range_rejected():
 
 
 def test_planted_shift_recovered():
-    cfg = synth.make_config(1)
+    cfg = synth.make_workload("plain-64x64-K8")
     out = oracle.cmif(cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], cfg["K_A"], cfg["K_B"])
     idx, mi, n = oracle.gamma_argmax(out["mi"], out["n"], 0.5)
     r, c = divmod(idx, out["mi"].shape[1])
     assert (r - 63, c - 63) == tuple(cfg["shift"])
-    cfg = synth.make_config(2, scale=0.25)
+    cfg = synth.make_workload("single-256x256-K16", scale=0.25)
     out = oracle.cmif(cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], cfg["K_A"], cfg["K_B"])
     idx, mi, n = oracle.gamma_argmax(out["mi"], out["n"], 0.5)
     H = cfg["A"].shape[0]

@@ -1,5 +1,6 @@
-"""Pins of the oracle's extensions: Alg. 1's ZERO-PAD search window (Alg. 1
-line 2, Sec. 4), the two-stage rigid search (Sec. 4) and NMI (Sec. 2).
+"""Pins of the oracle's extensions: Alg. 1's ZERO-PAD search window (Alg. 1,
+Sec. 4), the two-stage rigid search (Sec. 4), NMI (Sec. 2), SWMI (Sec. 3) and
+label volumes.
 
 Each pin ties the oracle to something other than itself: the unpadded direct
 CMIF at the same displacement (padding with mask 0 adds no pixel pairs), the

@@ -34,7 +34,7 @@ def _dev(x):
 
 
 def _cases():
-    cfg = synth.make_config(1)
+    cfg = synth.make_workload("plain-64x64-K8")
     yield cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 8, 8
     rng = np.random.default_rng(77)
     A = synth.make_field(rng, 45, 70, 30, 12).image(45, 70)
