@@ -110,25 +110,48 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+        with open(self.path) as f:
+            out = parse_clock_csv(f)
         os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return out
+
+
+def parse_clock_csv(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen, from the
+    lines nvidia-smi writes for ClockSampler.Q (csv, no header, no units); None
+    when no line holds a sample."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+REJECT_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clocks_rejected(clocks, floor=0.85):
+    """True when a timed region must be taken again: it saw a hardware or thermal
+    slowdown, or its median SM clock sat below floor x the maximum with no reason
+    active (a clock lock left by someone else).  sw_power_cap alone is kept."""
+    if not clocks:
+        return False
+    if any(r in REJECT_REASONS for r in clocks["reasons"]):
+        return True
+    return not clocks["reasons"] and clocks["sm_mhz"] < floor * clocks["sm_max_mhz"]
 
 
 def cpu_oracle_rate(cfg, budget_s, rng_seed=7):
@@ -471,35 +494,48 @@ def main():
     if st[0] != "OK":
         raise SystemExit(f"device status after warm-up: {st}")
 
-    plan.set_profiling(True)
-    clk = ClockSampler(local)
-    clk.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage = {}
-    launches = 0
-    for i in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps (outside the step's events)
-        ev0[i].record(stream)
-        step()
-        ev1[i].record(stream)
-        for name, ms in plan.stage_times():  # synchronises; between steps
-            stage.setdefault(name, []).append(ms)
-            launches += 2 if name in ("peak", "finalize") else 1  # peak: partial + final; finalize: + merge
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = clk.stop()
-    plan.set_profiling(False)
-    ms_steps = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    ms_per_step = sum(ms_steps) / len(ms_steps)
-    if dist:
-        t = torch.tensor([ms_per_step], device=dev, dtype=torch.float64)
+    def timed_region():
+        plan.set_profiling(True)
+        clk = ClockSampler(local)
+        clk.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        stage = {}
+        launches = 0
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the step's events)
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+            for name, ms in plan.stage_times():  # synchronises; between steps
+                stage.setdefault(name, []).append(ms)
+                launches += 2 if name in ("peak", "finalize") else 1  # peak: partial + final; finalize: + merge
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = clk.stop()
+        plan.set_profiling(False)
+        ms_steps = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        ms_per_step = sum(ms_steps) / len(ms_steps)
+        if dist:
+            t = torch.tensor([ms_per_step], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_per_step = float(t.item())
+        return ms_per_step, stage, launches, clocks
+
+    ms_per_step, stage, launches, clocks = timed_region()
+    retake = clocks_rejected(clocks)
+    if dist:  # every rank takes the same decision (the retake has barriers)
+        t = torch.tensor([1.0 if retake else 0.0], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+        retake = bool(t.item() > 0)
+    if retake:
+        first = clocks
+        ms_per_step, stage, launches, clocks = timed_region()
+        clocks = dict(clocks or {}, rejected_first_run=first)
     st = plan.status()
 
     # end to end through the host-buffer entry point (pinned host memory)
