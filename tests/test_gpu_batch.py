@@ -112,11 +112,8 @@ def test_batch_vs_oracle(cm, graph):
     for i, p in enumerate(pairs):
         best, per = _pair_oracle(cm, p)
         H, W = p["A"].shape
-        C = W + p["B"].shape[1] - 1
         ga, gdy, gdx, gn, gmi = got[i]
         assert abs(gmi - best[2]) <= MI_TOL, (i, got[i], best)
-        if ga != best[0] or (gdy, gdx) != divmod(best[1], C) and False:
-            pass
         mi_at = per[ga][0][gdy + H - 1, gdx + W - 1]
         assert abs(mi_at - best[2]) <= MI_TOL
     # the translation-only pair equals a direct cmif_compute
@@ -173,3 +170,22 @@ def test_weighted_graph_replay(cm):
         assert plan.status()[0] == "OK"
         plan.close()
     assert torch.equal(outs[0], outs[1])
+
+
+def test_sharded_batch_single_rank_equals_direct(cm):
+    """compute_batch_sharded without a process group (one rank) runs every pair
+    and returns, in pair order, the records and statuses of one Batch run."""
+    from paper_2106_14699_gb300 import shard
+    cfg = synth.make_workload("uneven-batch-128pairs", scale=0.08)
+    pairs = cfg["pairs"][:6]
+    dev_pairs = [dict(A=_dev(p["A"]), M_A=_dev(p["M_A"]), B=_dev(p["B"]), M_B=_dev(p["M_B"]), K_A=p["K_A"],
+                      K_B=p["K_B"], angles=p["angles"], gamma=0.5) for p in pairs]
+    recs, stats = shard.compute_batch_sharded(dev_pairs, cm.FP32, graph=False)
+    batch = cm.Batch(dev_pairs, cm.FP32, graph=False)
+    res = torch.empty(24 * len(dev_pairs), dtype=torch.uint8, device="cuda:0")
+    stat = torch.full((len(dev_pairs),), -1, dtype=torch.int32, device="cuda:0")
+    batch.run(res, stat)
+    torch.cuda.synchronize()
+    batch.close()
+    assert recs == cm.peaks_from_bytes(res, len(dev_pairs))
+    assert stats == stat.cpu().tolist() == [0] * len(dev_pairs)

@@ -106,3 +106,90 @@ def test_gloo_world2_merge_equals_single_process(tmp_path):
         assert gmi == rmi
     # B is A turned by angles[3]; turning B by angles[4] = 2 pi - angles[3] undoes it
     assert shard.alg1_choice(got[0])[0] == best[0] == 4
+
+
+# ---- batch pairs as units --------------------------------------------------
+
+def test_shard_pairs_partition_and_balance():
+    rng = np.random.default_rng(4)
+    works = [int(w) for w in rng.integers(1, 1000, 37)] + [5000, 5000]
+    for world in (1, 2, 3, 8, 50):
+        shares = [shard.shard_pairs(works, world, r) for r in range(world)]
+        flat = sorted(i for s in shares for i in s)
+        assert flat == list(range(len(works)))                 # every pair exactly once
+        loads = [sum(works[i] for i in s) for s in shares]
+        assert max(loads) <= sum(works) / world + max(works)   # longest-first bound
+        assert all(s == sorted(s) for s in shares)
+    assert shard.shard_pairs([], 2, 1) == []
+    with pytest.raises(ValueError):
+        shard.shard_pairs(works, 2, 2)
+    # the model: a pair's work grows with K_A K_B, its angles and its transform grid
+    w = shard.pair_work(100, 100, 100, 100, 8, 8, 4)
+    assert shard.pair_work(100, 100, 100, 100, 16, 16, 4) > 3 * w
+    assert shard.pair_work(100, 100, 100, 100, 8, 8, 8) > 1.9 * w
+    assert shard.pair_work(200, 100, 200, 100, 8, 8, 4) == 2 * w
+
+
+def _batch_pairs():
+    rng = np.random.default_rng(17)
+    out = []
+    for H, W, K, n_ang in [(12, 14, 3, 2), (9, 10, 2, 1), (16, 11, 4, 3), (8, 8, 3, 0), (13, 9, 2, 2)]:
+        A = rng.integers(0, K, (H, W)).astype(np.int32)
+        A[: H // 2, : W // 2] = 0
+        B = np.roll(A, (1, -2), axis=(0, 1))
+        angles = [2 * math.pi * t / 5 for t in range(n_ang)]
+        out.append(dict(A=A, B=B, K=K, angles=angles))
+    return out
+
+
+def _pair_record(p, gamma=0.5):
+    """Alg. 1's choice for one pair by the oracle (angle index 0 without angles)."""
+    per = []
+    for th in (p["angles"] or [None]):
+        wB, wM = (p["B"], None) if th is None else oracle.warp_nn(p["B"], None, th)
+        ref = oracle.cmif(p["A"], None, wB, wM, p["K"], p["K"])
+        per.append((ref["mi"], ref["n"]))
+    (a, idx, mi, n), _ = oracle.align(per, gamma)
+    if a < 0:
+        return shard.EMPTY
+    dy, dx = divmod(idx, 2 * p["A"].shape[1] - 1)
+    return (a, dy - (p["A"].shape[0] - 1), dx - (p["A"].shape[1] - 1), n, mi)
+
+
+def _works(pairs):
+    return [shard.pair_work(*p["A"].shape, *p["B"].shape, p["K"], p["K"], len(p["angles"])) for p in pairs]
+
+
+def _pairs_rank_main(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        pairs = _batch_pairs()
+        ran = []
+
+        def run_local(idx):
+            ran.extend(idx)
+            return [(_pair_record(pairs[i]), 0) for i in idx]
+        recs, stats = shard.run_pairs_sharded(_works(pairs), run_local)
+        np.save(f"{out_path}.{rank}.npy", np.array([recs, stats, ran], dtype=object), allow_pickle=True)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_world2_pairs_equal_single_process(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    out = str(tmp_path / "pairs")
+    mp.start_processes(_pairs_rank_main, args=(world, _free_port(), out), nprocs=world, join=True,
+                       start_method="spawn")
+    got = [np.load(f"{out}.{r}.npy", allow_pickle=True) for r in range(world)]
+    recs0, stats0, ran0 = got[0]
+    recs1, stats1, ran1 = got[1]
+    assert list(recs0) == list(recs1) and list(stats0) == list(stats1)   # every rank holds all results
+    assert sorted(list(ran0) + list(ran1)) == list(range(5))              # each pair computed once
+    assert ran0 and ran1                                                  # both ranks worked
+    pairs = _batch_pairs()
+    assert [tuple(r) for r in recs0] == [_pair_record(p) for p in pairs]
+    assert list(stats0) == [0] * 5
