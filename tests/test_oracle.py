@@ -228,6 +228,14 @@ def test_gamma_argmax_and_align_rules():
     # gamma 0.5: N >= 5 excludes index 1 (N=2) and index 5 (N=4); tie 0.9 at 1 is excluded,
     # the lowest index among the remaining maxima (0.9 at index 3) wins
     assert oracle.gamma_argmax(mi, n, 0.5)[0] == 3
+    # gamma 1: N >= max N (Alg. 1's gate is inclusive) keeps only the maximal overlaps;
+    # for full masks of equal size that is chi = 0 alone, whatever the MI elsewhere
+    rng = np.random.default_rng(6)
+    A = rng.integers(0, 3, (7, 9)).astype(np.int32)
+    B = rng.integers(0, 3, (7, 9)).astype(np.int32)
+    ref = oracle.cmif(A, None, B, None, 3, 3)
+    idx, _, n0 = oracle.gamma_argmax(ref["mi"], ref["n"], 1.0)
+    assert divmod(idx, 17) == (6, 8) and n0 == 63
     maps = [(mi, n), (mi * 0 + 0.9, n), (mi + 0.5, n)]
     best, top = oracle.align(maps, 0.5, top_k=3)
     assert best[0] == 2 and abs(best[2] - 1.4) < 1e-15

@@ -99,6 +99,17 @@ def test_two_stage_rules():
     # u = 1/2 re-evaluates the grid winner itself: equal I_T, strict > keeps stage (i)
     best2, theta2 = oracle.align_two_stage(A, None, B, MB, 3, 3, n_grid, [0.5], 0.5)
     assert best2 == best and theta2 == theta
+    # the refinement interval reaches exactly the grid neighbours of theta*: the
+    # draws u = 0 and u = 1 evaluate the grid angles next to the stage (i) choice
+    seen = []
+
+    def recording_warp(Bi, Mi, th):
+        seen.append(th)
+        return oracle.warp_nn(Bi, Mi, th)
+    oracle.align_two_stage(A, None, B, MB, 3, 3, n_grid, [0.0, 1.0], 0.5, warp=recording_warp)
+    step = 2 * math.pi / n_grid
+    assert len(seen) == n_grid + 2 and np.allclose(seen[:n_grid], [step * t for t in range(n_grid)], atol=1e-12)
+    assert abs(seen[n_grid] - (theta - step)) < 1e-12 and abs(seen[n_grid + 1] - (theta + step)) < 1e-12
     # refinement never lowers I, and a refined winner lies within one grid step
     u = [0.05, 0.3, 0.62, 0.9, 0.77]
     best3, theta3 = oracle.align_two_stage(A, None, B, MB, 3, 3, n_grid, u, 0.5)
