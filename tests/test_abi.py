@@ -81,3 +81,49 @@ def test_host_side_argument_errors_of_the_extensions(libcmif):
     assert libcmif.cmif_batch_create(ctypes.byref(b), 0, None, cm.FP32, 0) == INVALID          # no pairs
     assert libcmif.cmif_batch_create(None, 1, None, cm.FP32, 0) == INVALID
     assert not b.value
+
+
+_LAYOUT_PROBE = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "cmif.h"
+#define OFF(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+    printf("sizeof.cmif_peak %zu\nsizeof.cmif_pair_desc %zu\n", sizeof(cmif_peak), sizeof(cmif_pair_desc));
+    OFF(cmif_peak, angle_idx); OFF(cmif_peak, dy); OFF(cmif_peak, dx); OFF(cmif_peak, n); OFF(cmif_peak, mi);
+    OFF(cmif_pair_desc, A); OFF(cmif_pair_desc, M_A); OFF(cmif_pair_desc, B); OFF(cmif_pair_desc, M_B);
+    OFF(cmif_pair_desc, H_A); OFF(cmif_pair_desc, W_A); OFF(cmif_pair_desc, H_B); OFF(cmif_pair_desc, W_B);
+    OFF(cmif_pair_desc, K_A); OFF(cmif_pair_desc, K_B); OFF(cmif_pair_desc, angles_rad);
+    OFF(cmif_pair_desc, n_angles); OFF(cmif_pair_desc, gamma);
+    printf("prec %d %d %d %d\n", CMIF_FP32, CMIF_SPLIT32, CMIF_FP64, CMIF_AUTO);
+    printf("flags %u %u %u %u %u\n", CMIF_FLAG_DEBUG_COUNTS, CMIF_FLAG_GRAPH, CMIF_FLAG_WINDOW, CMIF_FLAG_NMI,
+           CMIF_FLAG_WEIGHTED);
+    printf("status %d %d %d %d %d %d %d %d %d\n", CMIF_OK, CMIF_ERR_INVALID_ARG, CMIF_ERR_LABEL_RANGE, CMIF_ERR_OOM,
+           CMIF_ERR_CUDA, CMIF_ERR_PRECISION, CMIF_ERR_TIMEOUT, CMIF_ERR_NOT_IMPLEMENTED, CMIF_ERR_UNSUPPORTED);
+    return 0;
+}
+"""
+
+
+def test_binding_mirrors_the_header(tmp_path, libcmif):
+    """The ctypes structs, precision and flag constants and status names of the
+    binding match what a C compiler makes of include/cmif.h, and every status
+    has its string."""
+    import subprocess
+    src, exe = tmp_path / "probe.c", tmp_path / "probe"
+    src.write_text(_LAYOUT_PROBE)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    out = dict(line.split(" ", 1) for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    assert int(out["sizeof.cmif_peak"]) == ctypes.sizeof(cm.Peak)
+    assert int(out["sizeof.cmif_pair_desc"]) == ctypes.sizeof(cm.PairDesc)
+    for T, S in (("cmif_peak", cm.Peak), ("cmif_pair_desc", cm.PairDesc)):
+        for name, _ in S._fields_:
+            assert int(out[f"{T}.{name}"]) == getattr(S, name).offset, (T, name)
+    assert [int(v) for v in out["prec"].split()] == [cm.FP32, cm.SPLIT32, cm.FP64, cm.AUTO]
+    assert [int(v) for v in out["flags"].split()] == [cm.FLAG_DEBUG_COUNTS, cm.FLAG_GRAPH, cm.FLAG_WINDOW,
+                                                      cm.FLAG_NMI, cm.FLAG_WEIGHTED]
+    codes = [int(v) for v in out["status"].split()]
+    assert codes == sorted(cm.STATUS_NAMES)
+    for c in codes:
+        s = libcmif.cmif_status_string(c)
+        assert s and s != libcmif.cmif_status_string(99)
