@@ -127,3 +127,12 @@ def test_binding_mirrors_the_header(tmp_path, libcmif):
     for c in codes:
         s = libcmif.cmif_status_string(c)
         assert s and s != libcmif.cmif_status_string(99)
+
+
+def test_peaks_from_bytes_decodes_the_record_layout():
+    import struct
+    recs = [(3, -7, 12, 4096, 1.25), (-1, 0, 0, 0, 0.0), (0, 1023, -1023, 1, 2.0 ** -22)]
+    raw = b"".join(struct.pack("<iiiid", *r) for r in recs)
+    assert len(raw) == 24 * len(recs)
+    assert cm.peaks_from_bytes(raw, len(recs)) == recs
+    assert cm.peaks_from_bytes(raw, 1) == recs[:1]
