@@ -37,7 +37,7 @@ GAMMA = 0.5
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # DRAM bytes per launch of the pair kernels, from ncu captures of the same
-# kernel instantiations on smaller cases (profiles/k_pair_*_small_*.md) scaled
+# kernel instantiations on smaller cases (1024 x 256 and 256 x 1024 pairs) scaled
 # by the units processed (2047/511 output rows; 1025/257 kx columns).  Set to
 # None when a kernel changes after its capture.
 NCU_TRAFFIC = {
@@ -81,8 +81,50 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
+class _Nvml:
+    """The few read-only NVML calls the clock sampler needs, through ctypes (no
+    Python NVML package on the GPU hosts).  Raises OSError when NVML is absent."""
+
+    SM = 1  # NVML_CLOCK_SM
+    # clock event reason bits of nvml.h
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        n = ctypes.c_uint()
+        if self.lib.nvmlDeviceGetCount_v2(ctypes.byref(n)) != 0 or n.value == 0:
+            raise OSError("no NVML device")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(min(index, n.value - 1), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reason_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.max_sm = self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def _clock(self, fn):
+        v = self.c.c_uint()
+        if fn(self.h, self.SM, self.c.byref(v)) != 0:
+            raise OSError("clock query failed")
+        return float(v.value)
+
+    def sample(self):
+        r = self.c.c_ulonglong()
+        if self.reason_fn(self.h, self.c.byref(r)) != 0:
+            raise OSError("reason query failed")
+        return self._clock(self.lib.nvmlDeviceGetClockInfo), self.max_sm, \
+            sorted(nm for bit, nm in self.REASONS.items() if r.value & bit)
+
+
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """SM clock and clock event reasons sampled during the timed region: every
+    2 ms from NVML in a background thread, or, without NVML, every 10 ms from
+    nvidia-smi.  stop() returns the median SM clock, the maximum, the reasons
+    seen and the number of samples."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -91,18 +133,49 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.path = None
+        self.thread = None
+        self.samples = []
 
     def start(self):
+        import threading
+        try:
+            nv = _Nvml(self.idx)
+            nv.sample()
+        except Exception:
+            nv = None
+        if nv is not None:
+            self.stop_evt = threading.Event()
+
+            def run():
+                while not self.stop_evt.is_set():
+                    try:
+                        self.samples.append(nv.sample())
+                    except Exception:
+                        pass
+                    time.sleep(0.002)
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return
         fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # nvidia-smi's start-up, so that the region is covered
         except Exception:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_evt.set()
+            self.thread.join(timeout=5)
+            if not self.samples:
+                return None
+            sm = [x[0] for x in self.samples]
+            reasons = sorted({r for x in self.samples for r in x[2]})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.samples),
+                    "reasons": reasons, "samples": len(sm), "source": "nvml, 2 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -113,6 +186,8 @@ class ClockSampler:
         with open(self.path) as f:
             out = parse_clock_csv(f)
         os.unlink(self.path)
+        if out:
+            out["source"] = "nvidia-smi, 10 ms"
         return out
 
 
@@ -140,7 +215,7 @@ def parse_clock_csv(lines):
             "samples": len(sm)}
 
 
-REJECT_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+REJECT_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "hw_power_brake_slowdown")
 
 
 def clocks_rejected(clocks, floor=0.85):
@@ -184,31 +259,80 @@ def cpu_oracle_rate(cfg, budget_s, rng_seed=7):
     return n / secs, n, secs, threads
 
 
+def cpu_oracle_rate_units(units, budget_s, rng_seed=11):
+    """The oracle on a bounded random sample of a workload made of several maps.
+
+    units: list of (A, M_A, B, M_B, K_A, K_B), one per map (B already warped
+    for a rotation).  Shifts are drawn uniformly over all the maps' shifts (a
+    map is drawn with probability proportional to its shift count), so the
+    rate reflects the workload's mix.  Returns (shifts per second, shifts,
+    seconds, threads)."""
+    import oracle
+    rng = np.random.default_rng(rng_seed)
+    sizes = np.array([(u[0].shape[0] + u[2].shape[0] - 1) * (u[0].shape[1] + u[2].shape[1] - 1) for u in units],
+                     np.float64)
+    prob = sizes / sizes.sum()
+    threads = oracle.max_threads()
+
+    def run(n):
+        which = rng.choice(len(units), size=n, p=prob)
+        t0 = time.perf_counter()
+        for k in np.unique(which):
+            A, MA, B, MB, KA, KB = units[k]
+            m = int((which == k).sum())
+            dy = rng.integers(-(A.shape[0] - 1), B.shape[0], m).astype(np.int32)
+            dx = rng.integers(-(A.shape[1] - 1), B.shape[1], m).astype(np.int32)
+            oracle.cmif_at(A, MA, B, MB, KA, KB, dy, dx)
+        return time.perf_counter() - t0
+
+    n = max(64, threads)
+    while True:
+        el = run(n)
+        if el >= min(1.0, budget_s / 10) or n > 10_000_000:
+            break
+        n *= 4
+    n = max(threads, int(n * budget_s / max(el, 1e-9)))
+    secs = run(n)
+    return n / secs, n, secs, threads
+
+
 def run_reference(args, rank, world):
-    """The oracle (the direct method of Sec. 2.2) as the reference arm, on the host cores."""
+    """The oracle (the direct method of Sec. 2.2) as the reference arm, on the host cores.
+
+    A full 1024^2 map takes the direct method about two minutes on 16 cores, so
+    each step is a bounded random sample of the map's shifts (a few seconds);
+    ms_per_step is the measured time of one such step and units_per_step its
+    shifts, so that value = units / time of what actually ran."""
     if rank != 0:
         return
     import synth
     cfg = synth.make_workload(WORKLOAD)
-    per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
-    rates = []
-    n_tot, s_tot, thr = 0, 0.0, 1
+    HA, WA = cfg["A"].shape
+    HB, WB = cfg["B"].shape
+    per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    n_tot, s_tot, thr, ms_steps = 0, 0.0, 1, []
     for i in range(args.warmup + args.steps):
         rate, n, secs, thr = cpu_oracle_rate(cfg, per_step, rng_seed=100 + i)
         if i >= args.warmup:
-            rates.append(rate)
             n_tot += n
             s_tot += secs
+            ms_steps.append(1000.0 * secs)
     value = n_tot / s_tot
-    shifts = (2 * 1024 - 1) ** 2
+    shifts = (HA + HB - 1) * (WA + WB - 1)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * shifts / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms_steps) / len(ms_steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "shifts_per_map": shifts},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": HA, "W": WA, "K_A": cfg["K_A"], "K_B": cfg["K_B"],
+                   "shifts_per_map": shifts, "angles": 1, "precision": "FP64 direct method (oracle)",
+                   "gamma": GAMMA, "units_per_step": n_tot // max(1, args.steps),
+                   "step": "a bounded random sample of the map's shifts",
+                   "ms_per_map_at_this_rate": 1000.0 * shifts / value,
+                   "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                          "sample": f"{n_tot} random shifts of the 1024^2 K=16 map over {args.steps} steps "
-                                   f"(direct method, FP64 entropies)"},
+                                   f"of ~{per_step:.0f} s (direct method, FP64 entropies)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -410,12 +534,31 @@ def run_secondary(args):
     clocks = clk.stop()
     ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / steps
     st = plan.status()
+    cpu = None
+    if not args.no_cpu_baseline and args.workload in ("plain64", "single256", "rotation", "batch"):
+        # the oracle on a bounded sample of the same workload (host cores, after the timed region)
+        import oracle
+        if args.workload == "batch":
+            ou = [(p["A"], p["M_A"]) + oracle.warp_nn(p["B"], p["M_B"], th) + (p["K_A"], p["K_B"])
+                  for p in cfg["pairs"] for th in p["angles"]]
+            what = "random shifts over the 128 pairs x 4 angles (B warped by the oracle's NN warp)"
+        elif args.workload == "rotation":
+            ou = [(cfg["A"], cfg["M_A"]) + oracle.warp_nn(cfg["B"], cfg["M_B"], th) + (cfg["K_A"], cfg["K_B"])
+                  for th in cfg["angles"][::8]]
+            what = "random shifts of 8 of the 64 angles' maps (B warped by the oracle's NN warp)"
+        else:
+            ou = [(cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], cfg["K_A"], cfg["K_B"])]
+            what = "random shifts of the map"
+        rate, n_s, secs, thr = cpu_oracle_rate_units(ou, 10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{n_s} {what} ({secs:.1f} s, direct method, FP64)"}
     print(json.dumps({"metric": METRIC.replace("at 1024², K=16", "on " + name), "value": units / (ms * 1e-3),
                       "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "FP32" in name else "f64",
                       "data": "synthetic", "config": {"workload": name, "units_per_step": units,
                                                        "l2": "flushed between steps (256 MB write)"},
-                      "clocks": clocks, "device_status": {"status": st[0], "max_residual": st[1], "escalations": st[2]},
+                      "clocks": clocks, "cpu_baseline": cpu,
+                      "device_status": {"status": st[0], "max_residual": st[1], "escalations": st[2]},
                       **({"impl": "torch.fft (cuFFT) plain form: comparison baseline, not this library"}
                          if args.workload == "torchfft" else {})}),
           flush=True)

@@ -83,7 +83,7 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
 #define CMIF_FLAG_DEBUG_COUNTS 1u /* allow a non-NULL counts output in cmif_compute */
 #define CMIF_FLAG_GRAPH 2u        /* capture each call's launches in a CUDA graph once and replay it while the
                                      call's arguments (pointers, gamma, angles) are unchanged */
-#define CMIF_FLAG_WINDOW 4u       /* Alg. 1's padded search window (Sec. 4, Alg. 1's ZERO-PAD step: A and M_A zero-padded
+#define CMIF_FLAG_WINDOW 4u       /* Alg. 1's padded search window (Sec. 3.6, Alg. 1's ZERO-PAD step: A and M_A zero-padded
                                      by p_i = ceil(|X_B|_i (1 - gamma)) along each axis).  X_S becomes the shifts
                                      that keep B's domain inside padded A's: chi_i in [|X_B|_i - |X_A|_i - p_i, p_i]
                                      (|chi_i| <= p_i for equal sizes), intersected with the full range.  Only the
@@ -91,7 +91,7 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
                                      N = 0); max N and the peak are taken over the window.  A call whose window
                                      is empty (B cannot fit inside padded A) returns CMIF_ERR_INVALID_ARG. */
 #define CMIF_FLAG_NMI 8u          /* the map (mi_map, mi_maps) holds the normalised MI the paper cites next to MI
-                                     (Sec. 2), NMI = (H_A + H_B) / H_AB, from the same counts and fixed-point
+                                     (Sec. 2.1), NMI = (H_A + H_B) / H_AB, from the same counts and fixed-point
                                      entropy sums; 0 where N = 0 or H_AB = 0 (0/0 = 0, Sec. 3.2).  Alg. 1's
                                      argmax and the peaks then maximise NMI. */
 #define CMIF_FLAG_WEIGHTED 16u    /* the plan computes spatially weighted MI with cmif_compute_weighted (needs
@@ -200,12 +200,14 @@ cmif_status cmif_rotate_nn(const int32_t* B, const uint8_t* M_B, int H, int W, d
  *   topk_dev       : device cmif_peak[top_k]
  *   mi_maps        : device double[n_angles * R * C] or NULL (per-angle maps,
  *                    angle-major; NULL keeps only the peaks)
+ *   n_maps         : device int32[n_angles * R * C] or NULL: the per-angle
+ *                    N maps (Eq. number), same layout
  * The plan's sizes are those of A and of B (the rotation keeps B's canvas). */
 cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
                                  const uint8_t* M_B, const double* angles_rad_host, int n_angles, double gamma,
-                                 int top_k, cmif_peak* topk_dev, double* mi_maps, void* stream);
+                                 int top_k, cmif_peak* topk_dev, double* mi_maps, int32_t* n_maps, void* stream);
 
-/* Spatially weighted MI (SWMI, Sec. 3 "Generalization to spatially weighted MI"):
+/* Spatially weighted MI (SWMI, Sec. 3.3 "Generalization to spatially weighted MI"):
  * the level sets carry the weights, L_a^W[A](x) = W_A(x) where A(x) = a, else 0
  * (likewise B with W_B), so every count becomes a weighted sum,
  * C_AB^{a,b}(chi) = sum_x W_A(x) W_B(x + chi) [A(x) = a][B(x + chi) = b], and
@@ -226,7 +228,7 @@ cmif_status cmif_compute_weighted(cmif_plan plan, const int32_t* A, const double
                                   const double* W_B, double* mi_map, double* nw_map, double gamma, cmif_peak* peak_dev,
                                   void* stream);
 
-/* Two-stage rigid alignment (Sec. 4, the paragraph after Alg. 1): (i) Alg. 1
+/* Two-stage rigid alignment (Sec. 3.6, the paragraph after Alg. 1): (i) Alg. 1
  * over the grid theta_t = 2 pi t / n_grid, t < n_grid; (ii) Alg. 1 over
  * n_refine angles theta* + (2 u_i - 1) 2 pi / n_grid around the grid winner
  * theta* (0 when no grid angle has I_T > 0), continuing stage (i)'s I and
@@ -285,7 +287,7 @@ cmif_status cmif_batch_destroy(cmif_batch batch);
 
 /* Device status of the last call on this plan (synchronises the plan's
  * last stream).  device_side: CMIF_OK, or the first device problem in the
- * order LABEL_RANGE, PRECISION, TIMEOUT.  max_residual: the largest
+ * order LABEL_RANGE, TIMEOUT (the map is incomplete), PRECISION.  max_residual: the largest
  * pre-rounding residual of the authoritative precision.  escalations:
  * second-precision re-runs done by CMIF_AUTO.  Any output pointer may be NULL. */
 cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* max_residual, int* escalations);
@@ -315,12 +317,41 @@ cmif_status cmif_plan_stage_times(cmif_plan plan, int max_n, int* n, double* ms,
  * the B-marginals would not fit in shared memory; CMIF_ERR_INVALID_ARG as
  * cmif_compute.  The first call on a device resolves the array's address and
  * uploads the twiddle tables with a synchronous copy: make that first call
- * before any stream capture.  All calls share the one array: calls that may
+ * before any stream capture (a first call on a stream that is being captured
+ * returns CMIF_ERR_INVALID_ARG and does nothing).  All calls share the one array: calls that may
  * overlap on the GPU (different streams, threads) race and must not be issued. */
 cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, int K_A, int K_B, const int32_t* A,
                                  const uint8_t* M_A, const int32_t* B, const uint8_t* M_B, double* mi_map,
                                  int32_t* n_map, double gamma, cmif_peak* peak_dev, int32_t* status_dev,
                                  void* stream);
+
+/* Fixed-point scale of the epilogue's per-shift entropy sums (Eq. finalentropy):
+ * units of 2^-CMIF_ENTROPY_FIX_BITS. */
+#define CMIF_ENTROPY_FIX_BITS 24
+
+/* The per-count entropy term T(c) = c log2 c of Eq. finalentropy, exactly as
+ * the row epilogue evaluates it (every precision), for the counts
+ * c = c0 .. c0 + n - 1: out_dev[i] = T(c0 + i) in units of
+ * 2^-CMIF_ENTROPY_FIX_BITS.  T(c) = c * L(c) with an integer L(c), the
+ * fixed-point log2 c; T(0) = T(1) = 0.  The MI of a shift is
+ * (sum_joint T - sum_A T - sum_B T + T(N)) / N (Eq. finalentropy rearranged),
+ * so its error is at most 4 * max_c |L(c) 2^-24 - log2 c|; this entry point
+ * lets a caller measure that maximum over every count a map can hold
+ * (c <= 2^22).  out_dev: device int64[n]; 0 <= c0, 0 <= n, c0 + n <= 2^22 + 1
+ * (else CMIF_ERR_INVALID_ARG).  Asynchronous on stream. */
+cmif_status cmif_entropy_terms(int c0, int n, int64_t* out_dev, void* stream);
+
+/* Diagnostics of the bounded device waits (Sec. 3.2's row transforms run in a
+ * kernel whose rows arrive by bulk copies completed on mbarriers; every wait
+ * gives up after a poll limit, records CMIF_ERR_TIMEOUT in the status word and
+ * ends the kernel's work cleanly).  poll_limit > 0 sets the limit of the
+ * plan's later calls (0 restores the default of 2^24 polls); withhold_row >= 0
+ * makes the Tensor-Memory row kernel (FP32, transform widths 1024 and 2048)
+ * skip the bulk copy of that output row's first label pair, so that the wait
+ * for it runs out: the call then reports CMIF_ERR_TIMEOUT from cmif_get_status
+ * and that map row is not written.  -1 turns it off.  Used by the tests to
+ * exercise the timeout path without any fault; not for production calls. */
+cmif_status cmif_plan_set_wait_test(cmif_plan plan, int poll_limit, int withhold_row);
 
 /* Static string for a status code. */
 const char* cmif_status_string(cmif_status status);

@@ -20,15 +20,15 @@ Functions and the passages they follow:
                      strict-greater update over transforms of Alg. 1.  Pinned by
                      hand-built cases.
 * ``alg1_padded`` -- one transform of Alg. 1 with its ZERO-PAD step (Alg. 1,
-                     Sec. 4): A and M_A padded by ceil(|X_B|_i (1 - gamma))
+                     Sec. 3.6): A and M_A padded by ceil(|X_B|_i (1 - gamma))
                      zeros along each axis, the direct CMIF of the padded pair, X_S
                      = the shifts that keep B's domain inside padded A's, and the
                      gated argmax over X_S.  Pinned by tests/test_oracle.py
                      (padding changes nothing inside X_S; full-mask cases).
-* ``nmi``         -- the normalised MI the paper cites next to MI (Sec. 2),
+* ``nmi``         -- the normalised MI the paper cites next to MI (Sec. 2.1),
                      (H_A + H_B) / H_AB from the direct method's entropies, 0/0 = 0.
                      Pinned by closed forms (A = B: 2; independent labels: 1).
-* ``swmi``        -- spatially weighted MI (Sec. 3): the direct weighted histogram
+* ``swmi``        -- spatially weighted MI (Sec. 3.3): the direct weighted histogram
                      per displacement (each overlapping pixel pair adds W_A W_B to its
                      joint bin), MI by Eq. mi on the weighted relative frequencies.
                      numpy, small inputs.  Pinned by tests/test_oracle_alg1.py (unit
@@ -39,7 +39,7 @@ Functions and the passages they follow:
                      histogram of the overlapping voxels, MI by Eq. mi.  numpy, small
                      inputs.  Pinned by tests/test_oracle_alg1.py (depth 1 = the C
                      oracle, N closed form, MI(0) = H(A), swap symmetry).
-* ``align_two_stage`` -- the two-stage rigid search of Sec. 4 (grid, then random
+* ``align_two_stage`` -- the two-stage rigid search of Sec. 3.6 (grid, then random
                      refinement in [theta - 2 pi/|Omega|, theta + 2 pi/|Omega|]), the
                      uniform draws passed in.  Pinned by hand-checked compositions.
 """
@@ -259,7 +259,7 @@ def alg1_padded(A, M_A, B, M_B, K_A, K_B, gamma):
 
 
 def align_two_stage(A, M_A, B, M_B, K_A, K_B, n_grid, refine_u, gamma, padded=False, warp=None):
-    """Two-stage rigid alignment (Sec. 4): Alg. 1 over theta_t = 2 pi t / n_grid,
+    """Two-stage rigid alignment (Sec. 3.6): Alg. 1 over theta_t = 2 pi t / n_grid,
     then over theta* + (2 u_i - 1) 2 pi / n_grid (theta* = the grid choice, 0 for
     the identity), keeping I and T-hat across the stages (strict >).
 
@@ -309,7 +309,7 @@ def nmi(A, M_A, B, M_B, K_A, K_B):
 
 
 def swmi(A, W_A, B, W_B, K_A, K_B):
-    """Spatially weighted MI over the full shift range (Sec. 3), by the direct
+    """Spatially weighted MI over the full shift range (Sec. 3.3), by the direct
     weighted histogram: at each chi every pixel pair (x, x + chi) with both weights
     > 0 adds W_A(x) W_B(x + chi) to bin (A(x), B(x + chi)); p = bins / N with N the
     total; MI = sum p log2(p / (p_a p_b)) (Eq. mi), 0 where N = 0.  W_* = None means
@@ -357,7 +357,7 @@ def cmif3(A, M_A, B, M_B, K_A, K_B):
     chi = (dz, dy, dx) of the full linear range, by the direct method: the joint
     histogram of the voxel pairs (A(x), B(x + chi)) where both masks are 1, MI =
     sum p log2(p / (p_a p_b)) (Eq. mi), 0 where N = 0; and NMI = (H_A + H_B) / H_AB
-    from the same histogram's entropies (Sec. 2), 0 where N = 0 or H_AB = 0.
+    from the same histogram's entropies (Sec. 2.1), 0 where N = 0 or H_AB = 0.
     Returns dict(mi, n, nmi, h_ab) as maps of (D_A + D_B - 1) * (H_A + H_B - 1) rows
     (depth-offset major) by W_A + W_B - 1."""
     A = np.asarray(A, np.int64)

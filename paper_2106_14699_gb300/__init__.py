@@ -51,7 +51,7 @@ EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_create_3d", "cm
            "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
            "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_rotate_nn", "cmif_align_rotations",
            "cmif_align_two_stage", "cmif_compute_weighted", "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status",
-           "cmif_batch_destroy", "cmif_status_string"]
+           "cmif_batch_destroy", "cmif_entropy_terms", "cmif_plan_set_wait_test", "cmif_status_string"]
 
 _lib = None
 
@@ -77,13 +77,15 @@ def lib():
         L.cmif_plan_stage_times.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_char_p)]
         L.cmif_compute_noalloc.argtypes = [I, I, I, I, I, I, P, P, P, P, P, P, D, P, P, P]
         L.cmif_rotate_nn.argtypes = [P, P, I, I, D, P, P, P]
-        L.cmif_align_rotations.argtypes = [P, P, P, P, P, P, I, D, I, P, P, P]
+        L.cmif_align_rotations.argtypes = [P, P, P, P, P, P, I, D, I, P, P, P, P]
         L.cmif_compute_weighted.argtypes = [P, P, P, P, P, P, P, D, P, P]
         L.cmif_align_two_stage.argtypes = [P, P, P, P, P, I, P, I, D, ctypes.POINTER(Peak), ctypes.POINTER(D), P]
         L.cmif_batch_create.argtypes = [ctypes.POINTER(P), I, P, I, U]
         L.cmif_compute_batch.argtypes = [P, P, P, P]
         L.cmif_batch_get_status.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
         L.cmif_batch_destroy.argtypes = [P]
+        L.cmif_entropy_terms.argtypes = [I, I, P, P]
+        L.cmif_plan_set_wait_test.argtypes = [P, I, I]
         L.cmif_status_string.argtypes = [I]
         L.cmif_status_string.restype = ctypes.c_char_p
         for name in EXPORTS[:-1]:
@@ -158,12 +160,13 @@ class Plan:
         _check(lib().cmif_compute_host(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), _ptr(mi_map), _ptr(n_map),
                                        float(gamma), pk, _stream(stream)), "cmif_compute_host")
 
-    def align_rotations(self, A, M_A, B, M_B, angles_rad, gamma, top_k, topk_dev, mi_maps=None, stream=None):
+    def align_rotations(self, A, M_A, B, M_B, angles_rad, gamma, top_k, topk_dev, mi_maps=None, stream=None,
+                        n_maps=None):
         """Alg. 1 over rotations (device tensors; angles: host sequence of radians); asynchronous."""
         ang = np.ascontiguousarray(np.asarray(angles_rad, dtype=np.float64))
         _check(lib().cmif_align_rotations(self._h, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B), ang.ctypes.data,
                                           len(ang), float(gamma), int(top_k), _ptr(topk_dev), _ptr(mi_maps),
-                                          _stream(stream)), "cmif_align_rotations")
+                                          _ptr(n_maps), _stream(stream)), "cmif_align_rotations")
 
     def align_two_stage(self, A, M_A, B, M_B, n_grid, refine_u, gamma, stream=None):
         """Two-stage rigid alignment; returns ((angle_idx, dy, dx, n, mi), angle_rad); synchronises."""
@@ -173,6 +176,10 @@ class Plan:
                                           u.ctypes.data if len(u) else None, len(u), float(gamma), ctypes.byref(pk),
                                           ctypes.byref(ang), _stream(stream)), "cmif_align_two_stage")
         return (pk.angle_idx, pk.dy, pk.dx, pk.n, pk.mi), ang.value
+
+    def set_wait_test(self, poll_limit=0, withhold_row=-1):
+        """Diagnostics of the bounded device waits (cmif_plan_set_wait_test)."""
+        _check(lib().cmif_plan_set_wait_test(self._h, int(poll_limit), int(withhold_row)), "cmif_plan_set_wait_test")
 
     def status(self):
         """(device status name, max residual, escalations) of the last call; synchronises."""
@@ -288,14 +295,53 @@ def peaks_from_bytes(buf, count):
     return out
 
 
+def entropy_terms(c0, n, out, stream=None):
+    """cmif_entropy_terms: out (torch int64 CUDA tensor of n elements) = the epilogue's c log2 c
+    for c = c0 .. c0 + n - 1, in units of 2^-ENTROPY_FIX_BITS."""
+    _check(lib().cmif_entropy_terms(int(c0), int(n), _ptr(out), _stream(stream)), "cmif_entropy_terms")
+
+
+ENTROPY_FIX_BITS = 24
+
+
 def compute_noalloc(A, M_A, B, M_B, K_A, K_B, mi_map, n_map=None, gamma=0.0, peak=None, status=None,
                     stream=None):
-    """cmif_compute_noalloc on torch CUDA tensors (no plan, no device allocation in the library)."""
+    """cmif_compute_noalloc on torch CUDA tensors (no plan, no device allocation in the library).
+
+    The tensors are checked here (dtype, shape, contiguity, device) because the C
+    entry point writes through the raw pointers it is given; the call runs on A's device."""
+    import torch
     H_A, W_A = A.shape
     H_B, W_B = B.shape
-    _check(lib().cmif_compute_noalloc(H_A, W_A, H_B, W_B, K_A, K_B, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B),
-                                      _ptr(mi_map), _ptr(n_map), float(gamma), _ptr(peak), _ptr(status),
-                                      _stream(stream)), "cmif_compute_noalloc")
+    R, C = H_A + H_B - 1, W_A + W_B - 1
+    dev = A.device
+
+    def need(t, dtype, numel, what, shape=None):
+        ok = (t.device == dev and t.dtype == dtype and t.is_contiguous() and t.numel() >= numel and
+              (shape is None or tuple(t.shape) == shape))
+        if not ok:
+            raise CmifError(1, f"cmif_compute_noalloc: {what} must be a contiguous {dtype} tensor on {dev}"
+                               + (f" of shape {shape}" if shape else f" with at least {numel} elements"))
+
+    if dev.type != "cuda":
+        raise CmifError(1, "cmif_compute_noalloc: A must be a CUDA tensor")
+    need(A, torch.int32, H_A * W_A, "A", (H_A, W_A))
+    need(B, torch.int32, H_B * W_B, "B", (H_B, W_B))
+    if M_A is not None:
+        need(M_A, torch.uint8, H_A * W_A, "M_A", (H_A, W_A))
+    if M_B is not None:
+        need(M_B, torch.uint8, H_B * W_B, "M_B", (H_B, W_B))
+    need(mi_map, torch.float64, R * C, "mi_map", (R, C))
+    if n_map is not None:
+        need(n_map, torch.int32, R * C, "n_map", (R, C))
+    if peak is not None:
+        need(peak, torch.uint8, 24, "peak")
+    if status is not None:
+        need(status, torch.int32, 1, "status")
+    with torch.cuda.device(dev):
+        _check(lib().cmif_compute_noalloc(H_A, W_A, H_B, W_B, K_A, K_B, _ptr(A), _ptr(M_A), _ptr(B), _ptr(M_B),
+                                          _ptr(mi_map), _ptr(n_map), float(gamma), _ptr(peak), _ptr(status),
+                                          _stream(stream)), "cmif_compute_noalloc")
 
 
 def cmif(A, M_A, B, M_B, K_A, K_B, precision=FP32, gamma=0.0, with_counts=False, plan=None, stream=None):

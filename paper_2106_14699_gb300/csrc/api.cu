@@ -72,6 +72,10 @@ struct cmif_plan_s {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
+    // diagnostics (cmif_plan_set_wait_test): poll limit of the row kernel's bounded
+    // waits (0: default) and an output row whose first bulk copy is withheld (-1: none)
+    int test_wait_polls = 0;
+    int test_withhold_row = -1;
 };
 
 namespace {
@@ -202,7 +206,9 @@ struct DeviceGuard {
 
 template <typename T>
 void fill_io(PipeArgs<T>& a, const int32_t* A, const uint8_t* MA, const int32_t* B, const uint8_t* MB, double* mi,
-             int32_t* n, int32_t* counts, DevStatus* st) {
+             int32_t* n, int32_t* counts, DevStatus* st, const cmif_plan_s* p) {
+    a.wait_polls = p->test_wait_polls;
+    a.withhold_row = p->test_withhold_row;
     a.A = A;
     a.MA = MA;
     a.B = B;
@@ -213,7 +219,7 @@ void fill_io(PipeArgs<T>& a, const int32_t* A, const uint8_t* MA, const int32_t*
     a.st = st;
 }
 
-// Alg. 1's search window (Sec. 4: A zero-padded by ceil(|X_B|_i (1 - gamma)) along
+// Alg. 1's search window (Sec. 3.6: A zero-padded by ceil(|X_B|_i (1 - gamma)) along
 // each axis; X_S = the shifts that keep B's domain inside padded A's):
 //   chi_i in [|X_B|_i - |X_A|_i - p_i, p_i], intersected with the full range.
 // In output indices (row = chi_y + H_A - 1) that is [H_B - 1 - p_y, H_A - 1 + p_y].
@@ -242,7 +248,7 @@ cmif_status compute_map(cmif_plan p, const Geom& g, const int32_t* A, const uint
     if (e0 != cudaSuccess) return from_cuda(e0);
     if (p->prec == CMIF_FP32 || p->prec == CMIF_AUTO) {
         PipeArgs<float> a = p->w32.args;
-        fill_io(a, A, MA, B, MB, mi, n, counts, p->st);
+        fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
         a.prof = p->prof.enabled ? &p->prof : nullptr;
         a.stages = stages32;
         a.prec_slot = 0;
@@ -261,7 +267,7 @@ cmif_status compute_map(cmif_plan p, const Geom& g, const int32_t* A, const uint
         cudaError_t e;
         if (second == CMIF_FP64) {
             PipeArgs<double> a = p->w64.args;
-            fill_io(a, A, MA, B, MB, mi, n, counts, p->st);
+            fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
             a.prof = p->prof.enabled ? &p->prof : nullptr;
             a.stages = STAGE_ALL;
             a.prec_slot = 1;
@@ -269,7 +275,7 @@ cmif_status compute_map(cmif_plan p, const Geom& g, const int32_t* A, const uint
             e = run_pipeline<double>(g, a, s);
         } else {
             PipeArgs<df32> a = p->ws32.args;
-            fill_io(a, A, MA, B, MB, mi, n, counts, p->st);
+            fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
             a.prof = p->prof.enabled ? &p->prof : nullptr;
             a.stages = STAGE_ALL;
             a.prec_slot = 1;
@@ -416,8 +422,10 @@ void key_add(std::vector<unsigned char>& k, const V& v) {
 // arguments) is unchanged.  Capture uses relaxed mode and a non-default
 // stream, so the caller's stream may be the legacy default stream.
 template <typename Fn>
-cmif_status run_graph(cmif_plan p, cudaStream_t s, const std::vector<unsigned char>& key, Fn&& record) {
+cmif_status run_graph(cmif_plan p, cudaStream_t s, std::vector<unsigned char> key, Fn&& record) {
     if (!p->use_graph) return record(s);
+    key_add(key, p->test_wait_polls);  // baked into the captured launches
+    key_add(key, p->test_withhold_row);
     cudaError_t e = cudaSuccess;
     if (!(p->gexec && key == p->gkey)) {
         if (!p->cap_stream) {
@@ -449,7 +457,7 @@ cmif_status run_graph(cmif_plan p, cudaStream_t s, const std::vector<unsigned ch
 // Alg. 1 over rotations for one pair (see cmif_align_rotations); enqueues on s.
 cmif_status align_core(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B, const uint8_t* M_B,
                        const double* angles, int n_angles, double gamma, int top_k, void* topk_dev, double* mi_maps,
-                       cudaStream_t s) {
+                       int32_t* n_maps, cudaStream_t s) {
     Geom g;
     if (!call_geom(plan, gamma, &g)) return CMIF_ERR_INVALID_ARG;
     const size_t RC = (size_t)g.R * g.C;
@@ -462,15 +470,17 @@ cmif_status align_core(cmif_plan plan, const int32_t* A, const uint8_t* M_A, con
         plan->prof.end(s);
         if (e != cudaSuccess) return from_cuda(e);
         double* mi = mi_maps ? mi_maps + (size_t)i * RC : plan->mibuf;
-        if (mi_maps && (g.r0 > 0 || g.r1 < g.R)) {  // rows outside the window are not computed: zero
-            e = cudaMemsetAsync(mi, 0, RC * sizeof(double), s);
+        int32_t* nm = n_maps ? n_maps + (size_t)i * RC : plan->nbuf;
+        if (g.r0 > 0 || g.r1 < g.R) {  // rows outside the window are not computed: zero
+            if (mi_maps) e = cudaMemsetAsync(mi, 0, RC * sizeof(double), s);
+            if (e == cudaSuccess && n_maps) e = cudaMemsetAsync(nm, 0, RC * sizeof(int32_t), s);
             if (e != cudaSuccess) return from_cuda(e);
         }
         const unsigned stages = (i == 0) ? STAGE_ALL : (STAGE_FWD_B | STAGE_PAIRS);
-        cmif_status cs = compute_map(plan, g, A, M_A, plan->wB, plan->wM, mi, plan->nbuf, nullptr, s, stages);
+        cmif_status cs = compute_map(plan, g, A, M_A, plan->wB, plan->wM, mi, nm, nullptr, s, stages);
         if (cs != CMIF_OK) return cs;
         plan->prof.begin("peak", s);
-        e = launch_peak(mi, plan->nbuf, g, plan->st, gamma, plan->parts, plan->nparts, i, peaks + i, s);
+        e = launch_peak(mi, nm, g, plan->st, gamma, plan->parts, plan->nparts, i, peaks + i, s);
         plan->prof.end(s);
         if (e != cudaSuccess) return from_cuda(e);
     }
@@ -618,6 +628,8 @@ cmif_status cmif_compute_weighted(cmif_plan plan, const int32_t* A, const double
         a.A = A; a.MA = nullptr; a.B = B; a.MB = nullptr;
         a.WA = W_A; a.WB = W_B; a.weighted = 1;
         a.mi = mi_map; a.nw = nw; a.n = nullptr; a.counts = nullptr; a.st = plan->st;
+        a.wait_polls = plan->test_wait_polls;
+        a.withhold_row = plan->test_withhold_row;
         a.prof = plan->prof.enabled ? &plan->prof : nullptr;
         a.stages = STAGE_ALL;
         a.prec_slot = 1;
@@ -686,8 +698,8 @@ cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* ma
     if (e != cudaSuccess) return from_cuda(e);
     if (device_side) {
         *device_side = (h.flags & STATUS_LABEL_RANGE) ? CMIF_ERR_LABEL_RANGE
-                     : (h.flags & STATUS_PRECISION)   ? CMIF_ERR_PRECISION
                      : (h.flags & STATUS_TIMEOUT)     ? CMIF_ERR_TIMEOUT
+                     : (h.flags & STATUS_PRECISION)   ? CMIF_ERR_PRECISION
                                                       : CMIF_OK;
     }
     if (max_residual) {
@@ -707,7 +719,7 @@ cmif_status cmif_rotate_nn(const int32_t* B, const uint8_t* M_B, int H, int W, d
 
 cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
                                  const uint8_t* M_B, const double* angles_rad_host, int n_angles, double gamma,
-                                 int top_k, cmif_peak* topk_dev, double* mi_maps, void* stream) {
+                                 int top_k, cmif_peak* topk_dev, double* mi_maps, int32_t* n_maps, void* stream) {
     if (!plan || !A || !B || !angles_rad_host || !topk_dev || plan->g.Dz > 1) return CMIF_ERR_INVALID_ARG;
     if (n_angles < 1 || n_angles > kMaxAngles || top_k < 1 || top_k > n_angles) return CMIF_ERR_INVALID_ARG;
     if (!(gamma >= 0.0 && gamma <= 1.0)) return CMIF_ERR_INVALID_ARG;
@@ -720,10 +732,12 @@ cmif_status cmif_align_rotations(cmif_plan plan, const int32_t* A, const uint8_t
     std::vector<unsigned char> key;
     key_add(key, 2);
     key_add(key, A); key_add(key, M_A); key_add(key, B); key_add(key, M_B);
-    key_add(key, gamma); key_add(key, top_k); key_add(key, topk_dev); key_add(key, mi_maps); key_add(key, n_angles);
+    key_add(key, gamma); key_add(key, top_k); key_add(key, topk_dev); key_add(key, mi_maps); key_add(key, n_maps);
+    key_add(key, n_angles);
     for (int i = 0; i < n_angles; ++i) key_add(key, angles_rad_host[i]);
     return run_graph(plan, s, key, [&](cudaStream_t cs) -> cmif_status {
-        return align_core(plan, A, M_A, B, M_B, angles_rad_host, n_angles, gamma, top_k, topk_dev, mi_maps, cs);
+        return align_core(plan, A, M_A, B, M_B, angles_rad_host, n_angles, gamma, top_k, topk_dev, mi_maps, n_maps,
+                          cs);
     });
 }
 
@@ -743,7 +757,7 @@ cmif_status cmif_align_two_stage(cmif_plan plan, const int32_t* A, const uint8_t
     std::vector<double> grid(n_grid);
     for (int t = 0; t < n_grid; ++t) grid[t] = two_pi * t / n_grid;
     cmif_status st = cmif_align_rotations(plan, A, M_A, B, M_B, grid.data(), n_grid, gamma, 1,
-                                          reinterpret_cast<cmif_peak*>(slot), nullptr, stream);
+                                          reinterpret_cast<cmif_peak*>(slot), nullptr, nullptr, stream);
     if (st != CMIF_OK) return st;
     PeakRec best{};
     cudaError_t e = cudaMemcpyAsync(&best, slot, sizeof(PeakRec), cudaMemcpyDeviceToHost, s);
@@ -758,7 +772,7 @@ cmif_status cmif_align_two_stage(cmif_plan plan, const int32_t* A, const uint8_t
         const double half = two_pi / n_grid;
         for (int i = 0; i < n_refine; ++i) ref[i] = best_theta + (2.0 * refine_u_host[i] - 1.0) * half;
         st = cmif_align_rotations(plan, A, M_A, B, M_B, ref.data(), n_refine, gamma, 1,
-                                  reinterpret_cast<cmif_peak*>(slot + 1), nullptr, stream);
+                                  reinterpret_cast<cmif_peak*>(slot + 1), nullptr, nullptr, stream);
         if (st != CMIF_OK) return st;
         PeakRec r2{};
         e = cudaMemcpyAsync(&r2, slot + 1, sizeof(PeakRec), cudaMemcpyDeviceToHost, s);
@@ -858,7 +872,7 @@ cmif_status cmif_compute_batch(cmif_batch batch, cmif_peak* results_dev, int32_t
                 if (e != cudaSuccess) return from_cuda(e);
             } else {
                 st = align_core(p, d.A, d.M_A, d.B, d.M_B, batch->angles[i].data(), d.n_angles, d.gamma, 1,
-                                results_dev + i, nullptr, cs);
+                                results_dev + i, nullptr, nullptr, cs);
                 if (st != CMIF_OK) return st;
             }
             if (status_dev) {
@@ -881,8 +895,8 @@ cmif_status cmif_batch_get_status(cmif_batch batch, cmif_status* device_side, do
     if (e != cudaSuccess) return from_cuda(e);
     if (device_side)
         *device_side = (h.flags & STATUS_LABEL_RANGE) ? CMIF_ERR_LABEL_RANGE
-                     : (h.flags & STATUS_PRECISION)   ? CMIF_ERR_PRECISION
                      : (h.flags & STATUS_TIMEOUT)     ? CMIF_ERR_TIMEOUT
+                     : (h.flags & STATUS_PRECISION)   ? CMIF_ERR_PRECISION
                                                       : CMIF_OK;
     if (max_residual) {
         float f;
@@ -930,6 +944,19 @@ cmif_status cmif_plan_stage_times(cmif_plan plan, int max_n, int* n, double* ms,
         if (names) names[i] = plan->prof.names[i];
     }
     return CMIF_OK;
+}
+
+cmif_status cmif_plan_set_wait_test(cmif_plan plan, int poll_limit, int withhold_row) {
+    if (!plan || poll_limit < 0 || withhold_row < -1) return CMIF_ERR_INVALID_ARG;
+    plan->test_wait_polls = poll_limit;
+    plan->test_withhold_row = withhold_row;
+    return CMIF_OK;
+}
+
+cmif_status cmif_entropy_terms(int c0, int n, int64_t* out_dev, void* stream) {
+    if (!out_dev || c0 < 0 || n < 0 || (long long)c0 + n > (1LL << 22) + 1) return CMIF_ERR_INVALID_ARG;
+    static_assert(sizeof(long long) == sizeof(int64_t), "64-bit terms");
+    return from_cuda(launch_entropy_terms(c0, n, reinterpret_cast<long long*>(out_dev), (cudaStream_t)stream));
 }
 
 const char* cmif_status_string(cmif_status s) {

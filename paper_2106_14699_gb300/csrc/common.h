@@ -40,6 +40,6 @@ struct Geom {
 };
 
 constexpr float kResidualGuard = 0.25f;  // a count whose pre-rounding residual reaches this is not trusted
-constexpr int kFixBits = 22;             // fixed-point scale of sum c*log2(c): units of 2^-22
+constexpr int kFixBits = 24;             // fixed-point scale of sum c*log2(c): units of 2^-24
 
 }  // namespace cmif

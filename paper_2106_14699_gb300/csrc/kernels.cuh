@@ -25,21 +25,21 @@
 namespace cmif {
 
 // ---------------------------------------------------------------------------
-// c * log2(c) for an exact non-negative integer c < 2^23 held in a float,
-// in fixed point (units of 2^-kFixBits) so that per-shift sums are exact,
-// order independent and cheap (integer adds).  log2 of the mantissa comes
-// from the MUFU lg2 approximation.
+// c * log2(c) for an exact non-negative integer c < 2^23 held in a float, in
+// fixed point (units of 2^-kFixBits) so that per-shift sums are exact, order
+// independent and cheap (integer adds): c * L(c), where for c = m * 2^e,
+// m in [1, 2), L(c) = e * 2^F + round(log2(m) * 2^F).  log2(m) comes from the
+// MUFU lg2 approximation; the rounding to the 2^-F grid adds at most 2^-(F+1).
+// The largest |L(c) 2^-F - log2 c| over every count the epilogue can meet is
+// measured exhaustively through cmif_entropy_terms (include/cmif.h).
 __device__ __forceinline__ long long clog2c_fixed(float c) {
     const int ci = __float_as_int(c + 8388608.0f) - 0x4B000000;
     const int bits = __float_as_int(c);
-    const float m = __int_as_float((bits & 0x7FFFFF) | 0x3F800000);
-    const float lm = __log2f(m);
-    // (e << F) + round(lm * 2^F), e = exponent of c, with the constants folded
-    const int L = ((bits >> 23) << kFixBits) + __float_as_int(fmaf(lm, (float)(1 << kFixBits), 12582912.0f)) -
-                  (0x4B400000 + (127 << kFixBits));
+    const float lm = __log2f(__int_as_float((bits & 0x7FFFFF) | 0x3F800000));
     // c = 0: ci = 0, so the term is 0 (Sec. 3.2: 0 log 0 = 0) whatever L is.  c = 1:
-    // m = 1 and e = 0, so L = round(log2(1) * 2^F) = 0.  T stays one fixed function
-    // of c, so equal counts still cancel exactly between joint and marginal sums.
+    // m = 1 and e = 0, so L = 0.  T stays one fixed function of c, so equal counts
+    // still cancel exactly between joint and marginal sums.
+    const int L = ((bits >> 23) - 127) * (1 << kFixBits) + __float2int_rn(lm * (float)(1 << kFixBits));
     return (long long)ci * (long long)L;
 }
 
@@ -65,7 +65,7 @@ __device__ __forceinline__ double mi_finish(long long S, int N) {
 }
 
 // NMI(chi) = (H_A + H_B) / H_AB (the normalised MI the paper cites next to
-// MI, Sec. 2), from the same fixed-point sums kept apart: SJ = sum_joint c log2 c,
+// MI, Sec. 2.1), from the same fixed-point sums kept apart: SJ = sum_joint c log2 c,
 // SM = sum_A + sum_B.  With T(N) = N log2 N: H_A + H_B = (2 T(N) - SM) / N and
 // H_AB = (T(N) - SJ) / N.  0 when N = 0 or H_AB = 0 (0/0 = 0, Sec. 3.2).
 __device__ __forceinline__ double nmi_finish(long long SJ, long long SM, int N) {
@@ -141,7 +141,7 @@ struct TeamGeom {
 // stages the row as one byte per pixel (the label, or kMaskedOut where the
 // mask is 0; the label range is checked here), then every team builds its two
 // level sets from shared memory.  With a weight image WX (spatially weighted
-// MI, Sec. 3) the level sets carry the weight W(x) instead of 1 (weight 0 plays
+// MI, Sec. 3.3) the level sets carry the weight W(x) instead of 1 (weight 0 plays
 // the mask's 0) and the row's weights are staged too.
 constexpr unsigned char kMaskedOut = 255;
 
@@ -715,7 +715,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Spatially weighted MI (Sec. 3): the inverse row transform of weighted
+// Spatially weighted MI (Sec. 3.3): the inverse row transform of weighted
 // correlations (FP64 transforms) and the MI of their real-valued counts.  The
 // counts are not integers, so nothing is rounded: each position accumulates
 // sum c log2 c over joint, A- and B-marginal counts in FP64, with c log2 c = 0

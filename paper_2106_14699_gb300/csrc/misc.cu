@@ -179,11 +179,11 @@ cudaError_t launch_topk(const void* peaks, int n, int k, void* out, cudaStream_t
     return cudaGetLastError();
 }
 
-// A status word as a cmif_status code (0 OK, 2 LABEL_RANGE, 5 PRECISION, 6 TIMEOUT).
+// A status word as a cmif_status code (0 OK, 2 LABEL_RANGE, 6 TIMEOUT, 5 PRECISION, in that order).
 __global__ void k_status_code_of(const DevStatus* st, int32_t* out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const unsigned f = st->flags;
-        *out = (f & STATUS_LABEL_RANGE) ? 2 : (f & STATUS_PRECISION) ? 5 : (f & STATUS_TIMEOUT) ? 6 : 0;
+        *out = (f & STATUS_LABEL_RANGE) ? 2 : (f & STATUS_TIMEOUT) ? 6 : (f & STATUS_PRECISION) ? 5 : 0;
     }
 }
 
@@ -237,6 +237,21 @@ cudaError_t launch_check_escalate(DevStatus* st, cudaStream_t s) {
 
 cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s) {
     k_finalize<<<1, 32, 0, s>>>(st, slot_if_escalated, slot_default);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The epilogue's per-count entropy term T(c) = c log2 c (Eq. finalentropy), as
+// the row kernels evaluate it, for the counts c0 .. c0 + n - 1.
+__global__ void k_entropy_terms(int c0, int n, long long* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = clog2c_fixed((float)(c0 + i));
+}
+
+cudaError_t launch_entropy_terms(int c0, int n, long long* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = std::min((n + 255) / 256, 4096);
+    k_entropy_terms<<<blocks, 256, 0, s>>>(c0, n, out);
     return cudaGetLastError();
 }
 

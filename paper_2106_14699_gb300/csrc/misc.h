@@ -28,6 +28,8 @@ cudaError_t launch_warp_nn(const int32_t* B, const uint8_t* MB, int H, int W, do
 cudaError_t launch_merge_status(const DevStatus* m, DevStatus* tot, int slot_default, cudaStream_t s);
 cudaError_t launch_status_code(const DevStatus* st, int32_t* out, cudaStream_t s);
 cudaError_t launch_topk(const void* peaks, int n, int k, void* out, cudaStream_t s);
+// T(c) = c log2 c of the row epilogue (fixed point, units of 2^-kFixBits) for c0 .. c0 + n - 1.
+cudaError_t launch_entropy_terms(int c0, int n, long long* out, cudaStream_t s);
 cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td, Tw<df32>* ts);
 // Host copy of the FP32 twiddle tables (interleaved re, im) and the entry offsets
 // of each table, in the same layout get_twiddles() uploads.

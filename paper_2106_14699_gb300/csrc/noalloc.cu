@@ -33,6 +33,11 @@ struct NoAllocDevice {
 std::mutex g_mu;
 NoAllocDevice g_dev[64];
 
+bool is_set_up(int device) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return device >= 0 && device < 64 && g_dev[device].base != nullptr;
+}
+
 // One-time set-up on the current device: resolve the array's device address and
 // upload the twiddle tables into its head (a synchronous copy, no allocation).
 cudaError_t setup(int device, NoAllocDevice** out) {
@@ -66,8 +71,8 @@ __global__ void k_status_code(const DevStatus* st, int32_t* out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const unsigned f = st->flags;
         *out = (f & STATUS_LABEL_RANGE) ? CMIF_ERR_LABEL_RANGE
-             : (f & STATUS_PRECISION)   ? CMIF_ERR_PRECISION
              : (f & STATUS_TIMEOUT)     ? CMIF_ERR_TIMEOUT
+             : (f & STATUS_PRECISION)   ? CMIF_ERR_PRECISION
                                         : CMIF_OK;
     }
 }
@@ -107,6 +112,14 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
 
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return CMIF_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!is_set_up(device)) {
+        // The first call on a device uploads the twiddle tables with a synchronous
+        // copy, which a stream capture in progress would invalidate: refuse it.
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return CMIF_ERR_CUDA;
+        if (cap != cudaStreamCaptureStatusNone) return CMIF_ERR_INVALID_ARG;
+    }
     NoAllocDevice* d = nullptr;
     cudaError_t e = setup(device, &d);
     if (e != cudaSuccess) return to_status(e);
@@ -135,7 +148,6 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     if (off > kNoAllocBytes) return CMIF_ERR_UNSUPPORTED;
 
     unsigned char* b = d->base;
-    cudaStream_t s = (cudaStream_t)stream;
     DevStatus* st = reinterpret_cast<DevStatus*>(b + oSt);
     e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);  // the status word must start at zero every call
     if (e != cudaSuccess) return to_status(e);
@@ -158,6 +170,8 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     a.cb_smem = true;
     a.prof = nullptr;
     a.tm_cols = 0;
+    a.wait_polls = 0;
+    a.withhold_row = -1;
     e = run_pipeline<float>(g, a, s);
     if (e != cudaSuccess) return to_status(e);
     e = launch_finalize(st, 0, 0, s);

@@ -39,6 +39,8 @@ struct PipeArgs {
     bool cb_smem;     // B-marginal accumulators in shared memory
     Profiler* prof;   // optional launch timing (nullptr = off)
     int tm_cols;      // > 0: use the TMEM / TMA row kernel with this many TMEM columns
+    int wait_polls;   // poll limit of the TMEM row kernel's bounded waits (0: the default)
+    int withhold_row; // diagnostics: output row whose first bulk copy is withheld (-1: none)
     unsigned stages;  // STAGE_* bits: which parts of the sequence to launch
 };
 

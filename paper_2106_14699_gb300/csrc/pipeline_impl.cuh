@@ -75,8 +75,9 @@ static cudaError_t launch_pair_rows_v(const Geom& g, const PipeArgs<T>& a, cudaS
             auto kern = k_pair_rows_tm<Q, NMI>;
             cudaError_t e = ensure_smem(kern, RowTmCfg<Q>::SMEM);
             if (e != cudaSuccess) return e;
-            kern<<<a.rows_grid, RowTmCfg<Q>::THREADS, RowTmCfg<Q>::SMEM, s>>>(a.Y, g, a.tw, a.mi, a.n, a.st,
-                                                                             a.tm_cols);
+            kern<<<a.rows_grid, RowTmCfg<Q>::THREADS, RowTmCfg<Q>::SMEM, s>>>(
+                a.Y, g, a.tw, a.mi, a.n, a.st, a.tm_cols, a.wait_polls > 0 ? a.wait_polls : kDefaultWaitPolls,
+                a.withhold_row);
             return cudaGetLastError();
         }
     }

@@ -37,10 +37,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
                  : "=r"(done) : "r"(bar), "r"(phase) : "memory");
     return done != 0;
 }
-// Bounded wait: gives up after ~2^24 polls (far beyond any copy's latency) and
-// returns false, so that a lost copy can never hang the GPU.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
-    for (int it = 0; it < (1 << 24); ++it)
+// Bounded wait: gives up after `polls` polls (by default 2^24, far beyond any
+// copy's latency) and returns false, so that a lost copy can never hang the GPU.
+constexpr int kDefaultWaitPolls = 1 << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, int polls = kDefaultWaitPolls) {
+    for (int it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, phase)) return true;
     return false;
 }
@@ -147,7 +148,10 @@ template <int Q, bool NMI>
 __global__ void __launch_bounds__(RowTmCfg<Q>::THREADS, 1)
 k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* __restrict__ mi_map,
                int32_t* __restrict__ n_map, DevStatus* __restrict__ st,
-               int tm_cols) {
+               int tm_cols, int wait_polls, int withhold_row) {
+    // wait_polls: poll limit of the bounded waits.  withhold_row >= 0 (diagnostics
+    // only): the bulk copy of that output row's first pair is never issued, so the
+    // wait for it runs out and the kernel takes its timeout path.
     using C = RowTmCfg<Q>;
     constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, BT = C::THREADS, QH = C::QH;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -182,6 +186,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     uint32_t phase = 0;
     bool pending = false;  // a copy issued for this team and not yet waited for
     auto issue = [&](int row_i, int pair_i) {
+        if (row_i == withhold_row && pair_i == 0) return;  // diagnostics: leave this wait without its copy
         if (lane == 0) {
             fence_proxy_async_smem();
             const cpx<float>* src = Y + ((size_t)pair_i * Rout + row_i) * Qs;
@@ -215,7 +220,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
             const int pair = base + team;
             const bool act = pair < npairs;
             if (act) {
-                if (mbar_wait_bounded(bar, phase)) {
+                if (mbar_wait_bounded(bar, phase, wait_polls)) {
                     phase ^= 1u;
                     pending = false;
                 } else {
@@ -373,7 +378,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     }
     // A team may still have a copy in flight (prefetched for an item it will not run
     // after an abort): wait for it, bounded, before the block exits.
-    if (pending) mbar_wait_bounded(bar, phase);
+    if (pending) mbar_wait_bounded(bar, phase, wait_polls);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         res_max = fmaxf(res_max, __shfl_xor_sync(0xffffffffu, res_max, off));

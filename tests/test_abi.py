@@ -72,7 +72,7 @@ def test_host_side_argument_errors_of_the_extensions(libcmif):
     assert ce(P, 4, 4, 4, 4, 2, 2, cm.FP64, cm.FLAG_WEIGHTED | cm.FLAG_NMI) == UNSUPPORTED     # MI only
     assert ce(P, 4, 4, 4, 4, 2, 2, cm.FP64, cm.FLAG_WEIGHTED | cm.FLAG_DEBUG_COUNTS) == UNSUPPORTED
     assert libcmif.cmif_compute_weighted(None, None, None, None, None, None, None, 0.0, None, None) == INVALID
-    assert libcmif.cmif_align_rotations(None, None, None, None, None, None, 1, 0.5, 1, None, None, None) == INVALID
+    assert libcmif.cmif_align_rotations(None, None, None, None, None, None, 1, 0.5, 1, None, None, None, None) == INVALID
     pk, th = cm.Peak(), ctypes.c_double()
     assert libcmif.cmif_align_two_stage(None, None, None, None, None, 8, None, 0, 0.5, ctypes.byref(pk),
                                         ctypes.byref(th), None) == INVALID
@@ -81,6 +81,10 @@ def test_host_side_argument_errors_of_the_extensions(libcmif):
     assert libcmif.cmif_batch_create(ctypes.byref(b), 0, None, cm.FP32, 0) == INVALID          # no pairs
     assert libcmif.cmif_batch_create(None, 1, None, cm.FP32, 0) == INVALID
     assert not b.value
+    assert libcmif.cmif_entropy_terms(0, 4, None, None) == INVALID                              # no output
+    assert libcmif.cmif_entropy_terms(-1, 4, ctypes.c_void_p(16), None) == INVALID              # c0 < 0
+    assert libcmif.cmif_entropy_terms((1 << 22) - 2, 4, ctypes.c_void_p(16), None) == INVALID  # beyond 2^22
+    assert libcmif.cmif_plan_set_wait_test(None, 0, -1) == INVALID
 
 
 _LAYOUT_PROBE = r"""
@@ -100,6 +104,7 @@ int main(void) {
            CMIF_FLAG_WEIGHTED);
     printf("status %d %d %d %d %d %d %d %d %d\n", CMIF_OK, CMIF_ERR_INVALID_ARG, CMIF_ERR_LABEL_RANGE, CMIF_ERR_OOM,
            CMIF_ERR_CUDA, CMIF_ERR_PRECISION, CMIF_ERR_TIMEOUT, CMIF_ERR_NOT_IMPLEMENTED, CMIF_ERR_UNSUPPORTED);
+    printf("fixbits %d\n", CMIF_ENTROPY_FIX_BITS);
     return 0;
 }
 """
@@ -122,6 +127,7 @@ def test_binding_mirrors_the_header(tmp_path, libcmif):
     assert [int(v) for v in out["prec"].split()] == [cm.FP32, cm.SPLIT32, cm.FP64, cm.AUTO]
     assert [int(v) for v in out["flags"].split()] == [cm.FLAG_DEBUG_COUNTS, cm.FLAG_GRAPH, cm.FLAG_WINDOW,
                                                       cm.FLAG_NMI, cm.FLAG_WEIGHTED]
+    assert int(out["fixbits"]) == cm.ENTROPY_FIX_BITS
     codes = [int(v) for v in out["status"].split()]
     assert codes == sorted(cm.STATUS_NAMES)
     for c in codes:

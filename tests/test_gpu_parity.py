@@ -1,9 +1,10 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
 Counts (joint C_AB^{a,b}, marginals C_A^a, C_B^b and N) must be bit-exact;
-MI must be within 1e-6 bits of the oracle's FP64 value (the epilogue reduces
-c log2 c in fixed point, an FP64-grade reduction); the rounding residual of
-every count must stay under the 0.25 guard.
+MI must be within MI_TOL of the oracle's FP64 value (tests/tolerances.py: the
+epilogue sums c log2 c exactly in fixed point, each term from a log2 whose
+error over every possible count is bounded by an exhaustive test); the
+rounding residual of every count must stay under the 0.25 guard.
 """
 import math
 
@@ -12,11 +13,11 @@ import pytest
 
 import oracle
 import synth
+from tolerances import MI_TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-MI_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import synth
+from tolerances import MI_TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -67,7 +68,7 @@ def test_single1024_three_precisions(cm, capsys):
         report.append((name, ms, st[1], mism, full_mism, err, st[0]))
         assert st[0] == "OK" and st[1] < 0.25
         assert mism == 0 and full_mism == 0
-        assert err <= 1e-6
+        assert err <= MI_TOL
         if name != "FP64":
             del counts
         plan.close()

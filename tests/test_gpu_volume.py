@@ -1,15 +1,15 @@
 """GPU parity of the CMIF of label VOLUMES (cmif_plan_create_3d) against the
-oracle's direct 3-D method: N bit-exact, MI within 1e-6, the peak (dz, dy, dx);
+oracle's direct 3-D method: N bit-exact, MI within MI_TOL, the peak (dz, dy, dx);
 and a depth-1 volume plan equal to the image plan."""
 import numpy as np
 import pytest
 
 import oracle
+from tolerances import MI_TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-MI_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")

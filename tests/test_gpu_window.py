@@ -12,11 +12,11 @@ import pytest
 
 import oracle
 import synth
+from tolerances import MI_TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-MI_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")

@@ -1,5 +1,5 @@
 """Pins of the oracle's extensions: Alg. 1's ZERO-PAD search window (Alg. 1,
-Sec. 4), the two-stage rigid search (Sec. 4), NMI (Sec. 2), SWMI (Sec. 3) and
+Sec. 3.6), the two-stage rigid search (Sec. 3.6), NMI (Sec. 2.1), SWMI (Sec. 3.3) and
 label volumes.
 
 Each pin ties the oracle to something other than itself: the unpadded direct
@@ -137,7 +137,7 @@ def test_nmi_closed_forms():
 
 
 def test_swmi_pins():
-    """SWMI (Sec. 3): unit weights give the binary CMIF; 0/1 weights give the
+    """SWMI (Sec. 3.3): unit weights give the binary CMIF; 0/1 weights give the
     masked CMIF; scaling a weight image leaves MI unchanged (the relative
     frequencies do not change); for A = B at chi = 0 the weighted joint
     histogram is diagonal with weights w^2, so MI = the entropy of the labels
