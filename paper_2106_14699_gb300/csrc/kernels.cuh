@@ -160,7 +160,11 @@ struct FwdRowsCfg {
 template <typename T, int Q>
 __global__ void __launch_bounds__(FwdRowsCfg<T, Q>::THREADS)
 k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const double* __restrict__ WX, int H, int W,
-           int K, int Qs, cpx<T>* __restrict__ T1, Tw<T> tw, DevStatus* __restrict__ st, int conditional) {
+           int K, int Qs, cpx<T>* __restrict__ T1, Tw<T> tw, DevStatus* __restrict__ st, int conditional,
+           int* __restrict__ popc, const unsigned char* __restrict__ plane_need) {
+    // popc (nullable): per-label pixel counts under mask 1 are added to popc[0 .. K).
+    // plane_need (nullable): only planes whose entry is 1 are transformed (a team
+    // whose two planes are both unneeded idles; a block with no needed plane returns).
     using C = FwdRowsCfg<T, Q>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R;
@@ -170,7 +174,17 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const 
     const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
     const int npp = (K + 1) / 2;
     const int y = blockIdx.x, pp = blockIdx.y * C::TPB + team;
-    const bool active = pp < npp;
+    auto needed = [&](int q) {
+        if (q >= npp) return false;
+        if (!plane_need) return true;
+        return plane_need[2 * q] == 1 || (2 * q + 1 < K && plane_need[2 * q + 1] == 1);
+    };
+    if (plane_need) {
+        bool any = false;
+        for (int t = 0; t < C::TPB; ++t) any |= needed(blockIdx.y * C::TPB + t);
+        if (!any) return;  // uniform over the block
+    }
+    const bool active = needed(pp);
     const int la = 2 * pp, lb = 2 * pp + 1;
     const int32_t* xr = X + (size_t)y * W;
     const uint8_t* mr = MX ? MX + (size_t)y * W : nullptr;
@@ -190,6 +204,21 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const 
     }
     if (bad && blockIdx.y == 0) atomicOr(&st->flags, STATUS_LABEL_RANGE);
     __syncthreads();
+    if (popc && blockIdx.y == 0) {
+        // label histogram of the row (shared-memory bins in the first team's region,
+        // which the transform below only overwrites after the next barrier)
+        int* hist = reinterpret_cast<int*>(smem_raw);
+        for (int k = threadIdx.x; k < K; k += C::THREADS) hist[k] = 0;
+        __syncthreads();
+        for (int x = threadIdx.x; x < W; x += C::THREADS) {
+            const int c = code[x];
+            if (c != kMaskedOut) atomicAdd(&hist[c], 1);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += C::THREADS)
+            if (hist[k]) atomicAdd(&popc[k], hist[k]);
+        __syncthreads();
+    }
     unsigned char* region = smem_raw + (size_t)team * C::REGION;
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(region);
     auto load = [&](int x) -> cpx<T> {
@@ -237,9 +266,13 @@ struct ColCfg {
 template <typename T, int P>
 __global__ void __launch_bounds__(ColCfg<T, P>::THREADS)
 k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cpx<T>* __restrict__ F, Tw<T> tw,
-           const DevStatus* __restrict__ st, int conditional, T out_scale) {
+           const DevStatus* __restrict__ st, int conditional, T out_scale,
+           const unsigned char* __restrict__ plane_need, int slices) {
+    // plane_need (nullable): only the planes of labels whose entry is 1 are
+    // transformed; plane p belongs to label p / slices (volumes: slices = depth).
     using C = ColCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
+    if (plane_need && plane_need[blockIdx.y / slices] != 1) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<T>* tile = reinterpret_cast<cpx<T>*>(smem_raw + C::SCR);
@@ -348,12 +381,23 @@ template <typename T, int P, bool VOL>
 __global__ void __launch_bounds__(PairColsCfg<T, P>::THREADS, PairColsCfg<T, P>::MIN_BLOCKS)
 k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA, int KB, int Qh, int HA, int HB,
             int Rout, int Qs, int r0, int r1, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st,
-            int conditional, int* __restrict__ work_ctr, int DA, int DB, int R2) {
+            int conditional, int* __restrict__ work_ctr, int DA, int DB, int R2, const int* __restrict__ plist,
+            const int* __restrict__ lrange, int chunk_off, int chunk_cap) {
+    // List mode (plist non-null): only the pairs plist[lrange[0] + chunk_off + e],
+    // e < min(chunk_cap, lrange[1] - lrange[0] - chunk_off), are computed, pair e's
+    // rows going to Y + e * Rout * Qs.
     using C = PairColsCfg<T, P>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB, NQ = C::NQ;
     const int Dz = VOL ? DA + DB - 1 : 1;
-    const int npairs = KA * KB, nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb * Dz;
+    int npairs = KA * KB, lbase = 0;
+    if (plist) {
+        lbase = lrange[0] + chunk_off;
+        npairs = min(lrange[1] - lbase, chunk_cap);
+        if (npairs <= 0) return;  // uniform: nothing listed for this launch
+    }
+    auto real_pair = [&](int e) { return plist ? __ldg(plist + lbase + e) : e; };
+    const int nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb * Dz;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_item;
     cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -374,7 +418,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     cpx<T> v[M];
     auto load_fa = [&](int it) {
         if constexpr (VOL) return;  // volumes sum over slices in the item itself
-        const int kx = (it / npairs) * TPB + team, a = (it % npairs) / KB;
+        const int kx = (it / npairs) * TPB + team, a = real_pair(it % npairs) / KB;
         if (kx < Qh) {
             const cpx<T>* ga = FA + ((size_t)a * Qh + kx) * P + r * NQ + j;
 #pragma unroll
@@ -388,7 +432,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     while (true) {
         int next = 0;
         if (threadIdx.x == 0) next = atomicAdd(work_ctr, 1);
-        const int pair = item % npairs;
+        const int e = item % npairs, pair = real_pair(e);
         const int kxb = VOL ? item / npairs / Dz : item / npairs;
         const int dzo = VOL ? (item / npairs) % Dz : 0;
         const int kx0 = kxb * TPB, kx = kx0 + team, b = pair % KB;
@@ -410,7 +454,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
 #pragma unroll
             for (int i = 0; i < M; ++i) v[i] = cmulc(__ldg(gb + M * i), v[i]);
         }
-        if (!VOL && pair < KA + KB && (int)threadIdx.x < TPB && kxb + 2 < nkxb) {
+        if (!VOL && !plist && pair < KA + KB && (int)threadIdx.x < TPB && kxb + 2 < nkxb) {
             // the items of this kx block with pair < K_A + K_B each prefetch one
             // spectrum's columns of kx block kxb + 2 into L2 (one bulk request per column)
             const int kf = (kxb + 2) * TPB + threadIdx.x;
@@ -467,7 +511,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
         __syncthreads();
         next = s_item;
         if (next < n_items) load_fa(next);
-        cpx<T>* yp = Y + (size_t)pair * Rout * Qs;
+        cpx<T>* yp = Y + (size_t)e * Rout * Qs;
         if constexpr (sizeof(T) == 4 && TPB >= 2) {
             // Each row chunk of TPB complex leaves as TPB/2 16-byte pieces written by
             // adjacent lanes.  Logical columns 2h, 2h+1 sit in physical piece
@@ -568,7 +612,12 @@ template <typename T, int Q, bool CB_SMEM, bool NMI>
 __global__ void __launch_bounds__(RowCfg<T, Q>::THREADS, RowCfg<T, Q>::MIN_BLOCKS)
 k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ cb_global,
             double* __restrict__ mi_map, int32_t* __restrict__ n_map, int32_t* __restrict__ counts,
-            DevStatus* __restrict__ st, int prec_slot, int conditional) {
+            DevStatus* __restrict__ st, int prec_slot, int conditional, const int32_t* __restrict__ ov,
+            const int* __restrict__ ov_slot, unsigned* __restrict__ pair_res) {
+    // ov / ov_slot (nullable): a pair with ov_slot[pair] = s >= 0 takes its counts
+    // from ov[s][row][position] (exact counts from the second precision) instead of
+    // its own transform, and its residual is not counted.  pair_res (nullable):
+    // each pair's largest residual is folded into pair_res[pair].
     using C = RowCfg<T, Q>;
     constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, BT = C::THREADS;
     constexpr int HALVES = C::HALVES, QH = C::QH;
@@ -602,6 +651,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
         for (int base = 0; base < npairs; base += NT) {
             const int pair = base + team;
             const bool act = pair < npairs;
+            const int ovs = (act && ov_slot) ? ov_slot[pair] : -1;
             const cpx<T>* yr = Y + ((size_t)(act ? pair : 0) * Rout + row) * Qs;
             // Hermitian split: z = IDFT_L(E + iO), z[m] = x[2m] + i x[2m+1]
             auto load = [&](int k) -> cpx<T> {
@@ -616,12 +666,21 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
             team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)],
                                tw.n[ilog2c(L)]);
             // round to the nearest integer; track the worst residual (the exactness guard)
+            float rp = 0.f;
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 const T cr = rint_t<T>(v[k].x), ci = rint_t<T>(v[k].y);
-                res_max = fmaxf(res_max, fmaxf((float)fabs(v[k].x - cr), (float)fabs(v[k].y - ci)));
+                rp = fmaxf(rp, fmaxf((float)fabs(v[k].x - cr), (float)fabs(v[k].y - ci)));
                 v[k].x = cr;
                 v[k].y = ci;
+            }
+            if (ovs < 0) res_max = fmaxf(res_max, rp);
+            if (pair_res) {  // per-pair residual: reduce over the team's lanes of each warp
+                constexpr int WID = C::TEAM < 32 ? C::TEAM : 32;
+                float rr = (act && ovs < 0) ? rp : 0.f;
+#pragma unroll
+                for (int off = WID / 2; off > 0; off >>= 1) rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, off));
+                if (act && ovs < 0 && (lt % WID) == 0) atomic_max_float_pos(&pair_res[pair], rr);
             }
             const int nt = min(NT, npairs - base);
             const int a0 = base / KB, b0 = base - a0 * KB;
@@ -631,9 +690,14 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
                 float2* ob = reinterpret_cast<float2*>(region);
 #pragma unroll
                 for (int k2 = hf * (M / HALVES); k2 < (hf + 1) * (M / HALVES); ++k2) {
-                    const int m = R * (j + M * k2) + r - hf * (L / HALVES);
-                    const cpx<T> z = v[brev(k2, M)];
-                    ob[m] = make_float2((float)z.x, (float)z.y);
+                    const int mf = R * (j + M * k2) + r, m = mf - hf * (L / HALVES);
+                    if (ovs >= 0) {  // exact counts of positions 2 mf, 2 mf + 1 from the second precision
+                        const int2 q = *reinterpret_cast<const int2*>(ov + ((size_t)ovs * Rout + row) * Q + 2 * mf);
+                        ob[m] = make_float2((float)q.x, (float)q.y);
+                    } else {
+                        const cpx<T> z = v[brev(k2, M)];
+                        ob[m] = make_float2((float)z.x, (float)z.y);
+                    }
                 }
                 __syncthreads();
                 // the round's accumulation, compiled twice: with the debug count maps

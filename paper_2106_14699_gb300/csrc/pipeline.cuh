@@ -42,6 +42,17 @@ struct PipeArgs {
     int wait_polls;   // poll limit of the TMEM row kernel's bounded waits (0: the default)
     int withhold_row; // diagnostics: output row whose first bulk copy is withheld (-1: none)
     unsigned stages;  // STAGE_* bits: which parts of the sequence to launch
+    // per-pair precision (CMIF_AUTO): all nullable / 0 when unused
+    int* popA;                  // [K_A] label pixel counts of A, added by the forward row kernel
+    int* popB;                  // [K_B]
+    const unsigned char* needA; // [K_A] planes to transform (entry 1), others skipped
+    const unsigned char* needB; // [K_B]
+    const int* plist;           // list mode of the pair kernels: the list of pairs (a * K_B + b)
+    const int* lrange;          // [2]: entries [lrange[0], lrange[1]) of plist belong to this stage
+    int chunk_off, chunk_cap;   // this launch takes entries lrange[0] + chunk_off .. + chunk_cap
+    int32_t* ov;                // [list slot][R][Q] exact counts of listed pairs (written by the second tier)
+    const int* ov_slot;         // [K_A * K_B] list slot of a pair, -1: the FP32 counts stand
+    unsigned* pair_res;         // [K_A * K_B] largest FP32 residual of each pair (float bits)
 };
 
 enum : unsigned {

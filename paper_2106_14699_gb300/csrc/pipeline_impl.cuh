@@ -20,25 +20,28 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
 
 template <typename T, int Q>
 static cudaError_t launch_fwd_rows(const int32_t* X, const uint8_t* MX, const double* WX, int H, int W, int K, int Qs,
-                                   cpx<T>* T1, const Tw<T>& tw, DevStatus* st, int conditional, cudaStream_t s) {
+                                   cpx<T>* T1, const Tw<T>& tw, DevStatus* st, int conditional, int* popc,
+                                   const unsigned char* need, cudaStream_t s) {
     using C = FwdRowsCfg<T, Q>;
     auto kern = k_fwd_rows<T, Q>;
     cudaError_t e = ensure_smem(kern, C::smem(Q, true));
     if (e != cudaSuccess) return e;
     dim3 grid(H, ((K + 1) / 2 + C::TPB - 1) / C::TPB);
-    kern<<<grid, C::THREADS, C::smem(W, WX != nullptr), s>>>(X, MX, WX, H, W, K, Qs, T1, tw, st, conditional);
+    kern<<<grid, C::THREADS, C::smem(W, WX != nullptr), s>>>(X, MX, WX, H, W, K, Qs, T1, tw, st, conditional, popc,
+                                                             need);
     return cudaGetLastError();
 }
 
 template <typename T, int P>
 static cudaError_t launch_fwd_cols(const cpx<T>* T1, int H, int K, int Qh, int Qs, cpx<T>* F, const Tw<T>& tw,
-                                   const DevStatus* st, int conditional, T out_scale, cudaStream_t s) {
+                                   const DevStatus* st, int conditional, T out_scale, const unsigned char* need,
+                                   int slices, cudaStream_t s) {
     using C = ColCfg<T, P>;
     auto kern = k_fwd_cols<T, P>;
     cudaError_t e = ensure_smem(kern, C::smem(P));
     if (e != cudaSuccess) return e;
     dim3 grid((Qh + C::TPB - 1) / C::TPB, K);
-    kern<<<grid, C::THREADS, C::smem(H), s>>>(T1, H, K, Qh, Qs, F, tw, st, conditional, out_scale);
+    kern<<<grid, C::THREADS, C::smem(H), s>>>(T1, H, K, Qh, Qs, F, tw, st, conditional, out_scale, need, slices);
     return cudaGetLastError();
 }
 
@@ -57,13 +60,15 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
         if (e != cudaSuccess) return e;
         per_sm = n > 0 ? n : 1;
     }
-    const long long items = (long long)g.KA * g.KB * ((g.Qh + C::TPB - 1) / C::TPB) * (VOL ? g.Dz : 1);
+    const long long np = a.plist ? a.chunk_cap : (long long)g.KA * g.KB;  // list mode: at most chunk_cap pairs
+    const long long items = np * ((g.Qh + C::TPB - 1) / C::TPB) * (VOL ? g.Dz : 1);
     const long long slots = a.num_sms > 0 ? (long long)per_sm * a.num_sms : items;
     const int grid = (int)(items < slots ? items : slots);
     e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KA, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, g.r0, g.r1, a.Y, a.tw,
-                                        a.st, a.conditional, a.work_ctr, g.DA, g.DB, g.R2);
+                                        a.st, a.conditional, a.work_ctr, g.DA, g.DB, g.R2, a.plist, a.lrange,
+                                        a.chunk_off, a.chunk_cap);
     return cudaGetLastError();
 }
 
@@ -112,9 +117,9 @@ cudaError_t Sized<T, SZ>::fwd_rows(const Geom& g, const PipeArgs<T>& a, bool b_s
     const double* wa = a.weighted ? a.WA : nullptr;
     // volumes: the D slices of H rows are D * H rows of one image
     return b_side ? launch_fwd_rows<T, SZ>(a.B, a.MB, wb, g.DB * g.HB, g.WB, g.KB, g.Qs, a.T1B, a.tw, a.st,
-                                           a.conditional, s)
+                                           a.conditional, a.popB, a.needB, s)
                   : launch_fwd_rows<T, SZ>(a.A, a.MA, wa, g.DA * g.HA, g.WA, g.KA, g.Qs, a.T1A, a.tw, a.st,
-                                           a.conditional, s);
+                                           a.conditional, a.popA, a.needA, s);
 }
 
 template <typename T, int SZ>
@@ -122,9 +127,9 @@ cudaError_t Sized<T, SZ>::fwd_cols(const Geom& g, const PipeArgs<T>& a, bool b_s
     // B's spectra carry the 1/(P Q) of the unnormalised inverse transform (a power of two: exact)
     // volumes: K * D slice planes of H rows each (plane index label * D + z)
     return b_side ? launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB * g.DB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional,
-                                           T(1.0 / ((double)g.P * (double)g.Q)), s)
+                                           T(1.0 / ((double)g.P * (double)g.Q)), a.needB, g.DB, s)
                   : launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA * g.DA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional,
-                                           T(1), s);
+                                           T(1), a.needA, g.DA, s);
 }
 
 template <typename T, int SZ>
