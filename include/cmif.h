@@ -73,10 +73,22 @@ typedef enum {
  *   CMIF_SPLIT32: two-term FP32 transforms (hi + lo floats, ~48 significant
  *                 bits from FP32 units; exact everywhere in range)
  *   CMIF_FP64   : FP64 transforms (exact everywhere in range; slow on GB300)
- *   CMIF_AUTO   : FP32, re-run on the device in two-term FP32 when the FP32
- *                 residual breaches the guard (no host round trip); the
- *                 environment variable CMIF_AUTO_TIER2=fp64 at plan creation
- *                 makes the re-run FP64 instead. */
+ *   CMIF_AUTO   : FP32 transforms with the precision chosen per label pair,
+ *                 all on the device (no host round trip).  A predicate sends a
+ *                 pair to the second precision up front when the estimated
+ *                 FP32 error of its correlation, 0.25 * 2^-24 * log2(P Q) *
+ *                 sqrt(|X_a| |Y_b|) (|X_a|, |Y_b|: the two labels' pixel counts
+ *                 under the masks), reaches half the guard; the FP32 pass takes
+ *                 those pairs' exact counts and records every other pair's
+ *                 residual; pairs that still reach the guard are computed in
+ *                 the second precision as well and the FP32 row pass runs once
+ *                 more.  Only the listed pairs (at most 128 per map) pay for
+ *                 the second precision.  The second precision is two-term FP32;
+ *                 the environment variable CMIF_AUTO_TIER2=fp64 at plan creation
+ *                 makes it FP64, CMIF_AUTO_PREDICATE=0 turns the predicate
+ *                 off (the guard alone then picks the pairs) and
+ *                 CMIF_AUTO_PREDICATE=all sends every pair (up to the 128-pair
+ *                 list) to the second precision (diagnostics). */
 typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } cmif_precision;
 
 /* Plan flags. */
@@ -288,9 +300,21 @@ cmif_status cmif_batch_destroy(cmif_batch batch);
 /* Device status of the last call on this plan (synchronises the plan's
  * last stream).  device_side: CMIF_OK, or the first device problem in the
  * order LABEL_RANGE, TIMEOUT (the map is incomplete), PRECISION.  max_residual: the largest
- * pre-rounding residual of the authoritative precision.  escalations:
- * second-precision re-runs done by CMIF_AUTO.  Any output pointer may be NULL. */
+ * pre-rounding residual of the authoritative precision (CMIF_AUTO: over
+ * every pair, each in the precision it was computed in).  escalations: label
+ * pairs CMIF_AUTO computed in the second precision, summed over the call's
+ * maps.  Any output pointer may be NULL. */
 cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* max_residual, int* escalations);
+
+/* Per-pair precision of the last call (synchronises), summed over its maps:
+ * pairs_predicted = pairs the CMIF_AUTO predicate sent to the second precision
+ * up front, pairs_escalated = pairs sent there after their FP32 residual
+ * reached the guard, residual_fp32 = the largest residual of the pairs whose
+ * FP32 counts stood, residual_second = the largest residual of the
+ * second-precision pairs (FP64 and two-term plans: their one residual; FP32
+ * plans: 0).  Any output pointer may be NULL. */
+cmif_status cmif_get_precision_report(cmif_plan plan, int* pairs_predicted, int* pairs_escalated,
+                                      double* residual_fp32, double* residual_second);
 
 /* Launch timing (instrumentation, off by default).  When enabled, each
  * compute call records a CUDA event pair on its stream around every kernel

@@ -51,7 +51,8 @@ EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_create_3d", "cm
            "cmif_compute", "cmif_compute_host", "cmif_get_status", "cmif_plan_set_profiling",
            "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_rotate_nn", "cmif_align_rotations",
            "cmif_align_two_stage", "cmif_compute_weighted", "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status",
-           "cmif_batch_destroy", "cmif_entropy_terms", "cmif_plan_set_wait_test", "cmif_status_string"]
+           "cmif_batch_destroy", "cmif_entropy_terms", "cmif_plan_set_wait_test", "cmif_get_precision_report",
+           "cmif_status_string"]
 
 _lib = None
 
@@ -86,6 +87,8 @@ def lib():
         L.cmif_batch_destroy.argtypes = [P]
         L.cmif_entropy_terms.argtypes = [I, I, P, P]
         L.cmif_plan_set_wait_test.argtypes = [P, I, I]
+        L.cmif_get_precision_report.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D),
+                                                ctypes.POINTER(D)]
         L.cmif_status_string.argtypes = [I]
         L.cmif_status_string.restype = ctypes.c_char_p
         for name in EXPORTS[:-1]:
@@ -186,6 +189,13 @@ class Plan:
         ds, res, esc = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
         _check(lib().cmif_get_status(self._h, ctypes.byref(ds), ctypes.byref(res), ctypes.byref(esc)), "cmif_get_status")
         return STATUS_NAMES.get(ds.value, ds.value), res.value, esc.value
+
+    def precision_report(self):
+        """(pairs predicted, pairs escalated, FP32 residual, second-precision residual) of the last call."""
+        pp, pe, r0, r1 = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().cmif_get_precision_report(self._h, ctypes.byref(pp), ctypes.byref(pe), ctypes.byref(r0),
+                                               ctypes.byref(r1)), "cmif_get_precision_report")
+        return pp.value, pe.value, r0.value, r1.value
 
     def set_profiling(self, enable=True):
         _check(lib().cmif_plan_set_profiling(self._h, 1 if enable else 0), "cmif_plan_set_profiling")

@@ -25,6 +25,24 @@ struct Workspace {
     int rows_grid = 0;
     bool cb_smem = true;
     int rows_grid_w = 0;  // > 0: the plan computes weighted maps (FP64 workspace only)
+    int ypairs = 0;       // pairs the Y buffer holds (0: all K_A * K_B; the second precision of AUTO: one chunk)
+};
+
+// Per-pair precision of CMIF_AUTO: device buffers of the pair list and the exact
+// counts of the listed pairs.
+struct Escal {
+    int* popA = nullptr;              // [K_A] label pixel counts (A)
+    int* popB = nullptr;              // [K_B]
+    unsigned char* needA = nullptr;   // [K_A] planes the second precision transforms
+    unsigned char* needB = nullptr;   // [K_B]
+    int* plist = nullptr;             // [K_A K_B] listed pairs, in slot order
+    int* hdr = nullptr;               // [4] list ranges: stage 1 [hdr0, hdr1), stage 2 [hdr1, hdr2)
+    int* ov_slot = nullptr;           // [K_A K_B] slot of a pair, -1 when not listed
+    unsigned* pair_res = nullptr;     // [K_A K_B] FP32 residual per pair (float bits)
+    int32_t* ov = nullptr;            // [cap][R][Q] exact counts of the listed pairs
+    int cap = 0;                      // list capacity (slots)
+    int chunk = 0;                    // pairs per second-precision chunk (its Y buffer)
+    size_t bytes = 0;
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -76,6 +94,10 @@ struct cmif_plan_s {
     // waits (0: default) and an output row whose first bulk copy is withheld (-1: none)
     int test_wait_polls = 0;
     int test_withhold_row = -1;
+    // CMIF_AUTO: per-pair precision (predicate up front, guard after the FP32 pass)
+    Escal esc;
+    double pred_scale = 0.0;   // kappa u log2(PQ): the predicate is pred_scale sqrt(|X_a| |Y_b|) >= pred_thr
+    double pred_thr = 0.0;     // infinite when the predicate is off (CMIF_AUTO_PREDICATE=0)
 };
 
 namespace {
@@ -131,7 +153,7 @@ size_t workspace_bytes(const Geom& g, const Workspace<T>& w) {
     off = align_up(off + (size_t)g.KB * g.DB * g.HB * g.Qs * cs, 256);  // T1B
     off = align_up(off + (size_t)g.KA * g.DA * g.Qh * g.P * cs, 256);   // FA
     off = align_up(off + (size_t)g.KB * g.DB * g.Qh * g.P * cs, 256);   // FB
-    off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);  // Y
+    off = align_up(off + (size_t)(w.ypairs > 0 ? w.ypairs : g.KA * g.KB) * g.R * g.Qs * cs, 256);  // Y
     off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);  // CB
     off = align_up(off + sizeof(int), 256);  // work counter
     if (w.rows_grid_w > 0) {
@@ -150,7 +172,8 @@ void carve_workspace(const Geom& g, Workspace<T>& w, char* base) {
     w.args.T1B = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.DB * g.HB * g.Qs * cs, 256);
     w.args.FA = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.DA * g.Qh * g.P * cs, 256);
     w.args.FB = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KB * g.DB * g.Qh * g.P * cs, 256);
-    w.args.Y = (cpx<T>*)(base + off); off = align_up(off + (size_t)g.KA * g.KB * g.R * g.Qs * cs, 256);
+    w.args.Y = (cpx<T>*)(base + off);
+    off = align_up(off + (size_t)(w.ypairs > 0 ? w.ypairs : g.KA * g.KB) * g.R * g.Qs * cs, 256);
     w.args.cb_global = w.cb_smem ? nullptr : (float*)(base + off);
     off = align_up(off + (w.cb_smem ? 0 : (size_t)w.rows_grid * g.KB * g.Q * sizeof(float)), 256);
     w.args.work_ctr = (int*)(base + off);
@@ -238,55 +261,138 @@ bool call_geom(const cmif_plan p, double gamma, Geom* out) {
     return g.r0 < g.r1 && g.c0 < g.c1;
 }
 
+// Second precision for one stage of the pair list (entries [lrange[0], lrange[1])):
+// the level-set transforms of the planes the listed pairs need, then, chunk by
+// chunk, their products, inverse column transforms and exact counts (into the
+// plan's ov buffer).  Every launch returns at once when the stage lists nothing.
+template <typename T>
+cudaError_t tier2_stage(cmif_plan p, Workspace<T>& w, const Geom& g, const int32_t* A, const uint8_t* MA,
+                        const int32_t* B, const uint8_t* MB, const int* lrange, cudaStream_t s) {
+    PipeArgs<T> b = w.args;
+    fill_io(b, A, MA, B, MB, nullptr, nullptr, nullptr, p->st, p);
+    b.prof = p->prof.enabled ? &p->prof : nullptr;
+    b.prec_slot = 1;
+    b.conditional = 0;
+    b.needA = p->esc.needA;
+    b.needB = p->esc.needB;
+    b.stages = STAGE_FWD_A | STAGE_FWD_B;
+    cudaError_t e = run_pipeline<T>(g, b, s);
+    if (e != cudaSuccess) return e;
+    b.needA = b.needB = nullptr;
+    b.plist = p->esc.plist;
+    b.lrange = lrange;
+    b.ov = p->esc.ov;
+    b.chunk_cap = p->esc.chunk;
+    for (int off = 0; off < p->esc.cap; off += p->esc.chunk) {
+        b.chunk_off = off;
+        e = run_pair_counts<T>(g, b, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename Fn>
+cudaError_t with_tier2(cmif_plan p, Fn&& fn) {
+    return p->tier2 == CMIF_FP64 ? fn(p->w64) : fn(p->ws32);
+}
+
+// CMIF_AUTO: FP32 transforms with per-pair precision.  The predicate picks the
+// pairs whose FP32 correlation would not round exactly and computes them in the
+// second precision first; the FP32 row pass takes their exact counts and records
+// every other pair's residual; pairs that still breach the guard are computed in
+// the second precision too and the FP32 row pass runs once more (on the device,
+// only after a breach).  Counts of every pair are then exact (Sec. 3.2).
+cmif_status compute_map_auto(cmif_plan p, const Geom& g, const int32_t* A, const uint8_t* MA, const int32_t* B,
+                             const uint8_t* MB, double* mi, int32_t* n, int32_t* counts, cudaStream_t s,
+                             unsigned stages32) {
+    Escal& E = p->esc;
+    cudaError_t e = cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s);
+    PipeArgs<float> a = p->w32.args;
+    fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
+    a.prof = p->prof.enabled ? &p->prof : nullptr;
+    a.prec_slot = 0;
+    a.conditional = 0;
+    // 1. FP32 level-set transforms, with the label pixel counts of the predicate
+    if (e == cudaSuccess && (stages32 & STAGE_FWD_A)) e = cudaMemsetAsync(E.popA, 0, g.KA * sizeof(int), s);
+    if (e == cudaSuccess && (stages32 & STAGE_FWD_B)) e = cudaMemsetAsync(E.popB, 0, g.KB * sizeof(int), s);
+    if (e != cudaSuccess) return from_cuda(e);
+    a.popA = (stages32 & STAGE_FWD_A) ? E.popA : nullptr;
+    a.popB = (stages32 & STAGE_FWD_B) ? E.popB : nullptr;
+    a.stages = stages32 & (STAGE_FWD_A | STAGE_FWD_B);
+    if (a.stages) e = run_pipeline<float>(g, a, s);
+    a.popA = a.popB = nullptr;
+    // 2. the predicate: stage 1 of the list
+    p->prof.begin("select_pairs", s);
+    if (e == cudaSuccess)
+        e = launch_select_pairs(E.popA, E.popB, g.KA, g.KB, p->pred_scale, p->pred_thr, E.cap, E.plist, E.hdr,
+                                E.ov_slot, E.pair_res, E.needA, E.needB, p->st, s);
+    p->prof.end(s);
+    // 3. second precision for the predicted pairs
+    if (e == cudaSuccess)
+        e = with_tier2(p, [&](auto& w) { return tier2_stage(p, w, g, A, MA, B, MB, E.hdr + 0, s); });
+    // 4. FP32 pair stages; listed pairs take their exact counts, the others' residuals are kept per pair
+    a.ov = E.ov;
+    a.ov_slot = E.ov_slot;
+    a.pair_res = E.pair_res;
+    a.stages = stages32 & STAGE_PAIRS;
+    if (e == cudaSuccess) e = run_pipeline<float>(g, a, s);
+    // 5. the guard: breached pairs form stage 2 of the list
+    p->prof.begin("check_pairs", s);
+    if (e == cudaSuccess)
+        e = launch_check_pairs(E.pair_res, g.KA, g.KB, E.cap, E.plist, E.hdr, E.ov_slot, E.needA, E.needB, p->st, s);
+    p->prof.end(s);
+    // 6. second precision for them, 7. the FP32 row pass again (only after a breach)
+    if (e == cudaSuccess)
+        e = with_tier2(p, [&](auto& w) { return tier2_stage(p, w, g, A, MA, B, MB, E.hdr + 1, s); });
+    a.stages = STAGE_ROWS;
+    a.conditional = 1;
+    if (e == cudaSuccess) e = run_pipeline<float>(g, a, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    p->prof.begin("finalize", s);
+    e = launch_finalize(p->st, 2, 2, s);
+    if (e == cudaSuccess) e = launch_merge_status(p->st, p->st_total, 2, s);
+    p->prof.end(s);
+    return from_cuda(e);
+}
+
 // One full map into (mi, n, counts); its status in p->st (reset here) is folded
 // into p->st_total.  stages32 selects the FP32 stages (A's transforms may be
-// reused across calls); an FP64 pass always recomputes everything.
+// reused across calls); an FP64 or two-term pass always recomputes everything.
 cmif_status compute_map(cmif_plan p, const Geom& g, const int32_t* A, const uint8_t* MA, const int32_t* B,
                         const uint8_t* MB, double* mi, int32_t* n, int32_t* counts, cudaStream_t s,
                         unsigned stages32 = STAGE_ALL) {
-    cudaError_t e0 = cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s);
-    if (e0 != cudaSuccess) return from_cuda(e0);
-    if (p->prec == CMIF_FP32 || p->prec == CMIF_AUTO) {
+    if (p->prec == CMIF_AUTO) return compute_map_auto(p, g, A, MA, B, MB, mi, n, counts, s, stages32);
+    cudaError_t e = cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (p->prec == CMIF_FP32) {
         PipeArgs<float> a = p->w32.args;
         fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
         a.prof = p->prof.enabled ? &p->prof : nullptr;
         a.stages = stages32;
         a.prec_slot = 0;
         a.conditional = 0;
-        cudaError_t e = run_pipeline<float>(g, a, s);
-        if (e != cudaSuccess) return from_cuda(e);
+        e = run_pipeline<float>(g, a, s);
+    } else if (p->prec == CMIF_FP64) {
+        PipeArgs<double> a = p->w64.args;
+        fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
+        a.prof = p->prof.enabled ? &p->prof : nullptr;
+        a.stages = STAGE_ALL;
+        a.prec_slot = 1;
+        a.conditional = 0;
+        e = run_pipeline<double>(g, a, s);
+    } else {
+        PipeArgs<df32> a = p->ws32.args;
+        fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
+        a.prof = p->prof.enabled ? &p->prof : nullptr;
+        a.stages = STAGE_ALL;
+        a.prec_slot = 1;
+        a.conditional = 0;
+        e = run_pipeline<df32>(g, a, s);
     }
-    if (p->prec == CMIF_AUTO) {
-        cudaError_t e = launch_check_escalate(p->st, s);
-        if (e != cudaSuccess) return from_cuda(e);
-    }
-    // second tier: the plan's FP64 / split precision, or AUTO's re-run (gated on the device)
-    const cmif_precision second = (p->prec == CMIF_AUTO) ? p->tier2 : p->prec;
-    if (p->prec != CMIF_FP32) {
-        const int cond = (p->prec == CMIF_AUTO) ? 1 : 0;
-        cudaError_t e;
-        if (second == CMIF_FP64) {
-            PipeArgs<double> a = p->w64.args;
-            fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
-            a.prof = p->prof.enabled ? &p->prof : nullptr;
-            a.stages = STAGE_ALL;
-            a.prec_slot = 1;
-            a.conditional = cond;
-            e = run_pipeline<double>(g, a, s);
-        } else {
-            PipeArgs<df32> a = p->ws32.args;
-            fill_io(a, A, MA, B, MB, mi, n, counts, p->st, p);
-            a.prof = p->prof.enabled ? &p->prof : nullptr;
-            a.stages = STAGE_ALL;
-            a.prec_slot = 1;
-            a.conditional = cond;
-            e = run_pipeline<df32>(g, a, s);
-        }
-        if (e != cudaSuccess) return from_cuda(e);
-    }
+    if (e != cudaSuccess) return from_cuda(e);
     const int slot_default = (p->prec == CMIF_FP64 || p->prec == CMIF_SPLIT32) ? 1 : 0;
     p->prof.begin("finalize", s);
-    cudaError_t e = launch_finalize(p->st, 1, slot_default, s);
+    e = launch_finalize(p->st, slot_default, slot_default, s);
     if (e == cudaSuccess) e = launch_merge_status(p->st, p->st_total, slot_default, s);
     p->prof.end(s);
     return from_cuda(e);
@@ -350,6 +456,28 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
         st = choose_rows<df32>(p, p->ws32);
     }
     if (st != CMIF_OK) return st;
+    if (prec == CMIF_AUTO) {
+        // per-pair precision: the second precision holds the products of one chunk
+        // of listed pairs at a time (a few GB at most), and the exact counts of at
+        // most `cap` listed pairs
+        const int npairs = K_A * K_B;
+        const size_t per_pair = (size_t)g.R * g.Qs * (p->tier2 == CMIF_FP64 ? sizeof(cpx<double>) : sizeof(cpx<df32>));
+        const size_t budget = 4ull << 30;
+        p->esc.chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)npairs, budget / per_pair));
+        p->esc.cap = std::min(npairs, 128);
+        if (p->tier2 == CMIF_FP64) p->w64.ypairs = p->esc.chunk;
+        else p->ws32.ypairs = p->esc.chunk;
+        // the predicate: an FFT correlation of two 0/1 planes errs by about
+        // kappa u log2(PQ) sqrt(|X_a| |Y_b|) (u = 2^-24); kappa = 0.25 bounds the
+        // residuals measured at 256^2 and 1024^2 with balanced labels (1024^2, K = 16:
+        // 0.0195 at |X| ~ 2^16, where the model gives 0.021); pairs whose estimate
+        // reaches half the 0.25 guard go to the second precision up front
+        const double logpq = std::log2((double)g.P * (double)g.Q * (double)std::max(D_A, D_B));
+        p->pred_scale = 0.25 * std::ldexp(1.0, -24) * logpq;
+        const char* pe = std::getenv("CMIF_AUTO_PREDICATE");  // "0": off; "all": every pair (diagnostics)
+        p->pred_thr = (pe && std::strcmp(pe, "0") == 0) ? HUGE_VAL
+                    : (pe && std::strcmp(pe, "all") == 0) ? 0.0 : 0.5 * (double)kResidualGuard;
+    }
     const int nmi = (flags & CMIF_FLAG_NMI) ? 1 : 0;
     p->w32.args.nmi = nmi;
     p->w64.args.nmi = nmi;
@@ -379,8 +507,38 @@ size_t small_bytes_of(const cmif_plan p) {
 }
 
 // Device bytes of everything the plan uses: small buffers + one workspace per precision.
+// Device bytes of the per-pair precision buffers (CMIF_AUTO plans).
+size_t esc_bytes(const cmif_plan p) {
+    if (p->prec != CMIF_AUTO) return 0;
+    const Geom& g = p->g;
+    const size_t np = (size_t)g.KA * g.KB;
+    size_t off = 0;
+    off = align_up(off + g.KA * sizeof(int), 256) + align_up(g.KB * sizeof(int), 256);
+    off += align_up(g.KA, 256) + align_up(g.KB, 256);
+    off += align_up(np * sizeof(int), 256) + 256 + align_up(np * sizeof(int), 256) + align_up(np * sizeof(unsigned), 256);
+    off += align_up((size_t)p->esc.cap * g.R * g.Q * sizeof(int32_t), 256);
+    return off;
+}
+
+void esc_carve(cmif_plan p, char* base) {
+    const Geom& g = p->g;
+    const size_t np = (size_t)g.KA * g.KB;
+    size_t off = 0;
+    Escal& E = p->esc;
+    E.popA = (int*)(base + off); off += align_up(g.KA * sizeof(int), 256);
+    E.popB = (int*)(base + off); off += align_up(g.KB * sizeof(int), 256);
+    E.needA = (unsigned char*)(base + off); off += align_up(g.KA, 256);
+    E.needB = (unsigned char*)(base + off); off += align_up(g.KB, 256);
+    E.plist = (int*)(base + off); off += align_up(np * sizeof(int), 256);
+    E.hdr = (int*)(base + off); off += 256;
+    E.ov_slot = (int*)(base + off); off += align_up(np * sizeof(int), 256);
+    E.pair_res = (unsigned*)(base + off); off += align_up(np * sizeof(unsigned), 256);
+    E.ov = (int32_t*)(base + off); off += align_up((size_t)E.cap * g.R * g.Q * sizeof(int32_t), 256);
+    E.bytes = off;
+}
+
 size_t plan_bytes(cmif_plan p) {
-    size_t b = small_bytes_of(p);
+    size_t b = small_bytes_of(p) + esc_bytes(p);
     if (p->has32) b += workspace_bytes<float>(p->g, p->w32);
     if (p->has64) b += workspace_bytes<double>(p->g, p->w64);
     if (p->ws32.rows_grid > 0) b += workspace_bytes<df32>(p->g, p->ws32);
@@ -403,6 +561,7 @@ cmif_status plan_carve(cmif_plan p, char* base) {
     if (p->has32) { carve_workspace<float>(g, p->w32, base + off); off += workspace_bytes<float>(g, p->w32); }
     if (p->has64) { carve_workspace<double>(g, p->w64, base + off); off += workspace_bytes<double>(g, p->w64); }
     if (p->ws32.rows_grid > 0) { carve_workspace<df32>(g, p->ws32, base + off); off += workspace_bytes<df32>(g, p->ws32); }
+    if (p->prec == CMIF_AUTO) { esc_carve(p, base + off); off += p->esc.bytes; }
     p->w32.bytes = p->has32 ? workspace_bytes<float>(g, p->w32) : 0;
     p->w64.bytes = p->has64 ? workspace_bytes<double>(g, p->w64) : 0;
     p->ws32.bytes = p->ws32.rows_grid > 0 ? workspace_bytes<df32>(g, p->ws32) : 0;
@@ -703,11 +862,33 @@ cmif_status cmif_get_status(cmif_plan plan, cmif_status* device_side, double* ma
                                                       : CMIF_OK;
     }
     if (max_residual) {
-        float f;
-        std::memcpy(&f, &h.res_bits[0], sizeof(f));
-        *max_residual = f;
+        float f0, f1;
+        std::memcpy(&f0, &h.res_bits[0], sizeof(f0));
+        std::memcpy(&f1, &h.res_bits[1], sizeof(f1));
+        *max_residual = plan->prec == CMIF_AUTO ? std::max(f0, f1) : f0;
     }
-    if (escalations) *escalations = h.escalations;
+    if (escalations) *escalations = h.escalations + h.predicted;
+    return CMIF_OK;
+}
+
+cmif_status cmif_get_precision_report(cmif_plan plan, int* pairs_predicted, int* pairs_escalated,
+                                      double* residual_fp32, double* residual_second) {
+    if (!plan) return CMIF_ERR_INVALID_ARG;
+    DeviceGuard dg(plan->device);
+    DevStatus h{};
+    cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, plan->st_total, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return from_cuda(e);
+    float f0, f1;
+    std::memcpy(&f0, &h.res_bits[0], sizeof(f0));
+    std::memcpy(&f1, &h.res_bits[1], sizeof(f1));
+    if (pairs_predicted) *pairs_predicted = h.predicted;
+    if (pairs_escalated) *pairs_escalated = h.escalations;
+    // AUTO keeps the FP32 pairs' and the second-precision pairs' residuals apart;
+    // other plans have one authoritative residual
+    if (residual_fp32) *residual_fp32 = (plan->prec == CMIF_AUTO || plan->prec == CMIF_FP32) ? (double)f0 : 0.0;
+    if (residual_second)
+        *residual_second = plan->prec == CMIF_AUTO ? (double)f1 : (plan->prec == CMIF_FP32 ? 0.0 : (double)f0);
     return CMIF_OK;
 }
 
@@ -879,7 +1060,7 @@ cmif_status cmif_compute_batch(cmif_batch batch, cmif_peak* results_dev, int32_t
                 e = launch_status_code(p->st_total, status_dev + i, cs);
                 if (e != cudaSuccess) return from_cuda(e);
             }
-            e = launch_merge_status(p->st_total, batch->total, 0, cs);
+            e = launch_merge_status(p->st_total, batch->total, p->prec == CMIF_AUTO ? 2 : 0, cs);
             if (e != cudaSuccess) return from_cuda(e);
         }
         return CMIF_OK;
@@ -899,11 +1080,12 @@ cmif_status cmif_batch_get_status(cmif_batch batch, cmif_status* device_side, do
                      : (h.flags & STATUS_PRECISION)   ? CMIF_ERR_PRECISION
                                                       : CMIF_OK;
     if (max_residual) {
-        float f;
-        std::memcpy(&f, &h.res_bits[0], sizeof(f));
-        *max_residual = f;
+        float f0, f1;
+        std::memcpy(&f0, &h.res_bits[0], sizeof(f0));
+        std::memcpy(&f1, &h.res_bits[1], sizeof(f1));
+        *max_residual = std::max(f0, f1);  // res_bits[1] is 0 unless the pairs ran with per-pair precision
     }
-    if (escalations) *escalations = h.escalations;
+    if (escalations) *escalations = h.escalations + h.predicted;
     return CMIF_OK;
 }
 

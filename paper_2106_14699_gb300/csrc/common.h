@@ -9,8 +9,9 @@ struct DevStatus {
     unsigned flags;        // STATUS_* bits below
     unsigned res_bits[2];  // max |c - round(c)| seen, as float bits: [0] FP32 pass, [1] FP64 pass
     int max_n;             // max_chi N(chi) of the last map (for the gamma gate of Alg. 1)
-    int escalations;       // number of FP32 -> FP64 re-runs
-    int pad[3];
+    int escalations;       // CMIF_AUTO: label pairs re-run in the second precision after the FP32 guard breached
+    int predicted;         // CMIF_AUTO: label pairs the precision predicate sent to the second precision up front
+    int pad[2];
     unsigned long long max_nw_bits;  // weighted maps (SWMI): max N(chi) as double bits (N >= 0)
 };
 enum : unsigned {

@@ -396,7 +396,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
         npairs = min(lrange[1] - lbase, chunk_cap);
         if (npairs <= 0) return;  // uniform: nothing listed for this launch
     }
-    auto real_pair = [&](int e) { return plist ? __ldg(plist + lbase + e) : e; };
+    auto real_pair = [&](int e) { return plist ? ::__ldg(plist + lbase + e) : e; };
     const int nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb * Dz;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -776,6 +776,74 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
         atomic_max_float_pos(&st->res_bits[prec_slot], res_max);
         atomicMax(&st->max_n, row_max_n);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Exact counts of listed pairs in the second precision (per-pair escalation of
+// CMIF_AUTO): the inverse row transform (complex-to-real, length Q) of rows
+// [r0, r1) of the chunk's column-inverted products, rounded to the nearest
+// integers (Sec. 3.2).  The counts of list slot s = lrange[0] + chunk_off + e
+// (chunk pair e) go to ov[s][row][0 .. Q); the FP32 row kernels then take them
+// in place of their own.  The largest residual goes to st->res_bits[1].
+template <typename T, int Q>
+struct RowCntCfg {
+    static constexpr int L = Q / 2;
+    using G = TeamGeom<T, L>;
+    static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
+    static constexpr int NT = TEAM >= 128 ? 1 : 128 / TEAM;
+    static constexpr int THREADS = NT * TEAM;
+    static constexpr size_t SMEM = (size_t)NT * G::SCRATCH;
+};
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(RowCntCfg<T, Q>::THREADS)
+k_pair_rows_counts(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, const int* __restrict__ lrange, int chunk_off,
+                   int chunk_cap, int32_t* __restrict__ ov, DevStatus* __restrict__ st) {
+    using C = RowCntCfg<T, Q>;
+    constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT;
+    const int lbase = lrange[0] + chunk_off;
+    const int np = min(lrange[1] - lbase, chunk_cap);
+    if (np <= 0) return;  // uniform: nothing listed for this launch
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int team = threadIdx.x / C::TEAM, lt = threadIdx.x % C::TEAM, r = lt / M, j = lt % M;
+    unsigned char* region = smem_raw + (size_t)team * C::G::SCRATCH;
+    const int nrows = g.r1 - g.r0;
+    const long long ntask = (long long)np * nrows;
+    const cpx<T>* twq_c2r = tw.n[ilog2c(Q)];
+    float res = 0.f;
+    // a uniform trip count per block: every lane of a warp takes part in each transform's warp syncs
+    for (long long t0 = (long long)blockIdx.x * NT; t0 < ntask; t0 += (long long)gridDim.x * NT) {
+        const long long t = t0 + team;
+        const bool act = t < ntask;
+        const int e = act ? (int)(t / nrows) : 0, row = g.r0 + (act ? (int)(t % nrows) : 0);
+        const cpx<T>* yr = Y + ((size_t)e * g.R + row) * g.Qs;
+        // Hermitian split: z = IDFT_L(E + iO), z[m] = x[2m] + i x[2m+1]
+        auto load = [&](int k) -> cpx<T> {
+            if (!act) return {T(0), T(0)};
+            const cpx<T> yk = yr[k], ym = yr[L - k];
+            const cpx<T> ev = {yk.x + ym.x, yk.y - ym.y};
+            const cpx<T> d = {yk.x - ym.x, yk.y + ym.y};
+            const cpx<T> o = cmul(d, twl<+1>(twq_c2r, k));
+            return {ev.x - o.y, ev.y + o.x};
+        };
+        cpx<T> v[M];
+        team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)],
+                           tw.n[ilog2c(L)]);
+        if (act) {
+            int32_t* o = ov + ((size_t)(lbase + e) * g.R + row) * Q;
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const int mf = R * (j + M * k2) + r;
+                const cpx<T> z = v[brev(k2, M)];
+                const T cr = rint_t<T>(z.x), ci = rint_t<T>(z.y);
+                res = fmaxf(res, fmaxf((float)fabs(z.x - cr), (float)fabs(z.y - ci)));
+                *reinterpret_cast<int2*>(o + 2 * mf) = make_int2((int)(float)cr, (int)(float)ci);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) res = fmaxf(res, __shfl_xor_sync(0xffffffffu, res, off));
+    if ((threadIdx.x & 31) == 0) atomic_max_float_pos(&st->res_bits[1], res);
 }
 
 // ---------------------------------------------------------------------------

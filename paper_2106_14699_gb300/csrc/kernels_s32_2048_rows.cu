@@ -2,6 +2,7 @@
 #include "pipeline_impl.cuh"
 namespace cmif {
 template cudaError_t Sized<df32, 2048>::pair_rows(const Geom&, const PipeArgs<df32>&, cudaStream_t);
+template cudaError_t Sized<df32, 2048>::pair_rows_counts(const Geom&, const PipeArgs<df32>&, cudaStream_t);
 template size_t Sized<df32, 2048>::rows_smem(int, bool);
 template int Sized<df32, 2048>::rows_threads();
 template cudaError_t Sized<df32, 2048>::rows_max_blocks(int, bool, int*);

@@ -132,11 +132,15 @@ cudaError_t launch_warp_nn(const int32_t* B, const uint8_t* MB, int H, int W, do
 // Fold one map's device status into the call's running total.
 __global__ void k_merge_status(const DevStatus* __restrict__ m, DevStatus* __restrict__ tot, int slot_default) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        const bool esc = (m->flags & STATUS_ESCALATE) != 0;
-        const int slot = esc ? 1 : slot_default;
+        if (slot_default == 2) {  // per-pair precision: FP32 pairs and second-precision pairs kept apart
+            tot->res_bits[0] = max(tot->res_bits[0], m->res_bits[0]);
+            tot->res_bits[1] = max(tot->res_bits[1], m->res_bits[1]);
+        } else {
+            tot->res_bits[0] = max(tot->res_bits[0], m->res_bits[slot_default]);  // the authoritative pass
+        }
         tot->flags |= m->flags;
-        tot->res_bits[0] = max(tot->res_bits[0], m->res_bits[slot]);  // residual of the authoritative pass
         tot->escalations += m->escalations;
+        tot->predicted += m->predicted;
         tot->max_n = max(tot->max_n, m->max_n);
     }
 }
@@ -192,21 +196,13 @@ cudaError_t launch_status_code(const DevStatus* st, int32_t* out, cudaStream_t s
     return cudaGetLastError();
 }
 
-// AUTO: escalate to the FP64 pass when the FP32 residual reached the guard.
-__global__ void k_check_escalate(DevStatus* st) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        if (__uint_as_float(st->res_bits[0]) >= kResidualGuard) {
-            st->flags |= STATUS_ESCALATE;
-            st->escalations += 1;
-        }
-    }
-}
-
-// Final verdict on the authoritative precision's residual.
+// Final verdict on the authoritative precision's residual (slot 2: per-pair
+// precision, where both the FP32 pairs' and the second-precision pairs' count).
 __global__ void k_finalize(DevStatus* st, int slot_if_escalated, int slot_default) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const int slot = (st->flags & STATUS_ESCALATE) ? slot_if_escalated : slot_default;
-        if (__uint_as_float(st->res_bits[slot]) >= kResidualGuard) st->flags |= STATUS_PRECISION;
+        const unsigned r = slot == 2 ? max(st->res_bits[0], st->res_bits[1]) : st->res_bits[slot];
+        if (__uint_as_float(r) >= kResidualGuard) st->flags |= STATUS_PRECISION;
     }
 }
 
@@ -230,13 +226,136 @@ cudaError_t launch_peak_w(const double* mi, const double* nw, const Geom& g, con
     return launch_peak_t(mi, nw, g, st, gamma, parts, nparts, 0, peak_out, s);
 }
 
-cudaError_t launch_check_escalate(DevStatus* st, cudaStream_t s) {
-    k_check_escalate<<<1, 32, 0, s>>>(st);
+cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s) {
+    k_finalize<<<1, 32, 0, s>>>(st, slot_if_escalated, slot_default);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s) {
-    k_finalize<<<1, 32, 0, s>>>(st, slot_if_escalated, slot_default);
+// ---------------------------------------------------------------------------
+// Per-pair precision of CMIF_AUTO.  The rounding of Sec. 3.2 gives exact counts
+// only while every pre-rounding error stays under 0.5; the error of an FFT
+// correlation of two 0/1 planes grows like u log2(PQ) sqrt(|X_a| |Y_b|) (u the
+// unit roundoff, |X| the plane's pixel count), so pairs of large label areas
+// need the second precision first.
+
+// Ordered compaction of the flagged pairs of one block (1024 threads, <= 4096
+// pairs): slots first + 0, 1, ... in pair order, those below cap written to the
+// list (a pair beyond the cap keeps its FP32 counts); returns the number flagged.
+template <typename Flag>
+__device__ __forceinline__ int block_compact(Flag flag, int npairs, int first, int cap, int* __restrict__ plist,
+                                             int* __restrict__ ov_slot) {
+    __shared__ int s_cnt[1024];
+    constexpr int PER = 4;  // 1024 threads x 4 >= 4096 pairs
+    const int t = threadIdx.x;
+    bool f[PER];
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int p = t * PER + i;
+        f[i] = p < npairs && flag(p);
+        c += f[i];
+    }
+    s_cnt[t] = c;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan
+        const int v = t >= off ? s_cnt[t - off] : 0;
+        __syncthreads();
+        s_cnt[t] += v;
+        __syncthreads();
+    }
+    int slot = first + s_cnt[t] - c;
+    const int total = s_cnt[1023];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int p = t * PER + i;
+        if (f[i]) {
+            if (slot < cap) {
+                plist[slot] = p;
+                ov_slot[p] = slot;
+            }
+            ++slot;
+        }
+    }
+    __syncthreads();
+    return total;
+}
+
+// The predicate: a pair goes to the second precision up front when
+// scale * sqrt(|X_a| |Y_b|) >= thr (scale = kappa u log2(PQ), thr below the guard).
+// Also resets the list, the slots, the per-pair residuals and the plane masks.
+__global__ void __launch_bounds__(1024) k_select_pairs(const int* __restrict__ popA, const int* __restrict__ popB,
+                                                      int KA, int KB, double scale, double thr, int cap,
+                                                      int* __restrict__ plist, int* __restrict__ hdr,
+                                                      int* __restrict__ ov_slot, unsigned* __restrict__ pair_res,
+                                                      unsigned char* __restrict__ needA,
+                                                      unsigned char* __restrict__ needB, DevStatus* __restrict__ st) {
+    const int npairs = KA * KB;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) { ov_slot[p] = -1; pair_res[p] = 0u; }
+    for (int k = threadIdx.x; k < KA; k += blockDim.x) needA[k] = 0;
+    for (int k = threadIdx.x; k < KB; k += blockDim.x) needB[k] = 0;
+    __syncthreads();
+    auto flag = [&](int p) {
+        const double pa = popA[p / KB], pb = popB[p % KB];
+        return scale * sqrt(pa * pb) >= thr;
+    };
+    const int n = min(block_compact(flag, npairs, 0, cap, plist, ov_slot), cap);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        needA[plist[i] / KB] = 1;
+        needB[plist[i] % KB] = 1;
+    }
+    if (threadIdx.x == 0) {
+        hdr[0] = 0;
+        hdr[1] = n;
+        hdr[2] = n;
+        st->predicted += n;
+    }
+}
+
+// The guard after the FP32 pass: pairs not yet in the list whose residual reached
+// 0.25 are appended (stage 2); the planes they need that stage 1 did not transform
+// are marked; the re-run of the FP32 row pass is requested, with its residual and
+// max N started afresh.
+__global__ void __launch_bounds__(1024) k_check_pairs(const unsigned* __restrict__ pair_res, int KA, int KB, int cap,
+                                                     int* __restrict__ plist, int* __restrict__ hdr,
+                                                     int* __restrict__ ov_slot, unsigned char* __restrict__ needA,
+                                                     unsigned char* __restrict__ needB, DevStatus* __restrict__ st) {
+    const int npairs = KA * KB;
+    for (int k = threadIdx.x; k < KA; k += blockDim.x) if (needA[k] == 1) needA[k] = 2;  // done in stage 1
+    for (int k = threadIdx.x; k < KB; k += blockDim.x) if (needB[k] == 1) needB[k] = 2;
+    const int first = hdr[1];
+    __syncthreads();
+    auto flag = [&](int p) { return ov_slot[p] < 0 && __uint_as_float(pair_res[p]) >= kResidualGuard; };
+    const int n = min(block_compact(flag, npairs, first, cap, plist, ov_slot), cap - first);
+    for (int i = first + threadIdx.x; i < first + n; i += blockDim.x) {
+        const int a = plist[i] / KB, b = plist[i] % KB;
+        if (needA[a] == 0) needA[a] = 1;
+        if (needB[b] == 0) needB[b] = 1;
+    }
+    if (threadIdx.x == 0) {
+        hdr[2] = first + n;
+        if (n > 0) {
+            st->flags |= STATUS_ESCALATE;
+            st->escalations += n;
+            st->res_bits[0] = 0u;
+            st->max_n = 0;
+        }
+    }
+}
+
+cudaError_t launch_select_pairs(const int* popA, const int* popB, int KA, int KB, double scale, double thr, int cap,
+                                int* plist, int* hdr, int* ov_slot, unsigned* pair_res, unsigned char* needA,
+                                unsigned char* needB, DevStatus* st, cudaStream_t s) {
+    if (KA * KB > 4096 || cap < 1) return cudaErrorInvalidValue;
+    k_select_pairs<<<1, 1024, 0, s>>>(popA, popB, KA, KB, scale, thr, cap, plist, hdr, ov_slot, pair_res, needA,
+                                      needB, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_pairs(const unsigned* pair_res, int KA, int KB, int cap, int* plist, int* hdr,
+                               int* ov_slot, unsigned char* needA, unsigned char* needB, DevStatus* st,
+                               cudaStream_t s) {
+    if (KA * KB > 4096 || cap < 1) return cudaErrorInvalidValue;
+    k_check_pairs<<<1, 1024, 0, s>>>(pair_res, KA, KB, cap, plist, hdr, ov_slot, needA, needB, st);
     return cudaGetLastError();
 }
 

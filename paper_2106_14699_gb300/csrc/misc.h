@@ -21,7 +21,13 @@ cudaError_t launch_peak(const double* mi, const int32_t* n, const Geom& g, const
 // The same on a weighted map (real N, max N from the status word's max_nw_bits).
 cudaError_t launch_peak_w(const double* mi, const double* nw, const Geom& g, const DevStatus* st, double gamma,
                           PeakPart* parts, int nparts, void* peak_out, cudaStream_t s);
-cudaError_t launch_check_escalate(DevStatus* st, cudaStream_t s);
+// CMIF_AUTO per-pair precision: the predicate (list stage 1) and the guard check (stage 2).
+cudaError_t launch_select_pairs(const int* popA, const int* popB, int KA, int KB, double scale, double thr, int cap,
+                                int* plist, int* hdr, int* ov_slot, unsigned* pair_res, unsigned char* needA,
+                                unsigned char* needB, DevStatus* st, cudaStream_t s);
+cudaError_t launch_check_pairs(const unsigned* pair_res, int KA, int KB, int cap, int* plist, int* hdr,
+                               int* ov_slot, unsigned char* needA, unsigned char* needB, DevStatus* st,
+                               cudaStream_t s);
 cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s);
 cudaError_t launch_warp_nn(const int32_t* B, const uint8_t* MB, int H, int W, double theta, int32_t* Bo, uint8_t* Mo,
                            cudaStream_t s);

@@ -40,11 +40,13 @@ cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
             e = Sized<T, SZ>::fwd_cols(g, a, true, s);
         } if (e != cudaSuccess) return e);
     }
-    if (stg & STAGE_PAIRS) {
+    if (stg & STAGE_COLS) {
         CMIF_SIZE_SWITCH(g.P, {
             ProfScope ps(a.prof, f32 ? "pair_cols_f32" : split ? "pair_cols_s32" : "pair_cols_f64", s);
             e = Sized<T, SZ>::pair_cols(g, a, s);
         } if (e != cudaSuccess) return e);
+    }
+    if (stg & STAGE_ROWS) {
         if (a.weighted) {
             CMIF_SIZE_SWITCH(g.Q, {
                 ProfScope ps(a.prof, "pair_rows_weighted_f64", s);
@@ -59,6 +61,23 @@ cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     }
     return cudaSuccess;
 }
+
+template <typename T>
+cudaError_t run_pair_counts(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    constexpr bool split = std::is_same<T, df32>::value;
+    CMIF_SIZE_SWITCH(g.P, {
+        ProfScope ps(a.prof, split ? "pair_cols_list_s32" : "pair_cols_list_f64", s);
+        e = Sized<T, SZ>::pair_cols(g, a, s);
+    } if (e != cudaSuccess) return e);
+    CMIF_SIZE_SWITCH(g.Q, {
+        ProfScope ps(a.prof, split ? "pair_counts_s32" : "pair_counts_f64", s);
+        e = Sized<T, SZ>::pair_rows_counts(g, a, s);
+    } if (e != cudaSuccess) return e);
+    return cudaSuccess;
+}
+template cudaError_t run_pair_counts<double>(const Geom&, const PipeArgs<double>&, cudaStream_t);
+template cudaError_t run_pair_counts<df32>(const Geom&, const PipeArgs<df32>&, cudaStream_t);
 
 template <typename T>
 size_t rows_smem_bytes(int Q, int KB, bool cb_smem) {

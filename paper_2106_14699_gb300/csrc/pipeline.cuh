@@ -56,10 +56,12 @@ struct PipeArgs {
 };
 
 enum : unsigned {
-    STAGE_FWD_A = 1u,  // level-set transforms of A
-    STAGE_FWD_B = 2u,  // level-set transforms of B
-    STAGE_PAIRS = 4u,  // pair product, inverse transforms, epilogue
-    STAGE_ALL = 7u,
+    STAGE_FWD_A = 1u,   // level-set transforms of A
+    STAGE_FWD_B = 2u,   // level-set transforms of B
+    STAGE_COLS = 4u,    // pair product and inverse column transforms
+    STAGE_ROWS = 8u,    // inverse row transforms and the epilogue
+    STAGE_PAIRS = 12u,  // both pair stages
+    STAGE_ALL = 15u,
 };
 
 // The transform sizes the kernels are compiled for (P, Q = 16 .. 4096).
@@ -87,6 +89,7 @@ struct Sized {
     static cudaError_t fwd_cols(const Geom& g, const PipeArgs<T>& a, bool b_side, cudaStream_t s);  // P = SZ
     static cudaError_t pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);              // P = SZ
     static cudaError_t pair_rows(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);              // Q = SZ
+    static cudaError_t pair_rows_counts(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);       // Q = SZ, list mode
     static size_t rows_smem(int KB, bool cb_smem);
     static int rows_threads();
     static cudaError_t rows_max_blocks(int KB, bool cb_smem, int* out);
@@ -99,6 +102,10 @@ struct Sized {
 
 template <typename T>
 cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);
+// List mode of the second precision: pair products and inverse column transforms of
+// the chunk's listed pairs (into a.Y), then their exact counts (into a.ov).
+template <typename T>
+cudaError_t run_pair_counts(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);
 
 // Per-precision facts the host needs at plan time.
 template <typename T>

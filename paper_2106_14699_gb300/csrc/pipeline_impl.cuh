@@ -4,6 +4,7 @@
 #pragma once
 #include "pipeline.cuh"
 #include "rows_tm.cuh"
+#include <algorithm>
 #include <type_traits>
 
 namespace cmif {
@@ -77,12 +78,13 @@ static cudaError_t launch_pair_rows_v(const Geom& g, const PipeArgs<T>& a, cudaS
     using C = RowCfg<T, Q>;
     if constexpr (sizeof(T) == 4 && (Q == 1024 || Q == 2048)) {
         if (a.tm_cols > 0 && !a.counts) {  // debug count maps: the generic kernel below
-            auto kern = k_pair_rows_tm<Q, NMI>;
+            const bool ext = a.ov_slot || a.pair_res || a.conditional || a.wait_polls > 0 || a.withhold_row >= 0;
+            auto kern = ext ? k_pair_rows_tm<Q, NMI, true> : k_pair_rows_tm<Q, NMI, false>;
             cudaError_t e = ensure_smem(kern, RowTmCfg<Q>::SMEM);
             if (e != cudaSuccess) return e;
             kern<<<a.rows_grid, RowTmCfg<Q>::THREADS, RowTmCfg<Q>::SMEM, s>>>(
                 a.Y, g, a.tw, a.mi, a.n, a.st, a.tm_cols, a.wait_polls > 0 ? a.wait_polls : kDefaultWaitPolls,
-                a.withhold_row);
+                a.withhold_row, a.conditional, a.ov, a.ov_slot, a.pair_res);
             return cudaGetLastError();
         }
     }
@@ -92,13 +94,13 @@ static cudaError_t launch_pair_rows_v(const Geom& g, const PipeArgs<T>& a, cudaS
         cudaError_t e = ensure_smem(kern, smem);
         if (e != cudaSuccess) return e;
         kern<<<a.rows_grid, C::THREADS, smem, s>>>(a.Y, g, a.tw, a.cb_global, a.mi, a.n, a.counts, a.st,
-                                                   a.prec_slot, a.conditional);
+                                                   a.prec_slot, a.conditional, a.ov, a.ov_slot, a.pair_res);
     } else if constexpr (Q > 512) {  // Q <= 512: K_B (<= 64) x Q floats always fit in shared memory
         auto kern = k_pair_rows<T, Q, false, NMI>;
         cudaError_t e = ensure_smem(kern, smem);
         if (e != cudaSuccess) return e;
         kern<<<a.rows_grid, C::THREADS, smem, s>>>(a.Y, g, a.tw, a.cb_global, a.mi, a.n, a.counts, a.st,
-                                                   a.prec_slot, a.conditional);
+                                                   a.prec_slot, a.conditional, a.ov, a.ov_slot, a.pair_res);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -140,6 +142,19 @@ cudaError_t Sized<T, SZ>::pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
 template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::pair_rows(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     return launch_pair_rows<T, SZ>(g, a, s);
+}
+
+template <typename T, int SZ>
+cudaError_t Sized<T, SZ>::pair_rows_counts(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
+    using C = RowCntCfg<T, SZ>;
+    auto kern = k_pair_rows_counts<T, SZ>;
+    cudaError_t e = ensure_smem(kern, C::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long tasks = (long long)a.chunk_cap * (g.r1 - g.r0);
+    const long long blocks = std::min<long long>((tasks + C::NT - 1) / C::NT, 8LL * (a.num_sms > 0 ? a.num_sms : 152));
+    kern<<<(int)std::max<long long>(1, blocks), C::THREADS, C::SMEM, s>>>(a.Y, g, a.tw, a.lrange, a.chunk_off,
+                                                                          a.chunk_cap, a.ov, a.st);
+    return cudaGetLastError();
 }
 
 template <typename T, int SZ>
@@ -218,9 +233,9 @@ int Sized<T, SZ>::tm_cols(int KB) {
 template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::tm_max_blocks(int* out) {
     if constexpr (sizeof(T) == 4 && (SZ == 1024 || SZ == 2048)) {
-        cudaError_t e = ensure_smem(k_pair_rows_tm<SZ, false>, RowTmCfg<SZ>::SMEM);
+        cudaError_t e = ensure_smem(k_pair_rows_tm<SZ, false, false>, RowTmCfg<SZ>::SMEM);
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pair_rows_tm<SZ, false>, RowTmCfg<SZ>::THREADS,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pair_rows_tm<SZ, false, false>, RowTmCfg<SZ>::THREADS,
                                                              RowTmCfg<SZ>::SMEM);
     } else {
         *out = 0;

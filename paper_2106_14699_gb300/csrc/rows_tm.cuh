@@ -144,15 +144,28 @@ __host__ __device__ constexpr int tm_alloc_cols(int need) {
     return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 
-template <int Q, bool NMI>
+// EXT = false is the plain FP32 kernel; EXT = true adds the per-pair precision of
+// CMIF_AUTO (conditional re-run, exact counts of listed pairs, per-pair residuals)
+// and the diagnostics of the bounded waits (poll limit, withheld copy).  The two
+// are separate instantiations because the plain kernel sits at the register limit.
+template <int Q, bool NMI, bool EXT>
 __global__ void __launch_bounds__(RowTmCfg<Q>::THREADS, 1)
 k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* __restrict__ mi_map,
                int32_t* __restrict__ n_map, DevStatus* __restrict__ st,
-               int tm_cols, int wait_polls, int withhold_row) {
+               int tm_cols, int wait_polls, int withhold_row, int conditional, const int32_t* __restrict__ ov,
+               const int* __restrict__ ov_slot, unsigned* __restrict__ pair_res) {
     // wait_polls: poll limit of the bounded waits.  withhold_row >= 0 (diagnostics
     // only): the bulk copy of that output row's first pair is never issued, so the
-    // wait for it runs out and the kernel takes its timeout path.
+    // wait for it runs out and the kernel takes its timeout path.  conditional: run
+    // only when the status word asks for the re-run.  ov, ov_slot, pair_res: the
+    // exact counts of second-precision pairs and the per-pair residuals, as in
+    // k_pair_rows.
     using C = RowTmCfg<Q>;
+    if (EXT && conditional && !(st->flags & STATUS_ESCALATE)) return;  // uniform, before any set-up
+    if (!EXT) {
+        wait_polls = kDefaultWaitPolls;
+        withhold_row = -1;
+    }
     constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, BT = C::THREADS, QH = C::QH;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, team = tid >> 5, lane = tid & 31, r = lane / M, j = lane % M;
@@ -186,7 +199,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     uint32_t phase = 0;
     bool pending = false;  // a copy issued for this team and not yet waited for
     auto issue = [&](int row_i, int pair_i) {
-        if (row_i == withhold_row && pair_i == 0) return;  // diagnostics: leave this wait without its copy
+        if (EXT && row_i == withhold_row && pair_i == 0) return;  // diagnostics: leave this wait without its copy
         if (lane == 0) {
             fence_proxy_async_smem();
             const cpx<float>* src = Y + ((size_t)pair_i * Rout + row_i) * Qs;
@@ -252,6 +265,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 if (npair >= npairs) { nrow = row + gridDim.x; npair = team; }
                 if (nrow < g.r1) issue(nrow, npair);
             }
+            float rp = 0.f;
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 // nearest integers (the 1.5 * 2^23 shift, packed) and the residual
@@ -259,9 +273,16 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 const float2 c = __fadd2_rn(__fadd2_rn(x, make_float2(12582912.0f, 12582912.0f)),
                                             make_float2(-12582912.0f, -12582912.0f));
                 const float2 dv = __ffma2_rn(c, make_float2(-1.f, -1.f), x);
-                res_max = fmaxf(res_max, fmaxf(fabsf(dv.x), fabsf(dv.y)));
+                rp = fmaxf(rp, fmaxf(fabsf(dv.x), fabsf(dv.y)));
                 v[k].x = c.x;
                 v[k].y = c.y;
+            }
+            const int ovs = (EXT && act && ov_slot) ? ov_slot[pair] : -1;  // loaded after the transform: fewer live registers
+            if (ovs < 0) res_max = fmaxf(res_max, rp);
+            if (EXT && pair_res && act && ovs < 0) {  // the warp is this pair's team
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) rp = fmaxf(rp, __shfl_xor_sync(0xffffffffu, rp, off));
+                if (lane == 0) atomic_max_float_pos(&pair_res[pair], rp);
             }
             const int nt = min(NT, npairs - base);
             const int a0 = base / KB, b0 = base - a0 * KB;
@@ -271,10 +292,21 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 __syncthreads();
                 float2* ob = reinterpret_cast<float2*>(region);
 #pragma unroll
-                for (int k2 = hf * (M / 2); k2 < (hf + 1) * (M / 2); ++k2) {
-                    const int m = R * (j + M * k2) + r - hf * (L / 2);
-                    const cpx<float> z = v[brev(k2, M)];
-                    ob[m] = make_float2(z.x, z.y);
+                if (EXT && ovs >= 0) {  // exact counts of positions 2 mf, 2 mf + 1 from the second precision
+                    const int32_t* ovr = ov + ((size_t)ovs * Rout + row) * Q;
+#pragma unroll
+                    for (int k2 = hf * (M / 2); k2 < (hf + 1) * (M / 2); ++k2) {
+                        const int mf = R * (j + M * k2) + r;
+                        const int2 q = *reinterpret_cast<const int2*>(ovr + 2 * mf);
+                        ob[mf - hf * (L / 2)] = make_float2((float)q.x, (float)q.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int k2 = hf * (M / 2); k2 < (hf + 1) * (M / 2); ++k2) {
+                        const int m = R * (j + M * k2) + r - hf * (L / 2);
+                        const cpx<float> z = v[brev(k2, M)];
+                        ob[m] = make_float2(z.x, z.y);
+                    }
                 }
                 __syncthreads();
                 const uint32_t tcol = tbase + (uint32_t)(hf * KB * UH);

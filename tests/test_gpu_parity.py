@@ -188,28 +188,83 @@ def test_single1024_full_size_sampled(cm):
     assert (dy, dx) == tuple(cfg["shift"])
 
 
-@pytest.mark.parametrize("tier2", ["split", "fp64"])
-def test_auto_escalates_unbalanced_labels(cm, tier2, monkeypatch):
-    """A dominant label makes FP32 correlations of ~10^6 counts inexact; AUTO
-    must detect it on the device and re-run in the second tier (two-term FP32
-    by default, FP64 on request), which is exact."""
-    if tier2 == "fp64":
+def _timed(cm, plan, A, B, mi, n, reps=3):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.compute(A, None, B, None, mi, n, None, 0.5)
+    ev0.record()
+    for _ in range(reps):
+        plan.compute(A, None, B, None, mi, n, None, 0.5)
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+@pytest.mark.parametrize("mode", ["predicate", "guard", "guard-fp64"])
+def test_auto_per_pair_precision_unbalanced_labels(cm, mode, monkeypatch):
+    """A dominant label (98% of 1024^2 pixels) makes the FP32 correlation of the
+    pair (0, 0) inexact.  CMIF_AUTO computes that pair in the second precision:
+    chosen up front by the predicate, or, with the predicate off, after the FP32
+    guard breached (two-term FP32, or FP64 on request).  Only the listed pairs pay
+    for it: N exact and MI within tolerance at sampled shifts, and the AUTO map
+    costs the FP32 map plus well under the second-precision map it replaced (one
+    pair of four listed: about a quarter of it)."""
+    if mode != "predicate":
+        monkeypatch.setenv("CMIF_AUTO_PREDICATE", "0")
+    if mode == "guard-fp64":
         monkeypatch.setenv("CMIF_AUTO_TIER2", "fp64")
     rng = np.random.default_rng(21)
     H = 1024
     A = (rng.random((H, H)) < 0.02).astype(np.int32)
     B = (rng.random((H, H)) < 0.02).astype(np.int32)
-    g32 = run_gpu(cm, A, None, B, None, 2, 2, cm.FP32, counts=False)
-    ga = run_gpu(cm, A, None, B, None, 2, 2, cm.AUTO, counts=False)
-    plan_status = ga["status"]
+    dA, dB = _to(A), _to(B)
+    R = 2 * H - 1
+    mi = torch.empty((R, R), dtype=torch.float64, device="cuda:0")
+    n = torch.empty((R, R), dtype=torch.int32, device="cuda:0")
+    p32 = cm.Plan(H, H, H, H, 2, 2, cm.FP32)
+    pa = cm.Plan(H, H, H, H, 2, 2, cm.AUTO)
+    t32 = _timed(cm, p32, dA, dB, mi, n)
+    st32 = p32.status()
+    p2 = cm.Plan(H, H, H, H, 2, 2, cm.FP64 if mode == "guard-fp64" else cm.SPLIT32)
+    t2 = _timed(cm, p2, dA, dB, mi, n)
+    p2.close()
+    assert st32[0] == "PRECISION" and st32[1] >= 0.25, st32     # FP32 alone is not exact here
+    ta = _timed(cm, pa, dA, dB, mi, n)
+    st = pa.status()
+    pred, esc, r32, r2 = pa.precision_report()
+    print(f"[auto-{mode}] FP32 {t32:.2f} ms (residual {st32[1]:.3f}), whole map in the second precision "
+          f"{t2:.2f} ms, AUTO {ta:.2f} ms: {pred} predicted, "
+          f"{esc} escalated, residual FP32 pairs {r32:.3e}, second precision {r2:.3e}")
+    assert st[0] == "OK" and st[1] < 0.25, st
+    assert r32 < 0.25 and r2 < 0.25
+    if mode == "predicate":
+        assert pred >= 1 and esc == 0
+    else:
+        assert pred == 0 and esc >= 1
+    assert pred + esc < 4                                        # not every pair: the small labels stay FP32
+    pa.set_profiling(True)
+    pa.compute(dA, None, dB, None, mi, n, None, 0.5)
+    print(f"[auto-{mode}] launches: " + ", ".join(f"{k} {v:.3f}" for k, v in pa.stage_times()))
+    pa.set_profiling(False)
+    assert ta < t32 + 0.6 * t2, (ta, t32, t2)
     dys, dxs = _sample_shifts(rng, H, H, H, H, 64)
     ref = oracle.cmif_at(A, None, B, None, 2, 2, dys, dxs)
-    got = ga["mi"][dys + H - 1, dxs + H - 1]
-    if g32["status"][1] >= 0.25:
-        assert g32["status"][0] == "PRECISION"
-        assert plan_status[2] == 1 and plan_status[0] == "OK" and plan_status[1] < 0.25
-    assert float(np.abs(got - ref["mi"]).max()) <= MI_TOL
-    np.testing.assert_array_equal(ga["n"][dys + H - 1, dxs + H - 1], ref["n"])
+    got_mi, got_n = mi.cpu().numpy(), n.cpu().numpy()
+    np.testing.assert_array_equal(got_n[dys + H - 1, dxs + H - 1], ref["n"])
+    assert float(np.abs(got_mi[dys + H - 1, dxs + H - 1] - ref["mi"]).max()) <= MI_TOL
+    p32.close()
+    pa.close()
+
+
+@pytest.mark.parametrize("shape", RAGGED[2:], ids=lambda s: "x".join(map(str, s)))
+def test_auto_every_pair_listed_exact(cm, shape, monkeypatch):
+    """CMIF_AUTO with every pair sent to the second precision up front
+    (CMIF_AUTO_PREDICATE=all; pairs beyond the 128-slot list keep FP32): the FP32
+    row pass takes the listed pairs' counts from the second precision, and every
+    count (joint, marginals, N) still matches the oracle exactly."""
+    monkeypatch.setenv("CMIF_AUTO_PREDICATE", "all")
+    rng = np.random.default_rng(sum(shape) + 5)
+    A, MA, B, MB = _rand(rng, *shape)
+    check_exact(cm, A, MA, B, MB, shape[4], shape[5], cm.AUTO, gamma=0.4)
 
 
 def test_host_buffer_entry_point(cm):

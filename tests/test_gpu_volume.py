@@ -117,3 +117,19 @@ def test_volume_host_entry_auto_and_nmi(cm):
     assert np.all(got[zero] == 0.0)
     err = np.abs(got[~zero] - ref["nmi"][~zero])
     assert np.all(err <= 5e-6 / hab[~zero])
+
+
+def test_volume_auto_every_pair_listed(cm, monkeypatch):
+    """Volume plan with CMIF_AUTO and every pair sent to the second precision
+    (CMIF_AUTO_PREDICATE=all): the listed pairs' depth-summed products and exact
+    counts come from the two-term transforms; N and MI equal the oracle's."""
+    monkeypatch.setenv("CMIF_AUTO_PREDICATE", "all")
+    rng = np.random.default_rng(41)
+    A = rng.integers(0, 3, (4, 9, 10)).astype(np.int32)
+    B = rng.integers(0, 3, (3, 8, 11)).astype(np.int32)
+    MB = (rng.random(B.shape) > 0.2).astype(np.uint8)
+    mi, n, pk, st = _run(cm, A, None, B, MB, 3, cm.AUTO)
+    assert st[0] == "OK" and st[2] == 9, st       # all 3 x 3 pairs in the second precision
+    ref = oracle.cmif3(A, None, B, MB, 3, 3)
+    np.testing.assert_array_equal(n, ref["n"])
+    assert float(np.abs(mi - ref["mi"]).max()) <= MI_TOL
