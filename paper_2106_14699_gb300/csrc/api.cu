@@ -478,6 +478,8 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
         p->pred_thr = (pe && std::strcmp(pe, "0") == 0) ? HUGE_VAL
                     : (pe && std::strcmp(pe, "all") == 0) ? 0.0 : 0.5 * (double)kResidualGuard;
     }
+    const char* cm_env = std::getenv("CMIF_COL_M");  // column-team variant of the FP32 transforms
+    p->w32.args.col_m = (cm_env && std::strcmp(cm_env, "16") == 0) ? 16 : 0;
     const int nmi = (flags & CMIF_FLAG_NMI) ? 1 : 0;
     p->w32.args.nmi = nmi;
     p->w64.args.nmi = nmi;

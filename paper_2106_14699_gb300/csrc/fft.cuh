@@ -165,10 +165,20 @@ __host__ __device__ constexpr int grp_scratch_bytes() {
     return sizeof(T) == 4 ? (M * M + grp_pad<M>()) * 4 : M * M * (int)sizeof(cpx<T>);
 }
 
+// Shared memory of one team of R groups: the groups' scratch, or for R > 2 the
+// N complex values of the radix-R exchange if that is more.
+template <typename T, int M, int R>
+__host__ __device__ constexpr int team_scratch_bytes() {
+    return R > 2 && R * M * M * (int)sizeof(cpx<T>) > R * grp_scratch_bytes<T, M>()
+               ? R * M * M * (int)sizeof(cpx<T>) : R * grp_scratch_bytes<T, M>();
+}
+
 // Length N = R*M*M transform by a team of R groups x M lanes.
 //   load(n)  : x[n] for n in [0, N)
 //   r, j     : this lane's group and lane-in-group
-//   sm       : this group's scratch (grp_scratch_bytes<T, M>() bytes of shared memory)
+//   sm       : this group's scratch (grp_scratch_bytes<T, M>() bytes of shared memory);
+//              for R > 2 the team's groups' scratch must start at sm - r * grp_scratch and
+//              span at least N complex values (team_scratch_bytes)
 //   twq      : Tw::sq for this M;  twn : Tw::n for N (used when R > 1)
 // Result: v[brev(k2, M)] = X[R*(j + M*k2) + r], k2 in [0, M).
 // Every lane of every warp taking part must call this (it uses __syncwarp).
@@ -233,24 +243,46 @@ template <int M, int R, int DIR, bool PACK = true, typename T, typename Load>
 __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
                                          const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
     constexpr int NQ = M * M;
+    if constexpr (R > 2) {
+        // Radix-R decimation in frequency with every input loaded once: lane (r, j)
+        // takes the points m = j + M (r PER + t), t < PER, forms the R-point DFT of
+        // x[m + s NQ], s < R, in registers, twiddles frequency q by w_N^{m q} and
+        // hands it to group q through the team's buffer (N complex values in front
+        // of the groups' scratch: sm - r * grp_scratch).  Block-wide barriers: every
+        // team of the block must call this together.
+        constexpr int PER = M / R;
+        static_assert(PER >= 1, "radix-R step needs R <= M");
+        cpx<T>* xs = reinterpret_cast<cpx<T>*>(reinterpret_cast<char*>(sm) - r * grp_scratch_bytes<T, M>());
+        __syncthreads();  // earlier users of the team's scratch are done
 #pragma unroll
-    for (int i = 0; i < M; ++i) {
-        const int m = j + M * i;
-        if constexpr (R == 1) {
-            v[i] = load(m);
-        } else {
-            // radix-R decimation in frequency: y_r[m] = w_N^{m r} sum_s x[m + s NQ] w_R^{s r}
-            cpx<T> acc = load(m);
+        for (int t = 0; t < PER; ++t) {
+            const int m = j + M * (r * PER + t);
+            cpx<T> u[R];
 #pragma unroll
-            for (int s = 1; s < R; ++s) {
-                cpx<T> x = load(m + s * NQ);
-                if constexpr (R == 2) {
-                    acc = (r & 1) ? acc - x : acc + x;
-                } else {
-                    acc = acc + cmul(x, twl<DIR>(twn, ((s * r) % R) * NQ));
-                }
+            for (int s2 = 0; s2 < R; ++s2) u[s2] = load(m + s2 * NQ);
+            dft_reg<R, DIR, PACK>(u);  // u[brev(q)] = sum_s x[m + s NQ] w_R^{s q}
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const cpx<T> y = u[brev(q, R)];
+                xs[q * NQ + m] = q ? cmul(y, twl<DIR>(twn, m * q)) : y;
             }
-            v[i] = (r == 0) ? acc : cmul(acc, twl<DIR>(twn, m * r));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = xs[r * NQ + j + M * i];
+        __syncthreads();  // the groups' transposes below reuse this buffer
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int m = j + M * i;
+            if constexpr (R == 1) {
+                v[i] = load(m);
+            } else {
+                // radix-2 decimation in frequency: y_r[m] = w_N^{m r} (x[m] + (-1)^r x[m + NQ])
+                const cpx<T> x0 = load(m), x1 = load(m + NQ);
+                const cpx<T> acc = (r & 1) ? x0 - x1 : x0 + x1;
+                v[i] = (r == 0) ? acc : cmul(acc, twl<DIR>(twn, m * r));
+            }
         }
     }
     team_fft_core<M, DIR, PACK>(v, j, sm, twq);

@@ -127,12 +127,14 @@ __device__ __forceinline__ int circ_to_out(int s, int n, int lo_count /*H_A or W
 
 // ---------------------------------------------------------------------------
 // Team geometry for a transform of length N in precision T.
-template <typename T, int N>
+// MMAX caps the lanes per group (and the values per lane): the default is the
+// register budget of T; a smaller one trades a radix-R step for more warps.
+template <typename T, int N, int MMAX = max_m<T>()>
 struct TeamGeom {
-    static constexpr int M = team_m(N, max_m<T>());
+    static constexpr int M = team_m(N, MMAX);
     static constexpr int R = N / (M * M);
     static constexpr int TEAM = R * M;                                        // lanes
-    static constexpr int SCRATCH = R * grp_scratch_bytes<T, M>();            // bytes of FFT scratch
+    static constexpr int SCRATCH = team_scratch_bytes<T, M, R>();            // bytes of FFT scratch
 };
 
 // ---------------------------------------------------------------------------
@@ -251,9 +253,9 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const 
 // block first stages its H x TPB input tile in shared memory with coalesced
 // 16-byte loads (column slots XOR-swizzled by row, so that the teams' column
 // reads are conflict-free), then each team transforms one column.
-template <typename T, int P>
+template <typename T, int P, int MMAX = max_m<T>()>
 struct ColCfg {
-    using G = TeamGeom<T, P>;
+    using G = TeamGeom<T, P, MMAX>;
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
     static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
     static constexpr int THREADS = TPB * TEAM;
@@ -263,14 +265,14 @@ struct ColCfg {
     static constexpr size_t smem(int H) { return SCR + (size_t)H * TPB * sizeof(cpx<T>); }
 };
 
-template <typename T, int P>
-__global__ void __launch_bounds__(ColCfg<T, P>::THREADS)
+template <typename T, int P, int MMAX>
+__global__ void __launch_bounds__(ColCfg<T, P, MMAX>::THREADS)
 k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cpx<T>* __restrict__ F, Tw<T> tw,
            const DevStatus* __restrict__ st, int conditional, T out_scale,
            const unsigned char* __restrict__ plane_need, int slices) {
     // plane_need (nullable): only the planes of labels whose entry is 1 are
     // transformed; plane p belongs to label p / slices (volumes: slices = depth).
-    using C = ColCfg<T, P>;
+    using C = ColCfg<T, P, MMAX>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     if (plane_need && plane_need[blockIdx.y / slices] != 1) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB;
@@ -344,12 +346,15 @@ __device__ __forceinline__ void stage_table(cpx<T>* dst, const cpx<T>* __restric
 // TPB columns per block, one team of R x M lanes per column; the block's shared
 // memory holds one buffer (the teams' exchange, then the P x TPB output tile,
 // with the transpose scratch aliased on it) and the twiddle tables.
-template <typename T, int P>
+template <typename T, int P, int MMAX = max_m<T>()>
 struct PairColsCfg {
-    using G = TeamGeom<T, P>;
+    using G = TeamGeom<T, P, MMAX>;
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM, NQ = M * M;
-    static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
+    // at least 256 threads, and at least 32 bytes of adjacent kx per tile row (whole sectors)
+    static constexpr int TPB0 = TEAM >= 256 ? 1 : 256 / TEAM;
+    static constexpr int TPB = TPB0 * (int)sizeof(cpx<T>) >= 32 ? TPB0 : 32 / (int)sizeof(cpx<T>);
     static constexpr int THREADS = TPB * TEAM;
+    static constexpr int PER = R > 2 ? M / R : 1;  // points per lane of the radix-R combine
     static constexpr int SWZ = TPB >= 16 ? 0 : (TPB == 8 ? 1 : (TPB == 4 ? 2 : 3));
     // one buffer per block: the teams' group-transform exchange, then the P x TPB output tile
     static constexpr size_t XBUF = (size_t)TPB * P * sizeof(cpx<T>);
@@ -357,7 +362,8 @@ struct PairColsCfg {
     static constexpr size_t MAIN = (XBUF > FFT ? XBUF : FFT);
     static constexpr int TW_N = R == 2 ? P / 2 : (R > 2 ? P : 0);  // combine twiddles W_P^k
     static constexpr size_t SMEM = MAIN + (size_t)(NQ + TW_N) * sizeof(cpx<T>);
-    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;
+    // FP32: two blocks per SM (M = 32 needs 128 registers a thread, so 256 threads)
+    static constexpr int MIN_BLOCKS = sizeof(T) == 4 && (M < 32 || THREADS <= 256) ? 2 : 1;
 };
 
 // Pair product + inverse column transform of length P = R*M*M.  Persistent
@@ -377,8 +383,8 @@ struct PairColsCfg {
 // the sum over the slices z of conj(F_a,z) F_b,z+dz (the 3-D correlation's
 // depth sum, taken before the inverse transform, which is linear), and the
 // output row of depth offset index dzo is dzo * R2 + (the image's output row).
-template <typename T, int P, bool VOL>
-__global__ void __launch_bounds__(PairColsCfg<T, P>::THREADS, PairColsCfg<T, P>::MIN_BLOCKS)
+template <typename T, int P, bool VOL, int MMAX>
+__global__ void __launch_bounds__(PairColsCfg<T, P, MMAX>::THREADS, PairColsCfg<T, P, MMAX>::MIN_BLOCKS)
 k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA, int KB, int Qh, int HA, int HB,
             int Rout, int Qs, int r0, int r1, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st,
             int conditional, int* __restrict__ work_ctr, int DA, int DB, int R2, const int* __restrict__ plist,
@@ -386,7 +392,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     // List mode (plist non-null): only the pairs plist[lrange[0] + chunk_off + e],
     // e < min(chunk_cap, lrange[1] - lrange[0] - chunk_off), are computed, pair e's
     // rows going to Y + e * Rout * Qs.
-    using C = PairColsCfg<T, P>;
+    using C = PairColsCfg<T, P, MMAX>;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     constexpr int M = C::M, R = C::R, TPB = C::TPB, NQ = C::NQ;
     const int Dz = VOL ? DA + DB - 1 : 1;
@@ -486,27 +492,43 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                 v[brev(k2, M)] = r == 0 ? v[brev(k2, M)] + tx[NQ + k] : tx[k] - v[brev(k2, M)];
             }
         } else if constexpr (R > 2) {
+            // X[k + q NQ] = sum_s w_R^{sq} (W^{sk} E_s[k]) (W = W_P, inverse direction): group
+            // s twiddles its own values, the team exchanges them through shared memory, and
+            // lane (r, j) forms all R outputs of the points k = j + M (r PER + t), t < PER,
+            // with an R-point DFT in registers (outputs kept as v[t R + q]).
             __syncthreads();  // every group is done with its transpose scratch (aliases xbuf)
-#pragma unroll
-            for (int k2 = 0; k2 < M; ++k2) tx[r * NQ + j + M * k2] = v[brev(k2, M)];
-            __syncthreads();
-            // X[k + r NQ] = sum_s W_P^{s (k + r NQ)} E_s[k]   (inverse direction)
 #pragma unroll
             for (int k2 = 0; k2 < M; ++k2) {
                 const int k = j + M * k2;
-                cpx<T> acc = tx[k];
+                const cpx<T> e = v[brev(k2, M)];
+                tx[r * NQ + k] = r ? cmul(e, twl<+1>(tw_n, r * k)) : e;
+            }
+            __syncthreads();
 #pragma unroll
-                for (int s2 = 1; s2 < R; ++s2)
-                    acc = acc + cmul(tx[s2 * NQ + k], twl<+1>(tw_n, (s2 * (k + r * NQ)) & (P - 1)));
-                v[brev(k2, M)] = acc;
+            for (int t = 0; t < C::PER; ++t) {
+                const int k = j + M * (r * C::PER + t);
+                cpx<T> u[R];
+#pragma unroll
+                for (int s2 = 0; s2 < R; ++s2) u[s2] = tx[s2 * NQ + k];
+                dft_reg<R, +1>(u);
+#pragma unroll
+                for (int q = 0; q < R; ++q) v[t * R + q] = u[brev(q, R)];
             }
         }
         __syncthreads();  // exchange reads done: the buffer becomes the tile
-        // row = r*NQ + j + M*k2; tile slot (row, team) swizzled by row
+        // tile slot (row, team) swizzled by row
 #pragma unroll
-        for (int k2 = 0; k2 < M; ++k2) {
-            const int row = r * NQ + j + M * k2;
-            xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = v[brev(k2, M)];
+        for (int i = 0; i < M; ++i) {
+            int row;
+            cpx<T> val;
+            if constexpr (R > 2) {
+                row = j + M * (r * C::PER + i / R) + (i % R) * NQ;
+                val = v[i];
+            } else {
+                row = r * NQ + j + M * i;
+                val = v[brev(i, M)];
+            }
+            xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = val;
         }
         __syncthreads();
         next = s_item;
@@ -575,9 +597,9 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     }
 }
 
-template <typename T, int P>
+template <typename T, int P, int MMAX = max_m<T>()>
 constexpr size_t pair_cols_smem() {
-    return PairColsCfg<T, P>::SMEM;
+    return PairColsCfg<T, P, MMAX>::SMEM;
 }
 
 // ---------------------------------------------------------------------------

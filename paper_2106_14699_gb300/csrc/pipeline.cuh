@@ -39,6 +39,9 @@ struct PipeArgs {
     bool cb_smem;     // B-marginal accumulators in shared memory
     Profiler* prof;   // optional launch timing (nullptr = off)
     int tm_cols;      // > 0: use the TMEM / TMA row kernel with this many TMEM columns
+    int col_m;        // column transforms' lanes per group: 0 = the default (32 for FP32), 16 = the
+                      // 16-lane variant (FP32, P >= 1024); the spectra layout follows it, so the
+                      // forward and pair column kernels of one map must use the same value
     int wait_polls;   // poll limit of the TMEM row kernel's bounded waits (0: the default)
     int withhold_row; // diagnostics: output row whose first bulk copy is withheld (-1: none)
     unsigned stages;  // STAGE_* bits: which parts of the sequence to launch

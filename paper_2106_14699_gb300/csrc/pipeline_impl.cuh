@@ -9,6 +9,10 @@
 
 namespace cmif {
 
+// Sizes with the 16-lane variant of the column transforms (FP32 only).
+template <typename T, int SZ>
+constexpr bool kHasColVariant = std::is_same<T, float>::value && SZ >= 1024;
+
 // Opt the kernel in to `bytes` of dynamic shared memory.  Without the attribute,
 // static plus dynamic shared memory must stay within 48 KB, so a kernel with a
 // little static memory (a work index, an abort flag) fails to launch just below
@@ -33,12 +37,12 @@ static cudaError_t launch_fwd_rows(const int32_t* X, const uint8_t* MX, const do
     return cudaGetLastError();
 }
 
-template <typename T, int P>
+template <typename T, int P, int MMAX>
 static cudaError_t launch_fwd_cols(const cpx<T>* T1, int H, int K, int Qh, int Qs, cpx<T>* F, const Tw<T>& tw,
                                    const DevStatus* st, int conditional, T out_scale, const unsigned char* need,
                                    int slices, cudaStream_t s) {
-    using C = ColCfg<T, P>;
-    auto kern = k_fwd_cols<T, P>;
+    using C = ColCfg<T, P, MMAX>;
+    auto kern = k_fwd_cols<T, P, MMAX>;
     cudaError_t e = ensure_smem(kern, C::smem(P));
     if (e != cudaSuccess) return e;
     dim3 grid((Qh + C::TPB - 1) / C::TPB, K);
@@ -46,11 +50,11 @@ static cudaError_t launch_fwd_cols(const cpx<T>* T1, int H, int K, int Qh, int Q
     return cudaGetLastError();
 }
 
-template <typename T, int P, bool VOL>
+template <typename T, int P, bool VOL, int MMAX>
 static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
-    using C = PairColsCfg<T, P>;
-    auto kern = k_pair_cols<T, P, VOL>;
-    const size_t smem = pair_cols_smem<T, P>();
+    using C = PairColsCfg<T, P, MMAX>;
+    auto kern = k_pair_cols<T, P, VOL, MMAX>;
+    const size_t smem = pair_cols_smem<T, P, MMAX>();
     cudaError_t e = ensure_smem(kern, smem);
     if (e != cudaSuccess) return e;
     // persistent grid: every resident block slot of the device, at most one per item
@@ -128,15 +132,28 @@ template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::fwd_cols(const Geom& g, const PipeArgs<T>& a, bool b_side, cudaStream_t s) {
     // B's spectra carry the 1/(P Q) of the unnormalised inverse transform (a power of two: exact)
     // volumes: K * D slice planes of H rows each (plane index label * D + z)
-    return b_side ? launch_fwd_cols<T, SZ>(a.T1B, g.HB, g.KB * g.DB, g.Qh, g.Qs, a.FB, a.tw, a.st, a.conditional,
-                                           T(1.0 / ((double)g.P * (double)g.Q)), a.needB, g.DB, s)
-                  : launch_fwd_cols<T, SZ>(a.T1A, g.HA, g.KA * g.DA, g.Qh, g.Qs, a.FA, a.tw, a.st, a.conditional,
-                                           T(1), a.needA, g.DA, s);
+    auto go = [&](auto mm) {
+        constexpr int MM = decltype(mm)::value;
+        return b_side ? launch_fwd_cols<T, SZ, MM>(a.T1B, g.HB, g.KB * g.DB, g.Qh, g.Qs, a.FB, a.tw, a.st,
+                                                   a.conditional, T(1.0 / ((double)g.P * (double)g.Q)), a.needB,
+                                                   g.DB, s)
+                      : launch_fwd_cols<T, SZ, MM>(a.T1A, g.HA, g.KA * g.DA, g.Qh, g.Qs, a.FA, a.tw, a.st,
+                                                   a.conditional, T(1), a.needA, g.DA, s);
+    };
+    if constexpr (kHasColVariant<T, SZ>) {
+        if (a.col_m == 16) return go(std::integral_constant<int, 16>{});
+    }
+    return go(std::integral_constant<int, max_m<T>()>{});
 }
 
 template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
-    return g.Dz > 1 ? launch_pair_cols<T, SZ, true>(g, a, s) : launch_pair_cols<T, SZ, false>(g, a, s);
+    if constexpr (kHasColVariant<T, SZ>) {
+        if (a.col_m == 16)
+            return g.Dz > 1 ? launch_pair_cols<T, SZ, true, 16>(g, a, s) : launch_pair_cols<T, SZ, false, 16>(g, a, s);
+    }
+    constexpr int MM = max_m<T>();
+    return g.Dz > 1 ? launch_pair_cols<T, SZ, true, MM>(g, a, s) : launch_pair_cols<T, SZ, false, MM>(g, a, s);
 }
 
 template <typename T, int SZ>
