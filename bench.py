@@ -484,7 +484,7 @@ def run_secondary(args):
         cfg = synth.make_workload("rotation-512x512-K16-64angles")
         H, W = cfg["A"].shape
         win = args.workload == "rotation-window"
-        plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True, window=win)
+        plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, graph=True, window=win, batch_angles=True, autotune=True)
         top = torch.empty(24 * 5, dtype=torch.uint8, device=dev)
         A, B = d(cfg["A"]), d(cfg["B"])
         step = lambda: plan.align_rotations(A, None, B, None, cfg["angles"], 0.5, 5, top)
@@ -509,7 +509,7 @@ def run_secondary(args):
         cfg = synth.make_workload("uneven-batch-128pairs")
         pairs = [dict(A=d(p["A"]), M_A=d(p["M_A"]), B=d(p["B"]), M_B=d(p["M_B"]), K_A=p["K_A"], K_B=p["K_B"],
                       angles=p["angles"], gamma=0.5) for p in cfg["pairs"]]
-        plan = cm.Batch(pairs, cm.FP32, graph=True)
+        plan = cm.Batch(pairs, cm.FP32, graph=True, batch_angles=True, autotune=True)
         res = torch.empty(24 * len(pairs), dtype=torch.uint8, device=dev)
         stat = torch.empty(len(pairs), dtype=torch.int32, device=dev)
         step = lambda: plan.run(res, stat)

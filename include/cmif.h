@@ -108,6 +108,13 @@ typedef enum { CMIF_FP32 = 0, CMIF_SPLIT32 = 1, CMIF_FP64 = 2, CMIF_AUTO = 3 } c
                                      argmax and the peaks then maximise NMI. */
 #define CMIF_FLAG_WEIGHTED 16u    /* the plan computes spatially weighted MI with cmif_compute_weighted (needs
                                      CMIF_FP64; not with CMIF_FLAG_NMI or CMIF_FLAG_DEBUG_COUNTS) */
+#define CMIF_FLAG_AUTOTUNE 32u    /* run cmif_plan_autotune at creation (cache file: the environment variable
+                                     CMIF_TUNE_CACHE, or none) */
+#define CMIF_FLAG_BATCH_ANGLES 64u /* FP32 image plans: cmif_align_rotations runs up to 64 angles per launch of
+                                     each stage (warp, B's transforms, pair products, row epilogue, peaks), as
+                                     many as 40% of the free device memory at creation holds (the environment
+                                     variable CMIF_ANGLE_BATCH caps it); the workspace grows accordingly.
+                                     Results equal the angle-by-angle ones.  Ignored by other plans. */
 
 /* One argmax record of Alg. 1: the displacement chi = (dy, dx) maximising
  * CMIF among shifts with N(chi) >= gamma * max N, for transform angle_idx
@@ -282,7 +289,9 @@ typedef struct {
 /* Validate the pairs (limits as cmif_plan_create_ex, 0 <= n_angles <= 4096),
  * copy the descriptors and allocate the shared workspace.  The device images
  * the descriptors point to must stay valid and unchanged for the batch's life.
- * prec as for plans; flags: 0 or any of CMIF_FLAG_GRAPH, CMIF_FLAG_WINDOW, CMIF_FLAG_NMI. */
+ * prec as for plans; flags: 0 or any of CMIF_FLAG_GRAPH, CMIF_FLAG_WINDOW, CMIF_FLAG_NMI,
+ * CMIF_FLAG_AUTOTUNE (each pair's size class timed once) and CMIF_FLAG_BATCH_ANGLES (each
+ * pair's angles as units of one launch per stage, as far as memory allows). */
 cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc* descs, cmif_precision prec,
                               unsigned flags);
 
@@ -348,6 +357,31 @@ cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, int K_A, in
                                  const uint8_t* M_A, const int32_t* B, const uint8_t* M_B, double* mi_map,
                                  int32_t* n_map, double gamma, cmif_peak* peak_dev, int32_t* status_dev,
                                  void* stream);
+
+/* Launch-shape choices of a plan's FP32 transforms, as cmif_plan_autotune made them. */
+typedef struct {
+    int col_lanes;            /* lanes per group of the column transforms: 32, or 16 (radix-R exchange, more warps) */
+    int tmem_rows;            /* 1: the Tensor-Memory row kernel, 0: the generic one */
+    int cols_blocks_per_sm;   /* persistent blocks per SM of the pair-column kernel (0: as many as fit) */
+    double ms_per_map;        /* the chosen candidate's median time for one map (0 when not timed here) */
+    int from_cache;           /* 0: timed now, 1: this process's cache, 2: the cache file */
+    int candidates;           /* candidates timed now */
+} cmif_tuning;
+
+/* Autotuner (not in the paper: the library's choice of FFT radix split and
+ * launch shapes for the frequency-domain method of Sec. 3.2).  Times every
+ * candidate launch shape of the plan's FP32 transforms on synthetic labels of
+ * the plan's sizes -- the column transforms with 32 lanes per group (radix-2
+ * split) or 16 (radix-R split with a register DFT and one exchange), the
+ * Tensor-Memory or the generic row kernel, one or as many pair-column blocks
+ * per SM as fit -- and keeps the fastest (median of three maps, CUDA events).
+ * Choices are cached per process and, when cache_path is non-NULL, appended to
+ * that JSON-lines file and read back by later processes, keyed on the
+ * transform sizes, label counts, depths, precision, SM count and device name.
+ * Results do not depend on the choice (the same counts and MI).  Synchronous;
+ * uses a temporary device buffer for the synthetic labels.  FP64 and two-term
+ * plans have nothing to choose (out reports zeros).  out may be NULL. */
+cmif_status cmif_plan_autotune(cmif_plan plan, const char* cache_path, cmif_tuning* out);
 
 /* Fixed-point scale of the epilogue's per-shift entropy sums (Eq. finalentropy):
  * units of 2^-CMIF_ENTROPY_FIX_BITS. */

@@ -25,6 +25,8 @@ FLAG_GRAPH = 2
 FLAG_WINDOW = 4
 FLAG_NMI = 8
 FLAG_WEIGHTED = 16
+FLAG_AUTOTUNE = 32
+FLAG_BATCH_ANGLES = 64
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "LABEL_RANGE", 3: "OOM", 4: "CUDA", 5: "PRECISION",
                 6: "TIMEOUT", 7: "NOT_IMPLEMENTED", 8: "UNSUPPORTED"}
 
@@ -42,6 +44,11 @@ class PairDesc(ctypes.Structure):
                 ("n_angles", ctypes.c_int), ("gamma", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("col_lanes", ctypes.c_int), ("tmem_rows", ctypes.c_int), ("cols_blocks_per_sm", ctypes.c_int),
+                ("ms_per_map", ctypes.c_double), ("from_cache", ctypes.c_int), ("candidates", ctypes.c_int)]
+
+
 class Peak(ctypes.Structure):
     _fields_ = [("angle_idx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dx", ctypes.c_int32),
                 ("n", ctypes.c_int32), ("mi", ctypes.c_double)]
@@ -52,7 +59,7 @@ EXPORTS = ["cmif_plan_create", "cmif_plan_create_ex", "cmif_plan_create_3d", "cm
            "cmif_plan_stage_times", "cmif_compute_noalloc", "cmif_rotate_nn", "cmif_align_rotations",
            "cmif_align_two_stage", "cmif_compute_weighted", "cmif_batch_create", "cmif_compute_batch", "cmif_batch_get_status",
            "cmif_batch_destroy", "cmif_entropy_terms", "cmif_plan_set_wait_test", "cmif_get_precision_report",
-           "cmif_status_string"]
+           "cmif_plan_autotune", "cmif_status_string"]
 
 _lib = None
 
@@ -87,6 +94,7 @@ def lib():
         L.cmif_batch_destroy.argtypes = [P]
         L.cmif_entropy_terms.argtypes = [I, I, P, P]
         L.cmif_plan_set_wait_test.argtypes = [P, I, I]
+        L.cmif_plan_autotune.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(Tuning)]
         L.cmif_get_precision_report.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D),
                                                 ctypes.POINTER(D)]
         L.cmif_status_string.argtypes = [I]
@@ -127,10 +135,11 @@ class Plan:
     """A CMIF plan for images H_A x W_A and H_B x W_B with K_A, K_B labels."""
 
     def __init__(self, H_A, W_A, H_B, W_B, K_A, K_B, precision=FP32, debug_counts=False, graph=False, window=False,
-                 nmi=False, weighted=False):
+                 nmi=False, weighted=False, autotune=False, batch_angles=False):
         self._h = ctypes.c_void_p()
         flags = (FLAG_DEBUG_COUNTS if debug_counts else 0) | (FLAG_GRAPH if graph else 0) | \
-            (FLAG_WINDOW if window else 0) | (FLAG_NMI if nmi else 0) | (FLAG_WEIGHTED if weighted else 0)
+            (FLAG_WINDOW if window else 0) | (FLAG_NMI if nmi else 0) | (FLAG_WEIGHTED if weighted else 0) | \
+            (FLAG_AUTOTUNE if autotune else 0) | (FLAG_BATCH_ANGLES if batch_angles else 0)
         _check(lib().cmif_plan_create_ex(ctypes.byref(self._h), H_A, W_A, H_B, W_B, K_A, K_B, precision, flags),
                "cmif_plan_create_ex")
         self.H_A, self.W_A, self.H_B, self.W_B, self.K_A, self.K_B = H_A, W_A, H_B, W_B, K_A, K_B
@@ -197,6 +206,13 @@ class Plan:
                                                ctypes.byref(r1)), "cmif_get_precision_report")
         return pp.value, pe.value, r0.value, r1.value
 
+    def autotune(self, cache_path=None):
+        """cmif_plan_autotune: time the launch-shape candidates, keep the fastest; returns the choice."""
+        t = Tuning()
+        _check(lib().cmif_plan_autotune(self._h, cache_path.encode() if cache_path else None, ctypes.byref(t)),
+               "cmif_plan_autotune")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
     def set_profiling(self, enable=True):
         _check(lib().cmif_plan_set_profiling(self._h, 1 if enable else 0), "cmif_plan_set_profiling")
 
@@ -247,7 +263,8 @@ class Batch:
     """cmif_batch over pairs given as dicts with device tensors A, M_A, B, M_B, K_A, K_B,
     host angle lists `angles` (radians) and `gamma`."""
 
-    def __init__(self, pairs, precision=FP32, graph=True, window=False, nmi=False):
+    def __init__(self, pairs, precision=FP32, graph=True, window=False, nmi=False, autotune=False,
+                 batch_angles=False):
         self._keep = []
         descs = (PairDesc * len(pairs))()
         for i, p in enumerate(pairs):
@@ -262,7 +279,8 @@ class Batch:
         self._h = ctypes.c_void_p()
         _check(lib().cmif_batch_create(ctypes.byref(self._h), len(pairs), ctypes.cast(descs, ctypes.c_void_p),
                                        precision, (FLAG_GRAPH if graph else 0) | (FLAG_WINDOW if window else 0) |
-                                       (FLAG_NMI if nmi else 0)),
+                                       (FLAG_NMI if nmi else 0) | (FLAG_AUTOTUNE if autotune else 0) |
+                                       (FLAG_BATCH_ANGLES if batch_angles else 0)),
                "cmif_batch_create")
         self.n = len(pairs)
 

@@ -4,7 +4,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "cmif.h"
@@ -26,6 +29,10 @@ struct Workspace {
     bool cb_smem = true;
     int rows_grid_w = 0;  // > 0: the plan computes weighted maps (FP64 workspace only)
     int ypairs = 0;       // pairs the Y buffer holds (0: all K_A * K_B; the second precision of AUTO: one chunk)
+    // row-kernel alternatives (FP32): the Tensor-Memory kernel and the generic one
+    int tm_cols_avail = 0;  // > 0: the TMEM kernel applies (its TMEM columns)
+    int grid_tm = 0;        // its persistent grid
+    int grid_gen = 0;       // the generic kernel's grid, when its B-marginals fit in shared memory (else 0)
 };
 
 // Per-pair precision of CMIF_AUTO: device buffers of the pair list and the exact
@@ -94,6 +101,12 @@ struct cmif_plan_s {
     // waits (0: default) and an output row whose first bulk copy is withheld (-1: none)
     int test_wait_polls = 0;
     int test_withhold_row = -1;
+    // Rotation angles per launch (CMIF_FLAG_BATCH_ANGLES, FP32 plans): up to ucap
+    // angles run as units of one launch per stage; gcap is the geometry the FP32
+    // workspace is sized for (ucap units; g itself when ucap = 1).
+    int ucap = 1;
+    Geom gcap{};
+    int* maxn_u = nullptr;    // [ucap] per-unit max N of the gamma gate
     // CMIF_AUTO: per-pair precision (predicate up front, guard after the FP32 pass)
     Escal esc;
     double pred_scale = 0.0;   // kappa u log2(PQ): the predicate is pred_scale sqrt(|X_a| |Y_b|) >= pred_thr
@@ -113,7 +126,7 @@ cmif_status from_cuda(cudaError_t e) {
 // else in global memory.  Fills tm_cols, cb_smem and rows_grid.
 template <typename T>
 cmif_status choose_rows(cmif_plan p, Workspace<T>& w) {
-    const Geom& g = p->g;
+    const Geom& g = p->gcap;  // the capacity geometry: the row grid serves every unit of a batched call
     int bps = 0;
     cudaError_t e = cudaSuccess;
     w.args.tm_cols = 0;
@@ -141,7 +154,29 @@ cmif_status choose_rows(cmif_plan p, Workspace<T>& w) {
     w.args.rows_grid = w.rows_grid;
     w.args.num_sms = p->num_sms;
     w.args.cb_smem = w.cb_smem;
+    if (w.args.tm_cols > 0) {  // the generic kernel as an alternative the autotuner may pick
+        w.tm_cols_avail = w.args.tm_cols;
+        w.grid_tm = w.rows_grid;
+        int bg = 0;
+        if (rows_smem_bytes<T>(g.Q, g.KB, true) <= 200 * 1024 &&
+            rows_max_blocks_per_sm<T>(g.Q, g.KB, true, &bg) == cudaSuccess && bg >= 1)
+            w.grid_gen = std::min(g.R, bg * p->num_sms);
+        cudaGetLastError();
+    }
     return CMIF_OK;
+}
+
+// Switch an FP32 workspace between the TMEM and the generic row kernel (both
+// prepared by choose_rows; the generic one only where its B-marginals fit in
+// shared memory, so the workspace needs no global slice for it).
+template <typename T>
+bool set_rows_kernel(Workspace<T>& w, bool tmem) {
+    if (tmem ? w.tm_cols_avail <= 0 : w.grid_gen <= 0) return false;
+    w.args.tm_cols = tmem ? w.tm_cols_avail : 0;
+    w.rows_grid = tmem ? w.grid_tm : w.grid_gen;
+    w.args.rows_grid = w.rows_grid;
+    if (!tmem) w.cb_smem = w.args.cb_smem = true;
+    return true;
 }
 
 // Device bytes of the transform workspace of precision T (after choose_rows).
@@ -401,7 +436,7 @@ cmif_status compute_map(cmif_plan p, const Geom& g, const int32_t* A, const uint
 // Validate sizes and flags, set the geometry, pick kernels; allocates nothing
 // (except the per-device twiddle tables on first use).
 cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B, cmif_precision prec,
-                      unsigned flags, int D_A = 1, int D_B = 1) {
+                      unsigned flags, int D_A = 1, int D_B = 1, int max_units = kMaxUnits) {
     if (H_A < 1 || W_A < 1 || H_B < 1 || W_B < 1 || K_A < 1 || K_B < 1 || K_A > 64 || K_B > 64)
         return CMIF_ERR_INVALID_ARG;
     if (D_A < 1 || D_B < 1 || D_A > 1024 || D_B > 1024) return CMIF_ERR_INVALID_ARG;
@@ -409,7 +444,8 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
         return CMIF_ERR_INVALID_ARG;
     const bool volume = D_A > 1 || D_B > 1;
     if (volume && (flags & (CMIF_FLAG_WINDOW | CMIF_FLAG_WEIGHTED))) return CMIF_ERR_UNSUPPORTED;
-    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI | CMIF_FLAG_WEIGHTED))
+    if (flags & ~(CMIF_FLAG_DEBUG_COUNTS | CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI | CMIF_FLAG_WEIGHTED |
+                  CMIF_FLAG_AUTOTUNE | CMIF_FLAG_BATCH_ANGLES))
         return CMIF_ERR_INVALID_ARG;
     // weighted maps: FP64 transforms (real counts, no rounding), MI only
     if ((flags & CMIF_FLAG_WEIGHTED) && (prec != CMIF_FP64 || (flags & (CMIF_FLAG_NMI | CMIF_FLAG_DEBUG_COUNTS))))
@@ -417,7 +453,7 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     if (prec != CMIF_FP32 && prec != CMIF_SPLIT32 && prec != CMIF_FP64 && prec != CMIF_AUTO) return CMIF_ERR_INVALID_ARG;
     Geom g{};
     g.HA = H_A; g.WA = W_A; g.HB = H_B; g.WB = W_B; g.KA = K_A; g.KB = K_B;
-    g.DA = D_A; g.DB = D_B; g.Dz = D_A + D_B - 1;
+    g.DA = D_A; g.DB = D_B; g.Dz = D_A + D_B - 1; g.units = 1;
     g.R2 = H_A + H_B - 1;
     g.R = g.Dz * g.R2;
     g.C = W_A + W_B - 1;
@@ -432,6 +468,24 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) return CMIF_ERR_CUDA;
     p->g = g;
+    p->gcap = g;
+    p->ucap = 1;
+    if ((flags & CMIF_FLAG_BATCH_ANGLES) && !volume && prec == CMIF_FP32) {
+        // as many angles per launch as 40% of the free device memory holds (at most 64)
+        const size_t per_unit = (size_t)K_B * H_B * g.Qs * 8 + (size_t)K_B * g.Qh * g.P * 8 +
+                                (size_t)K_A * K_B * g.R * g.Qs * 8 + (size_t)g.R * g.C * 12 + (size_t)H_B * W_B * 5;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return CMIF_ERR_CUDA;
+        long long u = (long long)(0.4 * (double)fr / (double)per_unit);
+        const char* ue = std::getenv("CMIF_ANGLE_BATCH");  // an upper bound on the units per launch
+        if (ue && std::atoi(ue) > 0) u = std::min<long long>(u, std::atoi(ue));
+        p->ucap = (int)std::max<long long>(1, std::min<long long>(u, std::min(max_units, kMaxUnits)));
+        if (p->ucap > 1) {
+            p->gcap.units = p->ucap;
+            p->gcap.DB = p->ucap;
+            p->gcap.R = p->ucap * g.R2;
+        }
+    }
     p->prec = prec;
     p->flags = flags;
     p->use_graph = (flags & CMIF_FLAG_GRAPH) != 0;
@@ -498,13 +552,15 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
 
 size_t small_bytes_of(const cmif_plan p) {
     const Geom& g = p->g;
+    const size_t u = (size_t)p->ucap;
     size_t off = align_up(sizeof(DevStatus), 256) * 2;
-    off = align_up(off + (size_t)p->nparts * sizeof(PeakPart), 256);
-    off = align_up(off + (size_t)g.R * g.C * sizeof(int32_t), 256);
-    off = align_up(off + (size_t)g.R * g.C * sizeof(double), 256);
-    off = align_up(off + (size_t)g.HB * g.WB * sizeof(int32_t), 256);
-    off = align_up(off + (size_t)g.HB * g.WB, 256);
+    off = align_up(off + u * p->nparts * sizeof(PeakPart), 256);
+    off = align_up(off + u * g.R * g.C * sizeof(int32_t), 256);
+    off = align_up(off + u * g.R * g.C * sizeof(double), 256);
+    off = align_up(off + u * g.HB * g.WB * sizeof(int32_t), 256);
+    off = align_up(off + u * g.HB * g.WB, 256);
     off = align_up(off + (size_t)(kMaxAngles + 2) * sizeof(PeakRec), 256);
+    off = align_up(off + u * sizeof(int), 256);
     return off;
 }
 
@@ -541,7 +597,7 @@ void esc_carve(cmif_plan p, char* base) {
 
 size_t plan_bytes(cmif_plan p) {
     size_t b = small_bytes_of(p) + esc_bytes(p);
-    if (p->has32) b += workspace_bytes<float>(p->g, p->w32);
+    if (p->has32) b += workspace_bytes<float>(p->gcap, p->w32);
     if (p->has64) b += workspace_bytes<double>(p->g, p->w64);
     if (p->ws32.rows_grid > 0) b += workspace_bytes<df32>(p->g, p->ws32);
     return b;
@@ -553,18 +609,23 @@ cmif_status plan_carve(cmif_plan p, char* base) {
     size_t off = 0;
     p->st = (DevStatus*)(base + off); off += align_up(sizeof(DevStatus), 256);
     p->st_total = (DevStatus*)(base + off); off += align_up(sizeof(DevStatus), 256);
-    p->parts = (PeakPart*)(base + off); off = align_up(off + (size_t)p->nparts * sizeof(PeakPart), 256);
-    p->nbuf = (int32_t*)(base + off); off = align_up(off + (size_t)g.R * g.C * sizeof(int32_t), 256);
-    p->mibuf = (double*)(base + off); off = align_up(off + (size_t)g.R * g.C * sizeof(double), 256);
-    p->wB = (int32_t*)(base + off); off = align_up(off + (size_t)g.HB * g.WB * sizeof(int32_t), 256);
-    p->wM = (uint8_t*)(base + off); off = align_up(off + (size_t)g.HB * g.WB, 256);
+    const size_t u = (size_t)p->ucap;
+    p->parts = (PeakPart*)(base + off); off = align_up(off + u * p->nparts * sizeof(PeakPart), 256);
+    p->nbuf = (int32_t*)(base + off); off = align_up(off + u * g.R * g.C * sizeof(int32_t), 256);
+    p->mibuf = (double*)(base + off); off = align_up(off + u * g.R * g.C * sizeof(double), 256);
+    p->wB = (int32_t*)(base + off); off = align_up(off + u * g.HB * g.WB * sizeof(int32_t), 256);
+    p->wM = (uint8_t*)(base + off); off = align_up(off + u * g.HB * g.WB, 256);
     p->peaks = base + off; off = align_up(off + (size_t)(kMaxAngles + 2) * sizeof(PeakRec), 256);
+    p->maxn_u = (int*)(base + off); off = align_up(off + u * sizeof(int), 256);
     p->small_bytes = off;
-    if (p->has32) { carve_workspace<float>(g, p->w32, base + off); off += workspace_bytes<float>(g, p->w32); }
+    if (p->has32) {
+        carve_workspace<float>(p->gcap, p->w32, base + off);
+        off += workspace_bytes<float>(p->gcap, p->w32);
+    }
     if (p->has64) { carve_workspace<double>(g, p->w64, base + off); off += workspace_bytes<double>(g, p->w64); }
     if (p->ws32.rows_grid > 0) { carve_workspace<df32>(g, p->ws32, base + off); off += workspace_bytes<df32>(g, p->ws32); }
     if (p->prec == CMIF_AUTO) { esc_carve(p, base + off); off += p->esc.bytes; }
-    p->w32.bytes = p->has32 ? workspace_bytes<float>(g, p->w32) : 0;
+    p->w32.bytes = p->has32 ? workspace_bytes<float>(p->gcap, p->w32) : 0;
     p->w64.bytes = p->has64 ? workspace_bytes<double>(g, p->w64) : 0;
     p->ws32.bytes = p->ws32.rows_grid > 0 ? workspace_bytes<df32>(g, p->ws32) : 0;
     if (cudaMemset(p->st, 0, 2 * align_up(sizeof(DevStatus), 256)) != cudaSuccess) return CMIF_ERR_CUDA;
@@ -615,12 +676,72 @@ cmif_status run_graph(cmif_plan p, cudaStream_t s, std::vector<unsigned char> ke
     return from_cuda(e);
 }
 
+// Alg. 1 over rotations with up to ucap angles per launch of every stage: A's
+// transforms once, then per chunk of angles one warp launch, B's row and column
+// transforms of all the chunk's rotated images, one pair-column and one row
+// launch over (angle, pair) and (angle, row) work, and the per-angle peaks.
+cmif_status align_core_units(cmif_plan plan, const Geom& g, const int32_t* A, const uint8_t* M_A, const int32_t* B,
+                             const uint8_t* M_B, const double* angles, int n_angles, double gamma, int top_k,
+                             void* topk_dev, double* mi_maps, int32_t* n_maps, cudaStream_t s) {
+    const size_t RC = (size_t)g.R * g.C;
+    PeakRec* peaks = reinterpret_cast<PeakRec*>(plan->peaks);
+    cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), s);
+    if (e != cudaSuccess) return from_cuda(e);
+    PipeArgs<float> a = plan->w32.args;
+    fill_io(a, A, M_A, nullptr, nullptr, nullptr, nullptr, nullptr, plan->st, plan);
+    a.prof = plan->prof.enabled ? &plan->prof : nullptr;
+    a.prec_slot = 0;
+    a.conditional = 0;
+    a.stages = STAGE_FWD_A;
+    e = run_pipeline<float>(g, a, s);  // A's transforms, shared by every angle
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int c0 = 0; c0 < n_angles; c0 += plan->ucap) {
+        const int G = std::min(plan->ucap, n_angles - c0);
+        Geom gu = g;
+        gu.units = G;
+        gu.DB = G;
+        gu.R = G * g.R2;
+        double* mi = mi_maps ? mi_maps + (size_t)c0 * RC : plan->mibuf;
+        int32_t* nm = n_maps ? n_maps + (size_t)c0 * RC : plan->nbuf;
+        if (g.r0 > 0 || g.r1 < g.R) {  // rows outside the window are not computed: zero
+            if (mi_maps) e = cudaMemsetAsync(mi, 0, G * RC * sizeof(double), s);
+            if (e == cudaSuccess && n_maps) e = cudaMemsetAsync(nm, 0, G * RC * sizeof(int32_t), s);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        plan->prof.begin("warp_nn", s);
+        e = launch_warp_nn_multi(B, M_B, g.HB, g.WB, angles + c0, G, plan->wB, plan->wM, s);
+        plan->prof.end(s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(plan->st, 0, sizeof(DevStatus), s);
+        if (e != cudaSuccess) return from_cuda(e);
+        fill_io(a, A, M_A, plan->wB, plan->wM, mi, nm, nullptr, plan->st, plan);
+        a.stages = STAGE_FWD_B | STAGE_PAIRS;
+        a.rows_grid = std::min(G * (g.r1 - g.r0), plan->w32.rows_grid);
+        e = run_pipeline<float>(gu, a, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        plan->prof.begin("finalize", s);
+        e = launch_finalize(plan->st, 0, 0, s);
+        if (e == cudaSuccess) e = launch_merge_status(plan->st, plan->st_total, 0, s);
+        plan->prof.end(s);
+        if (e != cudaSuccess) return from_cuda(e);
+        plan->prof.begin("peak", s);
+        e = launch_peak_units(mi, nm, gu, plan->st, gamma, plan->parts, plan->nparts, c0, peaks + c0, plan->maxn_u, s);
+        plan->prof.end(s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    plan->prof.begin("topk", s);
+    e = launch_topk(peaks, n_angles, top_k, topk_dev, s);
+    plan->prof.end(s);
+    return from_cuda(e);
+}
+
 // Alg. 1 over rotations for one pair (see cmif_align_rotations); enqueues on s.
 cmif_status align_core(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B, const uint8_t* M_B,
                        const double* angles, int n_angles, double gamma, int top_k, void* topk_dev, double* mi_maps,
                        int32_t* n_maps, cudaStream_t s) {
     Geom g;
     if (!call_geom(plan, gamma, &g)) return CMIF_ERR_INVALID_ARG;
+    if (plan->ucap > 1 && plan->prec == CMIF_FP32)
+        return align_core_units(plan, g, A, M_A, B, M_B, angles, n_angles, gamma, top_k, topk_dev, mi_maps, n_maps, s);
     const size_t RC = (size_t)g.R * g.C;
     cudaError_t e = cudaMemsetAsync(plan->st_total, 0, sizeof(DevStatus), s);
     if (e != cudaSuccess) return from_cuda(e);
@@ -649,6 +770,172 @@ cmif_status align_core(cmif_plan plan, const int32_t* A, const uint8_t* M_A, con
     e = launch_topk(peaks, n_angles, top_k, topk_dev, s);
     plan->prof.end(s);
     return from_cuda(e);
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Autotuner: the FP32 path of a plan has a few launch-shape choices whose best
+// value depends on the transform sizes, the label counts and the GPU: the
+// column transforms' lanes per group (32, or 16 with a radix-R exchange), the
+// row kernel (Tensor-Memory or generic) and the pair-column kernel's persistent
+// blocks per SM.  The tuner times every candidate on synthetic labels of the
+// plan's sizes (CUDA events, the median of a few maps) and keeps the fastest;
+// results are cached per process and, optionally, in a JSON-lines file keyed
+// on (P, Q, K_A, K_B, depths, precision, SM count, device name).
+
+struct TuneRec {
+    int col_m = 0, tmem = 0, cols_bps = 0;
+    double ms = 0.0;
+};
+
+std::string tune_key(const cmif_plan p) {
+    const Geom& g = p->g;
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, p->device);
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "P%d.Q%d.KA%d.KB%d.DA%d.DB%d.%s.sm%d.%s", g.P, g.Q, g.KA, g.KB, g.DA, g.DB,
+                  p->prec == CMIF_AUTO ? "auto" : "fp32", p->num_sms, prop.name);
+    return buf;
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneRec> g_tune_cache;
+
+int json_int(const std::string& line, const char* field, int dflt) {
+    const std::string pat = std::string("\"") + field + "\": ";
+    const size_t at = line.find(pat);
+    return at == std::string::npos ? dflt : std::atoi(line.c_str() + at + pat.size());
+}
+
+bool tune_lookup_file(const char* path, const std::string& key, TuneRec* out) {
+    if (!path) return false;
+    std::FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    bool found = false;
+    char line[1024];
+    const std::string kpat = "\"key\": \"" + key + "\"";
+    while (std::fgets(line, sizeof line, f)) {
+        const std::string l(line);
+        if (l.find(kpat) == std::string::npos) continue;  // the last matching line wins
+        out->col_m = json_int(l, "col_m", 0);
+        out->tmem = json_int(l, "tmem_rows", 0);
+        out->cols_bps = json_int(l, "cols_blocks_per_sm", 0);
+        const size_t at = l.find("\"ms\": ");
+        out->ms = at == std::string::npos ? 0.0 : std::atof(l.c_str() + at + 6);
+        found = true;
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_store_file(const char* path, const std::string& key, const TuneRec& r) {
+    if (!path) return;
+    std::FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"col_m\": %d, \"tmem_rows\": %d, \"cols_blocks_per_sm\": %d, \"ms\": %.4f}\n",
+                 key.c_str(), r.col_m, r.tmem, r.cols_bps, r.ms);
+    std::fclose(f);
+}
+
+void apply_tune(cmif_plan p, const TuneRec& r) {
+    p->w32.args.col_m = r.col_m;
+    p->w32.args.cols_bps = r.cols_bps;
+    set_rows_kernel(p->w32, r.tmem != 0);
+    if (p->gexec) {  // captured launches used the old shapes
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+        p->gkey.clear();
+    }
+}
+
+cmif_status autotune(cmif_plan p, const char* cache_path, cmif_tuning* out) {
+    if (!p->has32) {  // FP64 / two-term plans: nothing to choose
+        if (out) *out = cmif_tuning{0, 0, 0, 0.0, 0, 0};
+        return CMIF_OK;
+    }
+    const std::string key = tune_key(p);
+    TuneRec best;
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { best = it->second; have = true; }
+    }
+    int from_cache = have ? 1 : 0;
+    if (!have && tune_lookup_file(cache_path, key, &best)) { have = true; from_cache = 2; }
+    int ncand = 0;
+    if (!have) {
+        const Geom& g = p->g;
+        const long long nA = (long long)g.DA * g.HA * g.WA, nB = (long long)g.DB * g.HB * g.WB;
+        int32_t* lab = nullptr;
+        cudaStream_t s = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaMalloc(&lab, (size_t)(nA + nB) * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e == cudaSuccess) e = launch_fill_labels(lab, nA, g.KA, 12345u, s);
+        if (e == cudaSuccess) e = launch_fill_labels(lab + nA, nB, g.KB, 67890u, s);
+        std::vector<TuneRec> cands;
+        const int col_ms[2] = {0, 16};
+        for (int cm : col_ms) {
+            if (cm == 16 && g.P < 1024) continue;
+            for (int tm = 1; tm >= 0; --tm) {
+                if (tm ? p->w32.tm_cols_avail <= 0 : (p->w32.tm_cols_avail > 0 && p->w32.grid_gen <= 0)) continue;
+                for (int bps : {0, 1}) cands.push_back(TuneRec{cm, tm, bps, 0.0});
+            }
+        }
+        const TuneRec before{p->w32.args.col_m, p->w32.args.tm_cols > 0 ? 1 : 0, p->w32.args.cols_bps, 0.0};
+        double best_ms = 1e30;
+        for (TuneRec& c : cands) {
+            if (e != cudaSuccess) break;
+            apply_tune(p, c);
+            PipeArgs<float> a = p->w32.args;
+            fill_io(a, lab, nullptr, lab + nA, nullptr, p->mibuf, p->nbuf, nullptr, p->st, p);
+            a.stages = STAGE_ALL;
+            a.prec_slot = 0;
+            a.conditional = 0;
+            std::vector<float> ts;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = run_pipeline<float>(g, a, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ts.push_back(ms);  // the first run warms up
+            }
+            if (e != cudaSuccess) break;
+            std::sort(ts.begin(), ts.end());
+            c.ms = ts[ts.size() / 2];
+            ++ncand;
+            if (c.ms < best_ms) { best_ms = c.ms; best = c; }
+        }
+        if (s) cudaStreamDestroy(s);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (lab) cudaFree(lab);
+        if (e != cudaSuccess) {
+            apply_tune(p, before);
+            cudaGetLastError();
+            return from_cuda(e);
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+        tune_store_file(cache_path, key, best);
+    } else if (from_cache == 2) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    // a cached choice may name an alternative this plan lacks (other flags): fall back
+    if (best.tmem ? p->w32.tm_cols_avail <= 0 : (p->w32.tm_cols_avail > 0 && p->w32.grid_gen <= 0)) best.tmem = !best.tmem;
+    if (best.col_m == 16 && p->g.P < 1024) best.col_m = 0;
+    apply_tune(p, best);
+    if (out) *out = cmif_tuning{best.col_m ? best.col_m : 32, best.tmem, best.cols_bps, best.ms, from_cache, ncand};
+    return CMIF_OK;
 }
 
 }  // namespace
@@ -685,6 +972,7 @@ cmif_status plan_create(cmif_plan* out, int D_A, int H_A, int W_A, int D_B, int 
             st = plan_carve(p, (char*)p->mem);
         }
     }
+    if (st == CMIF_OK && (flags & CMIF_FLAG_AUTOTUNE)) st = autotune(p, std::getenv("CMIF_TUNE_CACHE"), nullptr);
     if (st != CMIF_OK) {
         free_plan(p);
         return st;
@@ -980,7 +1268,8 @@ cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc
                               unsigned flags) {
     if (!out) return CMIF_ERR_INVALID_ARG;
     *out = nullptr;
-    if (n_pairs < 1 || !descs || (flags & ~(CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI)))
+    if (n_pairs < 1 || !descs ||
+        (flags & ~(CMIF_FLAG_GRAPH | CMIF_FLAG_WINDOW | CMIF_FLAG_NMI | CMIF_FLAG_AUTOTUNE | CMIF_FLAG_BATCH_ANGLES)))
         return CMIF_ERR_INVALID_ARG;
     for (int i = 0; i < n_pairs; ++i) {
         const cmif_pair_desc& d = descs[i];
@@ -1008,7 +1297,8 @@ cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc
         if (!p) return fail(CMIF_ERR_OOM);
         b->plans.push_back(p);
         cmif_status st = plan_init(p, d.H_A, d.W_A, d.H_B, d.W_B, d.K_A, d.K_B, prec,
-                                   flags & (CMIF_FLAG_WINDOW | CMIF_FLAG_NMI));
+                                   flags & (CMIF_FLAG_WINDOW | CMIF_FLAG_NMI | CMIF_FLAG_BATCH_ANGLES), 1, 1,
+                                   std::max(1, d.n_angles));
         if (st != CMIF_OK) return fail(st);
         max_bytes = std::max(max_bytes, plan_bytes(p));
     }
@@ -1022,6 +1312,12 @@ cmif_status cmif_batch_create(cmif_batch* out, int n_pairs, const cmif_pair_desc
     }
     b->total = (DevStatus*)((char*)b->mem + tot_off);
     if (cudaMemset(b->total, 0, sizeof(DevStatus)) != cudaSuccess) return fail(CMIF_ERR_CUDA);
+    if (flags & CMIF_FLAG_AUTOTUNE) {  // each size class is timed once (the tuner's cache serves the rest)
+        for (cmif_plan p : b->plans) {
+            cmif_status st = autotune(p, std::getenv("CMIF_TUNE_CACHE"), nullptr);
+            if (st != CMIF_OK) return fail(st);
+        }
+    }
     b->graph_holder.use_graph = (flags & CMIF_FLAG_GRAPH) != 0;
     b->graph_holder.device = b->device;
     *out = b;
@@ -1128,6 +1424,14 @@ cmif_status cmif_plan_stage_times(cmif_plan plan, int max_n, int* n, double* ms,
         if (names) names[i] = plan->prof.names[i];
     }
     return CMIF_OK;
+}
+
+cmif_status cmif_plan_autotune(cmif_plan plan, const char* cache_path, cmif_tuning* out) {
+    if (!plan) return CMIF_ERR_INVALID_ARG;
+    DeviceGuard dg(plan->device);
+    cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return autotune(plan, cache_path, out);
 }
 
 cmif_status cmif_plan_set_wait_test(cmif_plan plan, int poll_limit, int withhold_row) {

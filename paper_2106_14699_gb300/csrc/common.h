@@ -38,6 +38,11 @@ struct Geom {
     // H_A + H_B - 1 rows per depth offset, and the maps have R = Dz * R2 rows
     // (depth-offset major).  Images: DA = DB = Dz = 1, R2 = R.
     int DA, DB, Dz, R2;
+    // Units: several floating images against one A in one launch per stage (the
+    // rotation angles of Alg. 1).  Unit u's B planes are label * DB + u (DB = units),
+    // its map rows u * R2 + (row), R = units * R2; r0, r1 bound the rows of each
+    // unit.  1 for a single map (and for volumes).
+    int units;
 };
 
 constexpr float kResidualGuard = 0.25f;  // a count whose pre-rounding residual reaches this is not trusted

@@ -388,7 +388,9 @@ __global__ void __launch_bounds__(PairColsCfg<T, P, MMAX>::THREADS, PairColsCfg<
 k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA, int KB, int Qh, int HA, int HB,
             int Rout, int Qs, int r0, int r1, cpx<T>* __restrict__ Y, Tw<T> tw, const DevStatus* __restrict__ st,
             int conditional, int* __restrict__ work_ctr, int DA, int DB, int R2, const int* __restrict__ plist,
-            const int* __restrict__ lrange, int chunk_off, int chunk_cap) {
+            const int* __restrict__ lrange, int chunk_off, int chunk_cap, int units) {
+    // units > 1 (images only): several floating images (rotation angles) at once;
+    // unit u's spectra are F_b plane b * units + u, its output rows u * R2 + (row).
     // List mode (plist non-null): only the pairs plist[lrange[0] + chunk_off + e],
     // e < min(chunk_cap, lrange[1] - lrange[0] - chunk_off), are computed, pair e's
     // rows going to Y + e * Rout * Qs.
@@ -403,7 +405,8 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
         if (npairs <= 0) return;  // uniform: nothing listed for this launch
     }
     auto real_pair = [&](int e) { return plist ? ::__ldg(plist + lbase + e) : e; };
-    const int nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb * Dz;
+    const int U = VOL ? Dz : units;  // the middle item dimension: depth offsets or units
+    const int nkxb = (Qh + TPB - 1) / TPB, n_items = npairs * nkxb * U;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_item;
     cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -424,7 +427,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     cpx<T> v[M];
     auto load_fa = [&](int it) {
         if constexpr (VOL) return;  // volumes sum over slices in the item itself
-        const int kx = (it / npairs) * TPB + team, a = real_pair(it % npairs) / KB;
+        const int kx = (VOL ? it / npairs / U : (it / npairs) % nkxb) * TPB + team, a = real_pair(it % npairs) / KB;
         if (kx < Qh) {
             const cpx<T>* ga = FA + ((size_t)a * Qh + kx) * P + r * NQ + j;
 #pragma unroll
@@ -439,8 +442,11 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
         int next = 0;
         if (threadIdx.x == 0) next = atomicAdd(work_ctr, 1);
         const int e = item % npairs, pair = real_pair(e);
-        const int kxb = VOL ? item / npairs / Dz : item / npairs;
-        const int dzo = VOL ? (item / npairs) % Dz : 0;
+        // volumes: kx block outermost, then the depth offset (the slices' spectra of one
+        // kx block serve every depth offset); units: the unit outermost, so that the
+        // items in flight write the rows of few maps and complete their lines in L2
+        const int kxb = VOL ? item / npairs / U : (item / npairs) % nkxb;
+        const int dzo = VOL ? (item / npairs) % U : item / npairs / nkxb;  // VOL: depth offset index; else the unit
         const int kx0 = kxb * TPB, kx = kx0 + team, b = pair % KB;
         if constexpr (VOL) {
 #pragma unroll
@@ -456,7 +462,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                 }
             }
         } else if (kx < Qh) {
-            const cpx<T>* gb = FB + ((size_t)b * Qh + kx) * P + r * NQ + j;
+            const cpx<T>* gb = FB + ((size_t)(b * units + dzo) * Qh + kx) * P + r * NQ + j;
 #pragma unroll
             for (int i = 0; i < M; ++i) v[i] = cmulc(__ldg(gb + M * i), v[i]);
         }
@@ -465,7 +471,8 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             // spectrum's columns of kx block kxb + 2 into L2 (one bulk request per column)
             const int kf = (kxb + 2) * TPB + threadIdx.x;
             if (kf < Qh) {
-                const cpx<T>* src = pair < KA ? FA + ((size_t)pair * Qh + kf) * P : FB + ((size_t)(pair - KA) * Qh + kf) * P;
+                const cpx<T>* src = pair < KA ? FA + ((size_t)pair * Qh + kf) * P
+                                              : FB + ((size_t)((pair - KA) * units + dzo) * Qh + kf) * P;
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((unsigned)(P * sizeof(cpx<T>)))
                              : "memory");
             }
@@ -557,6 +564,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                             orow += dzo * R2;
                         }
                         if (orow < r0 || orow >= r1) continue;
+                        if constexpr (!VOL) orow += dzo * R2;  // the unit's rows
                         float4 pv = *src;
                         if (swap_halves) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
                         dst[(size_t)orow * (Qs / 2)] = pv;
@@ -571,6 +579,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                         orow += dzo * R2;
                     }
                     if (orow < r0 || orow >= r1 || kx0 + 2 * h >= Qs) continue;
+                    if constexpr (!VOL) orow += dzo * R2;
                     const int sw = (row >> C::SWZ) & (TPB - 1);
                     float4 pv = reinterpret_cast<const float4*>(xbuf)[row * PPR + (h ^ (sw >> 1))];
                     if (sw & 1) pv = make_float4(pv.z, pv.w, pv.x, pv.y);
@@ -587,6 +596,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                     orow += dzo * R2;
                 }
                 if (orow < r0 || orow >= r1 || kx0 + c >= Qs) continue;
+                if constexpr (!VOL) orow += dzo * R2;
                 const int sw = (row >> C::SWZ) & (TPB - 1);
                 yp[(size_t)orow * Qs + kx0 + c] = xbuf[(size_t)row * TPB + (c ^ sw)];
             }
@@ -655,7 +665,10 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
     float res_max = 0.f;
     int row_max_n = 0;
 
-    for (int row = g.r0 + blockIdx.x; row < g.r1; row += gridDim.x) {
+    // tasks: the window's rows of every unit (units > 1: several maps, R2 rows apart)
+    const int nr = g.r1 - g.r0, ntask = g.units * nr;
+    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+        const int row = (task / nr) * g.R2 + g.r0 + task % nr;
         EntAcc<NMI> S[U];
         float CA[U];
         int N[U];

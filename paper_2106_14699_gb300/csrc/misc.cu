@@ -27,11 +27,16 @@ __device__ __forceinline__ double max_n_of(const DevStatus* st, const double*) {
 __device__ __forceinline__ int32_t n_record(int32_t n) { return n; }
 __device__ __forceinline__ int32_t n_record(double n) { return (int32_t)fmin(rint(n), 2147483647.0); }
 
+// Units (blockIdx.y): map u starts unit_rc elements further on, its max N comes
+// from maxn_u[u] and its partials from parts + u * gridDim.x.
 template <typename NT>
 __global__ void k_peak_partial(const double* __restrict__ mi, const NT* __restrict__ n, int Cout, int r0, int r1,
                                int c0, int c1, const DevStatus* __restrict__ st, double gamma,
-                               PeakPart* __restrict__ parts) {
-    const double thr = gamma * max_n_of(st, n);
+                               PeakPart* __restrict__ parts, long long unit_rc, const int* __restrict__ maxn_u) {
+    mi += blockIdx.y * unit_rc;
+    n += blockIdx.y * unit_rc;
+    parts += (size_t)blockIdx.y * gridDim.x;
+    const double thr = gamma * (maxn_u ? (double)maxn_u[blockIdx.y] : max_n_of(st, n));
     const int wc = c1 - c0;
     const long long cnt = (long long)(r1 - r0) * wc;
     double bm = -INFINITY;
@@ -62,10 +67,16 @@ __global__ void k_peak_partial(const double* __restrict__ mi, const NT* __restri
 
 // R2 > 0 (volumes): the map rows are (depth offset, row) pairs, depth-offset
 // major; the record's first field then holds the depth offset dz.
+// Units (blockIdx.x): unit u reads its partials and map and writes record u.
 template <typename NT>
 __global__ void k_peak_final(const PeakPart* __restrict__ parts, int nparts, const double* __restrict__ mi,
                              const NT* __restrict__ n, int HA, int WA, int Cout, int angle_idx, int R2, int DA,
-                             void* __restrict__ peak_out) {
+                             void* __restrict__ peak_out, long long unit_rc) {
+    parts += (size_t)blockIdx.x * nparts;
+    mi += blockIdx.x * unit_rc;
+    n += blockIdx.x * unit_rc;
+    peak_out = reinterpret_cast<PeakRec*>(peak_out) + blockIdx.x;
+    angle_idx += blockIdx.x;
     double bm = -INFINITY;
     long long bi = -1;
     for (int k = threadIdx.x; k < nparts; k += blockDim.x)
@@ -119,6 +130,42 @@ __global__ void k_warp_nn(const int32_t* __restrict__ B, const uint8_t* __restri
         Bo[o] = lab;
         Mo[o] = m;
     }
+}
+
+// Several angles at once (blockIdx.y = angle): outputs Bo + y * H * W, Mo + y * H * W.
+__global__ void k_warp_nn_multi(const int32_t* __restrict__ B, const uint8_t* __restrict__ MB, int H, int W,
+                                AngleSet as, int32_t* __restrict__ Bo, uint8_t* __restrict__ Mo) {
+    const long long n = (long long)H * W;
+    const double ct = as.c[blockIdx.y], st = as.s[blockIdx.y];
+    Bo += blockIdx.y * n;
+    Mo += blockIdx.y * n;
+    const double cr = 0.5 * (H - 1), cc = 0.5 * (W - 1);
+    for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(o / W), j = (int)(o - (long long)i * W);
+        const double u = j - cc, v = i - cr;
+        const double xs = cc + u * ct - v * st;
+        const double ys = cr + u * st + v * ct;
+        const long long si = (long long)round(ys), sj = (long long)round(xs);
+        int32_t lab = 0;
+        uint8_t m = 0;
+        if (si >= 0 && si < H && sj >= 0 && sj < W) {
+            const long long src = si * W + sj;
+            if (!MB || MB[src]) { lab = B[src]; m = 1; }
+        }
+        Bo[o] = lab;
+        Mo[o] = m;
+    }
+}
+
+cudaError_t launch_warp_nn_multi(const int32_t* B, const uint8_t* MB, int H, int W, const double* theta, int n_angles,
+                                 int32_t* Bo, uint8_t* Mo, cudaStream_t s) {
+    if (n_angles < 1 || n_angles > kMaxUnits) return cudaErrorInvalidValue;
+    AngleSet as{};
+    for (int i = 0; i < n_angles; ++i) { as.c[i] = std::cos(theta[i]); as.s[i] = std::sin(theta[i]); }
+    const long long n = (long long)H * W;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+    k_warp_nn_multi<<<dim3(blocks, n_angles), 256, 0, s>>>(B, MB, H, W, as, Bo, Mo);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_warp_nn(const int32_t* B, const uint8_t* MB, int H, int W, double theta, int32_t* Bo, uint8_t* Mo,
@@ -206,24 +253,53 @@ __global__ void k_finalize(DevStatus* st, int slot_if_escalated, int slot_defaul
     }
 }
 
+// Max N over each unit's window (units > 1: the gamma gate of Alg. 1 is per map).
+__global__ void k_unit_max_n(const int32_t* __restrict__ n, int Cout, int r0, int r1, int c0, int c1,
+                             long long unit_rc, int* __restrict__ maxn_u) {
+    n += blockIdx.y * unit_rc;
+    const int wc = c1 - c0;
+    const long long cnt = (long long)(r1 - r0) * wc;
+    int m = 0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x)
+        m = max(m, n[(long long)(r0 + t / wc) * Cout + c0 + t % wc]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&maxn_u[blockIdx.y], m);
+}
+
 template <typename NT>
 static cudaError_t launch_peak_t(const double* mi, const NT* n, const Geom& g, const DevStatus* st, double gamma,
-                                 PeakPart* parts, int nparts, int angle_idx, void* peak_out, cudaStream_t s) {
+                                 PeakPart* parts, int nparts, int angle_idx, void* peak_out, int units,
+                                 const int* maxn_u, cudaStream_t s) {
     const int HA = g.HA, WA = g.WA, Cout = g.C;
-    k_peak_partial<NT><<<nparts, 256, 0, s>>>(mi, n, Cout, g.r0, g.r1, g.c0, g.c1, st, gamma, parts);
-    k_peak_final<NT><<<1, 256, 0, s>>>(parts, nparts, mi, n, HA, WA, Cout, angle_idx, g.Dz > 1 ? g.R2 : 0, g.DA,
-                                         peak_out);
+    const long long unit_rc = units > 1 ? (long long)g.R2 * Cout : 0;
+    k_peak_partial<NT><<<dim3(nparts, units), 256, 0, s>>>(mi, n, Cout, g.r0, g.r1, g.c0, g.c1, st, gamma, parts,
+                                                           unit_rc, units > 1 ? maxn_u : nullptr);
+    k_peak_final<NT><<<units, 256, 0, s>>>(parts, nparts, mi, n, HA, WA, Cout, angle_idx, g.Dz > 1 ? g.R2 : 0, g.DA,
+                                             peak_out, unit_rc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_peak(const double* mi, const int32_t* n, const Geom& g, const DevStatus* st, double gamma,
                         PeakPart* parts, int nparts, int angle_idx, void* peak_out, cudaStream_t s) {
-    return launch_peak_t(mi, n, g, st, gamma, parts, nparts, angle_idx, peak_out, s);
+    return launch_peak_t(mi, n, g, st, gamma, parts, nparts, angle_idx, peak_out, 1, nullptr, s);
+}
+
+cudaError_t launch_peak_units(const double* mi, const int32_t* n, const Geom& g, const DevStatus* st, double gamma,
+                              PeakPart* parts, int nparts, int angle0, void* peaks_out, int* maxn_u,
+                              cudaStream_t s) {
+    // per-unit max N first (zeroed here), then the gated argmax of every unit
+    cudaError_t e = cudaMemsetAsync(maxn_u, 0, (size_t)g.units * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const long long unit_rc = (long long)g.R2 * g.C;
+    k_unit_max_n<<<dim3(std::max(1, nparts / 2), g.units), 256, 0, s>>>(n, g.C, g.r0, g.r1, g.c0, g.c1, unit_rc,
+                                                                         maxn_u);
+    return launch_peak_t(mi, n, g, st, gamma, parts, nparts, angle0, peaks_out, g.units, maxn_u, s);
 }
 
 cudaError_t launch_peak_w(const double* mi, const double* nw, const Geom& g, const DevStatus* st, double gamma,
                           PeakPart* parts, int nparts, void* peak_out, cudaStream_t s) {
-    return launch_peak_t(mi, nw, g, st, gamma, parts, nparts, 0, peak_out, s);
+    return launch_peak_t(mi, nw, g, st, gamma, parts, nparts, 0, peak_out, 1, nullptr, s);
 }
 
 cudaError_t launch_finalize(DevStatus* st, int slot_if_escalated, int slot_default, cudaStream_t s) {
@@ -356,6 +432,25 @@ cudaError_t launch_check_pairs(const unsigned* pair_res, int KA, int KB, int cap
                                cudaStream_t s) {
     if (KA * KB > 4096 || cap < 1) return cudaErrorInvalidValue;
     k_check_pairs<<<1, 1024, 0, s>>>(pair_res, KA, KB, cap, plist, hdr, ov_slot, needA, needB, st);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Synthetic labels for timing runs (the autotuner): X[i] = hash(i, seed) mod K.
+// The transforms' cost does not depend on the labels.
+__global__ void k_fill_labels(int32_t* __restrict__ X, long long n, int K, unsigned seed) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)i * 2654435761u ^ seed;
+        h ^= h >> 16;
+        h *= 0x7feb352du;
+        h ^= h >> 15;
+        X[i] = (int32_t)(h % (unsigned)K);
+    }
+}
+
+cudaError_t launch_fill_labels(int32_t* X, long long n, int K, unsigned seed, cudaStream_t s) {
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+    k_fill_labels<<<blocks, 256, 0, s>>>(X, n, K, seed);
     return cudaGetLastError();
 }
 

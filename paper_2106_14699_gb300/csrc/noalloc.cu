@@ -101,7 +101,7 @@ extern "C" cmif_status cmif_compute_noalloc(int H_A, int W_A, int H_B, int W_B, 
     g.R = H_A + H_B - 1;
     g.C = W_A + W_B - 1;
     g.r0 = 0; g.r1 = g.R; g.c0 = 0; g.c1 = g.C;  // the whole map
-    g.DA = 1; g.DB = 1; g.Dz = 1; g.R2 = g.R;     // images
+    g.DA = 1; g.DB = 1; g.Dz = 1; g.R2 = g.R; g.units = 1;  // images, one map
     g.P = 16;
     while (g.P < g.R) g.P <<= 1;
     g.Q = 16;

@@ -42,6 +42,7 @@ struct PipeArgs {
     int col_m;        // column transforms' lanes per group: 0 = the default (32 for FP32), 16 = the
                       // 16-lane variant (FP32, P >= 1024); the spectra layout follows it, so the
                       // forward and pair column kernels of one map must use the same value
+    int cols_bps;     // persistent blocks per SM of the pair-column kernel (0: as many as fit)
     int wait_polls;   // poll limit of the TMEM row kernel's bounded waits (0: the default)
     int withhold_row; // diagnostics: output row whose first bulk copy is withheld (-1: none)
     unsigned stages;  // STAGE_* bits: which parts of the sequence to launch
@@ -105,6 +106,9 @@ struct Sized {
 
 template <typename T>
 cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);
+// The Tensor-Memory row kernel over several units (FP32, Q = 1024 or 2048).
+template <int Q, bool NMI>
+cudaError_t launch_rows_tm_units(const Geom& g, const PipeArgs<float>& a, cudaStream_t s);
 // List mode of the second precision: pair products and inverse column transforms of
 // the chunk's listed pairs (into a.Y), then their exact counts (into a.ov).
 template <typename T>

@@ -66,14 +66,15 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
         per_sm = n > 0 ? n : 1;
     }
     const long long np = a.plist ? a.chunk_cap : (long long)g.KA * g.KB;  // list mode: at most chunk_cap pairs
-    const long long items = np * ((g.Qh + C::TPB - 1) / C::TPB) * (VOL ? g.Dz : 1);
-    const long long slots = a.num_sms > 0 ? (long long)per_sm * a.num_sms : items;
+    const long long items = np * ((g.Qh + C::TPB - 1) / C::TPB) * (VOL ? g.Dz : g.units);
+    const int bps = a.cols_bps > 0 && a.cols_bps < per_sm ? a.cols_bps : per_sm;
+    const long long slots = a.num_sms > 0 ? (long long)bps * a.num_sms : items;
     const int grid = (int)(items < slots ? items : slots);
     e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     kern<<<grid, C::THREADS, smem, s>>>(a.FA, a.FB, g.KA, g.KB, g.Qh, g.HA, g.HB, g.R, g.Qs, g.r0, g.r1, a.Y, a.tw,
                                         a.st, a.conditional, a.work_ctr, g.DA, g.DB, g.R2, a.plist, a.lrange,
-                                        a.chunk_off, a.chunk_cap);
+                                        a.chunk_off, a.chunk_cap, VOL ? 1 : g.units);
     return cudaGetLastError();
 }
 
@@ -83,7 +84,10 @@ static cudaError_t launch_pair_rows_v(const Geom& g, const PipeArgs<T>& a, cudaS
     if constexpr (sizeof(T) == 4 && (Q == 1024 || Q == 2048)) {
         if (a.tm_cols > 0 && !a.counts) {  // debug count maps: the generic kernel below
             const bool ext = a.ov_slot || a.pair_res || a.conditional || a.wait_polls > 0 || a.withhold_row >= 0;
-            auto kern = ext ? k_pair_rows_tm<Q, NMI, true> : k_pair_rows_tm<Q, NMI, false>;
+            // the multi-unit kernel lives in its own translation unit (kernels_f32_rows_units.cu):
+            // compiled next to the plain one, it changed the plain kernel's register allocation
+            if (!ext && g.units > 1) return launch_rows_tm_units<Q, NMI>(g, a, s);
+            auto kern = ext ? k_pair_rows_tm<Q, NMI, 2> : k_pair_rows_tm<Q, NMI, 0>;
             cudaError_t e = ensure_smem(kern, RowTmCfg<Q>::SMEM);
             if (e != cudaSuccess) return e;
             kern<<<a.rows_grid, RowTmCfg<Q>::THREADS, RowTmCfg<Q>::SMEM, s>>>(
@@ -250,9 +254,9 @@ int Sized<T, SZ>::tm_cols(int KB) {
 template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::tm_max_blocks(int* out) {
     if constexpr (sizeof(T) == 4 && (SZ == 1024 || SZ == 2048)) {
-        cudaError_t e = ensure_smem(k_pair_rows_tm<SZ, false, false>, RowTmCfg<SZ>::SMEM);
+        cudaError_t e = ensure_smem(k_pair_rows_tm<SZ, false, 0>, RowTmCfg<SZ>::SMEM);
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pair_rows_tm<SZ, false, false>, RowTmCfg<SZ>::THREADS,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pair_rows_tm<SZ, false, 0>, RowTmCfg<SZ>::THREADS,
                                                              RowTmCfg<SZ>::SMEM);
     } else {
         *out = 0;

@@ -144,11 +144,13 @@ __host__ __device__ constexpr int tm_alloc_cols(int need) {
     return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 
-// EXT = false is the plain FP32 kernel; EXT = true adds the per-pair precision of
-// CMIF_AUTO (conditional re-run, exact counts of listed pairs, per-pair residuals)
-// and the diagnostics of the bounded waits (poll limit, withheld copy).  The two
-// are separate instantiations because the plain kernel sits at the register limit.
-template <int Q, bool NMI, bool EXT>
+// MODE 0 is the plain FP32 kernel (one map); MODE 1 takes several units per
+// launch (rotation angles); MODE 2 adds to that the per-pair precision of
+// CMIF_AUTO (conditional re-run, exact counts of listed pairs, per-pair
+// residuals) and the diagnostics of the bounded waits (poll limit, withheld
+// copy).  They are separate instantiations because the plain kernel sits at
+// the register limit.
+template <int Q, bool NMI, int MODE>
 __global__ void __launch_bounds__(RowTmCfg<Q>::THREADS, 1)
 k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* __restrict__ mi_map,
                int32_t* __restrict__ n_map, DevStatus* __restrict__ st,
@@ -161,6 +163,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     // exact counts of second-precision pairs and the per-pair residuals, as in
     // k_pair_rows.
     using C = RowTmCfg<Q>;
+    constexpr bool EXT = MODE == 2, MULTI = MODE >= 1;
     if (EXT && conditional && !(st->flags & STATUS_ESCALATE)) return;  // uniform, before any set-up
     if (!EXT) {
         wait_polls = kDefaultWaitPolls;
@@ -198,6 +201,8 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     // work items of this team: (row, base) in order; prefetch the first active one
     uint32_t phase = 0;
     bool pending = false;  // a copy issued for this team and not yet waited for
+    // work: the window's rows r0 + blockIdx.x + k * gridDim.x of every unit (units > 1:
+    // several maps, R2 rows apart), unit by unit
     auto issue = [&](int row_i, int pair_i) {
         if (EXT && row_i == withhold_row && pair_i == 0) return;  // diagnostics: leave this wait without its copy
         if (lane == 0) {
@@ -212,7 +217,9 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     float res_max = 0.f;
     int row_max_n = 0;
     bool aborted = false;
-    for (int row = g.r0 + blockIdx.x; row < g.r1 && !aborted; row += gridDim.x) {
+    int rbase = 0;  // first map row of the current unit (multi-unit kernels: unit * R2, up to R)
+    for (int rr = g.r0 + blockIdx.x; rr < g.r1 && !aborted; rr += gridDim.x) {
+        const int row = MULTI ? rbase + rr : rr;
         EntAcc<NMI> S[U];
         float CA[U];
         int N[U];
@@ -261,9 +268,19 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
             // (the next round of this row, else round 0 of its next row)
             __syncwarp();
             if (act && !pending) {
-                int nrow = row, npair = pair + NT;
-                if (npair >= npairs) { nrow = row + gridDim.x; npair = team; }
-                if (nrow < g.r1) issue(nrow, npair);
+                if constexpr (MULTI) {
+                    int nb = rbase, nrr = rr, npair = pair + NT;
+                    if (npair >= npairs) {
+                        npair = team;
+                        nrr = rr + gridDim.x;
+                        if (nrr >= g.r1) { nrr = g.r0 + blockIdx.x; nb += g.R2; }
+                    }
+                    if (nb < g.R && nrr < g.r1) issue(nb + nrr, npair);
+                } else {
+                    int nrow = row, npair = pair + NT;
+                    if (npair >= npairs) { nrow = row + gridDim.x; npair = team; }
+                    if (nrow < g.r1) issue(nrow, npair);
+                }
             }
             float rp = 0.f;
 #pragma unroll
@@ -273,12 +290,13 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 const float2 c = __fadd2_rn(__fadd2_rn(x, make_float2(12582912.0f, 12582912.0f)),
                                             make_float2(-12582912.0f, -12582912.0f));
                 const float2 dv = __ffma2_rn(c, make_float2(-1.f, -1.f), x);
-                rp = fmaxf(rp, fmaxf(fabsf(dv.x), fabsf(dv.y)));
+                if constexpr (EXT) rp = fmaxf(rp, fmaxf(fabsf(dv.x), fabsf(dv.y)));
+                else res_max = fmaxf(res_max, fmaxf(fabsf(dv.x), fabsf(dv.y)));
                 v[k].x = c.x;
                 v[k].y = c.y;
             }
             const int ovs = (EXT && act && ov_slot) ? ov_slot[pair] : -1;  // loaded after the transform: fewer live registers
-            if (ovs < 0) res_max = fmaxf(res_max, rp);
+            if (EXT && ovs < 0) res_max = fmaxf(res_max, rp);
             if (EXT && pair_res && act && ovs < 0) {  // the warp is this pair's team
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) rp = fmaxf(rp, __shfl_xor_sync(0xffffffffu, rp, off));
@@ -407,6 +425,12 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
             }
         }
         __syncthreads();
+        if constexpr (MULTI) {  // past the unit's last row: the next unit's first
+            if (rr + (int)gridDim.x >= g.r1 && rbase + g.R2 < g.R) {
+                rbase += g.R2;
+                rr = g.r0 + (int)blockIdx.x - (int)gridDim.x;
+            }
+        }
     }
     // A team may still have a copy in flight (prefetched for an item it will not run
     // after an abort): wait for it, bounded, before the block exits.

@@ -85,6 +85,7 @@ def test_host_side_argument_errors_of_the_extensions(libcmif):
     assert libcmif.cmif_entropy_terms(-1, 4, ctypes.c_void_p(16), None) == INVALID              # c0 < 0
     assert libcmif.cmif_entropy_terms((1 << 22) - 2, 4, ctypes.c_void_p(16), None) == INVALID  # beyond 2^22
     assert libcmif.cmif_plan_set_wait_test(None, 0, -1) == INVALID
+    assert libcmif.cmif_plan_autotune(None, None, None) == INVALID
 
 
 _LAYOUT_PROBE = r"""
@@ -100,8 +101,11 @@ int main(void) {
     OFF(cmif_pair_desc, K_A); OFF(cmif_pair_desc, K_B); OFF(cmif_pair_desc, angles_rad);
     OFF(cmif_pair_desc, n_angles); OFF(cmif_pair_desc, gamma);
     printf("prec %d %d %d %d\n", CMIF_FP32, CMIF_SPLIT32, CMIF_FP64, CMIF_AUTO);
-    printf("flags %u %u %u %u %u\n", CMIF_FLAG_DEBUG_COUNTS, CMIF_FLAG_GRAPH, CMIF_FLAG_WINDOW, CMIF_FLAG_NMI,
-           CMIF_FLAG_WEIGHTED);
+    printf("flags %u %u %u %u %u %u %u\n", CMIF_FLAG_DEBUG_COUNTS, CMIF_FLAG_GRAPH, CMIF_FLAG_WINDOW, CMIF_FLAG_NMI,
+           CMIF_FLAG_WEIGHTED, CMIF_FLAG_AUTOTUNE, CMIF_FLAG_BATCH_ANGLES);
+    printf("sizeof.cmif_tuning %zu\n", sizeof(cmif_tuning));
+    OFF(cmif_tuning, col_lanes); OFF(cmif_tuning, tmem_rows); OFF(cmif_tuning, cols_blocks_per_sm);
+    OFF(cmif_tuning, ms_per_map); OFF(cmif_tuning, from_cache); OFF(cmif_tuning, candidates);
     printf("status %d %d %d %d %d %d %d %d %d\n", CMIF_OK, CMIF_ERR_INVALID_ARG, CMIF_ERR_LABEL_RANGE, CMIF_ERR_OOM,
            CMIF_ERR_CUDA, CMIF_ERR_PRECISION, CMIF_ERR_TIMEOUT, CMIF_ERR_NOT_IMPLEMENTED, CMIF_ERR_UNSUPPORTED);
     printf("fixbits %d\n", CMIF_ENTROPY_FIX_BITS);
@@ -121,12 +125,14 @@ def test_binding_mirrors_the_header(tmp_path, libcmif):
     out = dict(line.split(" ", 1) for line in subprocess.check_output([str(exe)], text=True).splitlines())
     assert int(out["sizeof.cmif_peak"]) == ctypes.sizeof(cm.Peak)
     assert int(out["sizeof.cmif_pair_desc"]) == ctypes.sizeof(cm.PairDesc)
-    for T, S in (("cmif_peak", cm.Peak), ("cmif_pair_desc", cm.PairDesc)):
+    assert int(out["sizeof.cmif_tuning"]) == ctypes.sizeof(cm.Tuning)
+    for T, S in (("cmif_peak", cm.Peak), ("cmif_pair_desc", cm.PairDesc), ("cmif_tuning", cm.Tuning)):
         for name, _ in S._fields_:
             assert int(out[f"{T}.{name}"]) == getattr(S, name).offset, (T, name)
     assert [int(v) for v in out["prec"].split()] == [cm.FP32, cm.SPLIT32, cm.FP64, cm.AUTO]
     assert [int(v) for v in out["flags"].split()] == [cm.FLAG_DEBUG_COUNTS, cm.FLAG_GRAPH, cm.FLAG_WINDOW,
-                                                      cm.FLAG_NMI, cm.FLAG_WEIGHTED]
+                                                      cm.FLAG_NMI, cm.FLAG_WEIGHTED, cm.FLAG_AUTOTUNE,
+                                                      cm.FLAG_BATCH_ANGLES]
     assert int(out["fixbits"]) == cm.ENTROPY_FIX_BITS
     codes = [int(v) for v in out["status"].split()]
     assert codes == sorted(cm.STATUS_NAMES)

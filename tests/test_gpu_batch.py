@@ -189,3 +189,27 @@ def test_sharded_batch_single_rank_equals_direct(cm):
     batch.close()
     assert recs == cm.peaks_from_bytes(res, len(dev_pairs))
     assert stats == stat.cpu().tolist() == [0] * len(dev_pairs)
+
+
+def test_batch_with_batched_angles_and_autotune(cm, tmp_path, monkeypatch):
+    """A batch whose pairs run their angles as units of one launch per stage and
+    whose size classes were autotuned gives the same per-pair records as the plain
+    batch."""
+    monkeypatch.setenv("CMIF_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    cfg = synth.make_workload("uneven-batch-128pairs", scale=0.08)
+    pairs = cfg["pairs"][:6]
+    dev_pairs = [dict(A=_dev(p["A"]), M_A=_dev(p["M_A"]), B=_dev(p["B"]), M_B=_dev(p["M_B"]), K_A=p["K_A"],
+                      K_B=p["K_B"], angles=p["angles"], gamma=0.5) for p in pairs]
+    recs = []
+    for kw in ({}, {"batch_angles": True, "autotune": True}):
+        batch = cm.Batch(dev_pairs, cm.FP32, graph=True, **kw)
+        res = torch.empty(24 * len(dev_pairs), dtype=torch.uint8, device="cuda:0")
+        for _ in range(2):
+            res.zero_()
+            batch.run(res)
+            torch.cuda.synchronize()
+        assert batch.status()[0] == "OK"
+        recs.append(cm.peaks_from_bytes(res, len(dev_pairs)))
+        batch.close()
+    assert recs[0] == recs[1]
+    assert (tmp_path / "tune.jsonl").exists()

@@ -130,3 +130,64 @@ def test_sharded_entry_single_rank_equals_direct(cm):
     merged = shard.align_rotations_sharded(plan, A, None, B, None, angles, 0.5, 5)
     assert merged == direct
     plan.close()
+
+
+@pytest.mark.parametrize("window", [False, True])
+def test_batched_angles_equal_angle_by_angle(cm, window, monkeypatch):
+    """CMIF_FLAG_BATCH_ANGLES: the angles run as units of one launch per stage
+    (chunks of at most 5 here, so 16 angles take 5 + 5 + 5 + 1); maps, N maps and
+    the top-k equal the angle-by-angle run bit for bit, with unequal image sizes
+    and label counts."""
+    monkeypatch.setenv("CMIF_ANGLE_BATCH", "5")
+    rng = np.random.default_rng(77)
+    HA, WA, HB, WB, KA, KB = 70, 90, 61, 77, 6, 9
+    A = synth.make_field(rng, HA, WA, 60, KA).image(HA, WA)
+    B = synth.make_field(rng, HB, WB, 50, KB).image(HB, WB)
+    MB = (rng.random((HB, WB)) > 0.1).astype(np.uint8)
+    angles = np.linspace(0.0, 2 * math.pi, 16, endpoint=False) + 0.1
+    R, C = HA + HB - 1, WA + WB - 1
+    out = []
+    for batched in (False, True):
+        plan = cm.Plan(HA, WA, HB, WB, KA, KB, cm.FP32, window=window, batch_angles=batched)
+        maps = torch.full((16, R, C), float("nan"), dtype=torch.float64, device="cuda:0")
+        nmaps = torch.full((16, R, C), -1, dtype=torch.int32, device="cuda:0")
+        top = torch.zeros(24 * 16, dtype=torch.uint8, device="cuda:0")
+        plan.align_rotations(_dev(A), None, _dev(B), _dev(MB), angles, 0.5, 16, top, maps, n_maps=nmaps)
+        st = plan.status()
+        assert st[0] == "OK", st
+        out.append((maps, nmaps, top))
+        plan.close()
+    assert torch.equal(out[0][1], out[1][1])
+    assert torch.equal(torch.nan_to_num(out[0][0], nan=-7.0), torch.nan_to_num(out[1][0], nan=-7.0))
+    assert torch.equal(out[0][2], out[1][2])
+
+
+def test_batched_angles_vs_oracle(cm):
+    """Batched angles at 96^2 (the rotation workload scaled down), 16 angles in one
+    launch per stage: every map equals the oracle's on the device-warped B."""
+    cfg = synth.make_workload("rotation-512x512-K16-64angles", scale=96 / 512)
+    A, B = cfg["A"], cfg["B"]
+    H, W = A.shape
+    angles = cfg["angles"][::4]
+    n_ang = len(angles)
+    R, C = 2 * H - 1, 2 * W - 1
+    plan = cm.Plan(H, W, H, W, 16, 16, cm.FP32, batch_angles=True)
+    maps = torch.empty((n_ang, R, C), dtype=torch.float64, device="cuda:0")
+    nmaps = torch.empty((n_ang, R, C), dtype=torch.int32, device="cuda:0")
+    topk = torch.empty(24 * n_ang, dtype=torch.uint8, device="cuda:0")
+    plan.align_rotations(_dev(A), None, _dev(B), None, angles, 0.5, n_ang, topk, maps, n_maps=nmaps)
+    assert plan.status()[0] == "OK"
+    gm, gn = maps.cpu().numpy(), nmaps.cpu().numpy()
+    per = []
+    for i, th in enumerate(angles):
+        wB, wM = _warp_dev(cm, B, None, th)
+        ref = oracle.cmif(A, None, wB, wM, 16, 16)
+        np.testing.assert_array_equal(gn[i], ref["n"])
+        assert float(np.abs(gm[i] - ref["mi"]).max()) <= MI_TOL
+        per.append((ref["mi"], ref["n"]))
+    best, top = oracle.align(per, 0.5, top_k=n_ang)
+    got = cm.peaks_from_bytes(topk, n_ang)
+    assert got[0][0] == best[0]
+    for (ga, gdy, gdx, gnn, gmi), (ra, ridx, rmi, rn) in zip(got, top):
+        assert abs(gmi - rmi) <= MI_TOL
+    plan.close()
