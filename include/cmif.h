@@ -133,8 +133,11 @@ cmif_status cmif_plan_create(cmif_plan* out, int H, int W, int K_A, int K_B, cmi
 
 /* Create a plan (Sec. 3.1: domains X_A, X_B rectangular, any sizes).
  *   H_A, W_A, H_B, W_B >= 1, H*W <= 2^22 per image; 1 <= K_A, K_B <= 64;
- *   the transform sizes P >= H_A+H_B-1 and Q >= W_A+W_B-1 (powers of two)
- *   must not exceed 4096 (else CMIF_ERR_UNSUPPORTED).
+ *   the transform sizes P >= H_A+H_B-1 and Q >= W_A+W_B-1 must not exceed
+ *   4096 (else CMIF_ERR_UNSUPPORTED).  They are the smallest powers of two
+ *   (at least 16) or, for CMIF_FP32 plans, the smallest 3 * 2^k (96 .. 3072)
+ *   when that is smaller (CMIF_POW2_ONLY=1 in the environment at creation
+ *   keeps powers of two); the counts and MI do not depend on the choice.
  *   prec: see cmif_precision.  flags: CMIF_FLAG_*.
  * Allocates the workspace on the current CUDA device, which becomes the
  * plan's device.  On error *out is NULL.  The environment variable

@@ -61,6 +61,16 @@ int pow2_at_least(int v, int lo) {
     return p;
 }
 
+// Transform length for n outputs: the smallest power of two >= max(n, 16), or,
+// for FP32 transforms, the smallest 3 * 2^k (96 .. 3072) if that is smaller.
+int transform_size(int n, bool mixed) {
+    int best = pow2_at_least(n, 16);
+    if (mixed)
+        for (int t = 96; t <= 3072; t <<= 1)
+            if (t >= n && t < best) best = t;
+    return best;
+}
+
 }  // namespace
 
 struct cmif_plan_s {
@@ -457,8 +467,12 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     g.R2 = H_A + H_B - 1;
     g.R = g.Dz * g.R2;
     g.C = W_A + W_B - 1;
-    g.P = pow2_at_least(g.R2, 16);
-    g.Q = pow2_at_least(g.C, 16);
+    // FP32 plans may take lengths 3 * 2^k (the two-term and FP64 kernels, and hence
+    // AUTO's second precision, exist for powers of two only)
+    const char* p2e = std::getenv("CMIF_POW2_ONLY");
+    const bool mixed = prec == CMIF_FP32 && !(p2e && p2e[0] == '1');
+    g.P = transform_size(g.R2, mixed);
+    g.Q = transform_size(g.C, mixed);
     if (g.P > 4096 || g.Q > 4096) return CMIF_ERR_UNSUPPORTED;
     g.Qh = g.Q / 2 + 1;
     g.Qs = (int)align_up((size_t)g.Qh, 4);

@@ -126,13 +126,61 @@ __device__ __forceinline__ void dft_reg(cpx<T> (&v)[M]) {
 
 namespace cmif {
 
-// Lanes per group for a team transform: the largest power of two M with
-// M*M <= N, capped so that M complex values fit in registers (32 for FP32,
-// 16 for FP64).
+// Lanes per group for a team transform: the largest power of two M with M*M
+// dividing N (N = R M^2; for N = 2^k or 3 * 2^k), capped so that M complex
+// values fit in registers (32 for FP32, 16 for FP64).
 __host__ __device__ constexpr int team_m(int N, int mmax) {
     int M = mmax;
-    while (M > 1 && M * M > N) M >>= 1;
+    while (M > 1 && (M * M > N || N % (M * M) != 0)) M >>= 1;
     return M;
+}
+__host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// In-register R-point DFT with the output in natural order: u[q] = sum_s u_in[s]
+// e^{DIR 2 pi i s q / R}.  Powers of two by the radix-2 network (the bit-reversed
+// output renamed), R = 3 directly, R = 6 as two 3-point DFTs and a radix-2 step.
+template <int DIR, typename T>
+__device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
+    // X0 = a + b + c; X1,2 = a - (b + c)/2 -+ DIR i (sqrt(3)/2) (b - c) ... with the sign of DIR
+    const T h = T(0.5), s3 = T(0.86602540378443864676);
+    const cpx<T> t = {b.x + c.x, b.y + c.y}, d = {b.x - c.x, b.y - c.y};
+    const cpx<T> m = {a.x - h * t.x, a.y - h * t.y};
+    const cpx<T> id = {-s3 * d.y, s3 * d.x};  // i sqrt(3)/2 (b - c)
+    a = {a.x + t.x, a.y + t.y};
+    if (DIR > 0) {
+        b = {m.x + id.x, m.y + id.y};
+        c = {m.x - id.x, m.y - id.y};
+    } else {
+        b = {m.x - id.x, m.y - id.y};
+        c = {m.x + id.x, m.y + id.y};
+    }
+}
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_nat(cpx<T> (&u)[R]) {
+    if constexpr (R == 3) {
+        dft3<DIR>(u[0], u[1], u[2]);
+    } else if constexpr (R == 6) {
+        // E = DFT3(u0, u2, u4), O = DFT3(u1, u3, u5); X[k] = E[k] + w6^k O[k], X[k+3] = E[k] - w6^k O[k]
+        cpx<T> e0 = u[0], e1 = u[2], e2 = u[4], o0 = u[1], o1 = u[3], o2 = u[5];
+        dft3<DIR>(e0, e1, e2);
+        dft3<DIR>(o0, o1, o2);
+        const T h = T(0.5), s3 = T(0.86602540378443864676);
+        const cpx<T> w1 = {h, DIR * s3}, w2 = {-h, DIR * s3};
+        o1 = cmul(o1, w1);
+        o2 = cmul(o2, w2);
+        u[0] = e0 + o0; u[3] = e0 - o0;
+        u[1] = e1 + o1; u[4] = e1 - o1;
+        u[2] = e2 + o2; u[5] = e2 - o2;
+    } else {
+        static_assert(is_pow2(R), "R-point DFT: powers of two, 3 and 6");
+        cpx<T> t[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) t[i] = u[i];
+        dft_reg<R, DIR>(t);
+#pragma unroll
+        for (int q = 0; q < R; ++q) u[q] = t[brev(q, R)];
+    }
 }
 template <typename T>
 __host__ __device__ constexpr int max_m() { return sizeof(T) == 4 ? 32 : 16; }  // FP32: 32; FP64 and two-term FP32: 16
@@ -140,11 +188,21 @@ __host__ __device__ constexpr int max_m() { return sizeof(T) == 4 ? 32 : 16; }  
 // Twiddle tables in device memory, filled once per device from FP64 values.
 //   n[l][k]         = e^{-2 pi i k / 2^l},           k < 2^l
 //   sq[l][k1*M + j] = e^{-2 pi i j k1 / (M*M)},       M = 2^l, j, k1 < M
+//   n3[l][k]        = e^{-2 pi i k / (3 2^l)},       k < 3 2^l
 template <typename T>
 struct Tw {
     const cpx<T>* n[14];
     const cpx<T>* sq[6];
+    const cpx<T>* n3[12];
 };
+
+// The table of e^{-2 pi i k / N} for a transform length N = 2^l or 3 2^l.
+__host__ __device__ constexpr int ilog2_of(int n) { return n <= 1 ? 0 : 1 + ilog2_of(n >> 1); }
+template <int N, typename T>
+__device__ __forceinline__ const cpx<T>* tw_of(const Tw<T>& tw) {
+    if constexpr (N % 3 == 0) return tw.n3[ilog2_of(N / 3)];
+    else return tw.n[ilog2_of(N)];
+}
 
 template <int DIR, typename T>
 __device__ __forceinline__ cpx<T> twl(const cpx<T>* __restrict__ t, int k) {
@@ -243,7 +301,32 @@ template <int M, int R, int DIR, bool PACK = true, typename T, typename Load>
 __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
                                          const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
     constexpr int NQ = M * M;
-    if constexpr (R > 2) {
+    if constexpr (R > 2 && !is_pow2(R)) {
+        // Radix-R decimation in frequency (R = 3, 6) with every input loaded once: the
+        // team's lanes l = r M + j take the points m = l + TEAM t, form the R-point DFT
+        // of x[m + s NQ], s < R, twiddle frequency q by w_N^{m q} and hand it to group q
+        // through the team's buffer (as in the power-of-two case below).
+        constexpr int TEAM = R * M, PTS = (NQ + TEAM - 1) / TEAM;
+        cpx<T>* xs = reinterpret_cast<cpx<T>*>(reinterpret_cast<char*>(sm) - r * grp_scratch_bytes<T, M>());
+        const int lt = r * M + j;
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < PTS; ++t) {
+            const int m = lt + TEAM * t;
+            if (PTS * TEAM == NQ || m < NQ) {
+                cpx<T> u[R];
+#pragma unroll
+                for (int s2 = 0; s2 < R; ++s2) u[s2] = load(m + s2 * NQ);
+                dft_nat<R, DIR>(u);
+#pragma unroll
+                for (int q = 0; q < R; ++q) xs[q * NQ + m] = q ? cmul(u[q], twl<DIR>(twn, m * q)) : u[q];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = xs[r * NQ + j + M * i];
+        __syncthreads();
+    } else if constexpr (R > 2) {
         // Radix-R decimation in frequency with every input loaded once: lane (r, j)
         // takes the points m = j + M (r PER + t), t < PER, forms the R-point DFT of
         // x[m + s NQ], s < R, in registers, twiddles frequency q by w_N^{m q} and

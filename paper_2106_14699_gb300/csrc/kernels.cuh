@@ -127,6 +127,8 @@ __device__ __forceinline__ int circ_to_out(int s, int n, int lo_count /*H_A or W
 
 // ---------------------------------------------------------------------------
 // Team geometry for a transform of length N in precision T.
+__host__ __device__ constexpr int pow2_floor(int n) { return n < 2 ? 1 : 2 * pow2_floor(n / 2); }
+
 // MMAX caps the lanes per group (and the values per lane): the default is the
 // register budget of T; a smaller one trades a radix-R step for more warps.
 template <typename T, int N, int MMAX = max_m<T>()>
@@ -233,7 +235,7 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const 
         return {c == la ? one : T(0), c == lb ? one : T(0)};
     };
     cpx<T> v[M];
-    team_fft<M, R, -1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)], tw.n[ilog2c(Q)]);
+    team_fft<M, R, -1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)], tw_of<Q>(tw));
     __syncthreads();
 #pragma unroll
     for (int k2 = 0; k2 < M; ++k2) sm[R * (j + M * k2) + r] = v[brev(k2, M)];
@@ -241,7 +243,7 @@ k_fwd_rows(const int32_t* __restrict__ X, const uint8_t* __restrict__ MX, const 
     if (!active) return;
     const T h = T(0.5);
     for (int k = lt; k <= Q / 2; k += C::TEAM) {
-        const cpx<T> a = sm[k], b = sm[(Q - k) & (Q - 1)];
+        const cpx<T> a = sm[k], b = sm[k == 0 ? 0 : Q - k];
         // F_la = (X[k] + conj X[-k]) / 2,  F_lb = (X[k] - conj X[-k]) / (2i)
         T1[((size_t)la * H + y) * Qs + k] = {h * (a.x + b.x), h * (a.y - b.y)};
         if (lb < K) T1[((size_t)lb * H + y) * Qs + k] = {h * (a.y + b.y), h * (b.x - a.x)};
@@ -257,7 +259,7 @@ template <typename T, int P, int MMAX = max_m<T>()>
 struct ColCfg {
     using G = TeamGeom<T, P, MMAX>;
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
-    static constexpr int TPB = TEAM >= 256 ? 1 : 256 / TEAM;
+    static constexpr int TPB = TEAM >= 256 ? 1 : pow2_floor(256 / TEAM);  // a power of two (swizzle)
     static constexpr int THREADS = TPB * TEAM;
     static constexpr int SWZ = TPB >= 16 ? 0 : (TPB == 8 ? 1 : (TPB == 4 ? 2 : 3));
     static constexpr size_t SCR = (size_t)TPB * G::SCRATCH;
@@ -308,7 +310,7 @@ k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cp
     };
     cpx<T> v[M];
     team_fft<M, R, -1>(v, r, j, load, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(),
-                       tw.sq[ilog2c(M)], tw.n[ilog2c(P)]);
+                       tw.sq[ilog2c(M)], tw_of<P>(tw));
     if (!active) return;
     // Column ky is stored at slot (ky % R) * M*M + ky / R: the samples that one
     // group of the pair-product transform (same P, same R) takes are contiguous.
@@ -351,10 +353,11 @@ struct PairColsCfg {
     using G = TeamGeom<T, P, MMAX>;
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM, NQ = M * M;
     // at least 256 threads, and at least 32 bytes of adjacent kx per tile row (whole sectors)
-    static constexpr int TPB0 = TEAM >= 256 ? 1 : 256 / TEAM;
+    static constexpr int TPB0 = TEAM >= 256 ? 1 : pow2_floor(256 / TEAM);  // a power of two (swizzle)
     static constexpr int TPB = TPB0 * (int)sizeof(cpx<T>) >= 32 ? TPB0 : 32 / (int)sizeof(cpx<T>);
     static constexpr int THREADS = TPB * TEAM;
-    static constexpr int PER = R > 2 ? M / R : 1;  // points per lane of the radix-R combine
+    static constexpr int PER = R > 2 ? M / R : 1;  // points per lane of the radix-R combine (R a power of two)
+    static constexpr int PTS = (NQ + TEAM - 1) / TEAM;  // points per lane of the radix-3/6 combine
     static constexpr int SWZ = TPB >= 16 ? 0 : (TPB == 8 ? 1 : (TPB == 4 ? 2 : 3));
     // one buffer per block: the teams' group-transform exchange, then the P x TPB output tile
     static constexpr size_t XBUF = (size_t)TPB * P * sizeof(cpx<T>);
@@ -363,7 +366,7 @@ struct PairColsCfg {
     static constexpr int TW_N = R == 2 ? P / 2 : (R > 2 ? P : 0);  // combine twiddles W_P^k
     static constexpr size_t SMEM = MAIN + (size_t)(NQ + TW_N) * sizeof(cpx<T>);
     // FP32: two blocks per SM (M = 32 needs 128 registers a thread, so 256 threads)
-    static constexpr int MIN_BLOCKS = sizeof(T) == 4 && (M < 32 || THREADS <= 256) ? 2 : 1;
+    static constexpr int MIN_BLOCKS = sizeof(T) == 4 && (M < 32 ? is_pow2(R) && THREADS <= 512 : THREADS <= 256) ? 2 : 1;
 };
 
 // Pair product + inverse column transform of length P = R*M*M.  Persistent
@@ -416,7 +419,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     // that the items in flight stay within a few kx blocks whatever the blocks' pace.
     if (threadIdx.x == 0) s_item = atomicAdd(work_ctr, 1);
     stage_table(tw_sq, tw.sq[ilog2c(M)], NQ);
-    if (R > 1) stage_table(tw_n, tw.n[ilog2c(P)], C::TW_N);
+    if (R > 1) stage_table(tw_n, tw_of<P>(tw), C::TW_N);
     __syncthreads();
     int item = s_item;
     if (item >= n_items) return;
@@ -425,6 +428,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
     // r*NQ (the forward column transform's output order).  conj(F_a) F_b, F_b
     // carrying the 1/(P Q) of the inverse.
     cpx<T> v[M];
+    cpx<T> wo[(R > 2 && !is_pow2(R)) ? C::PTS * R : 1];  // outputs of the radix-3/6 combine
     auto load_fa = [&](int it) {
         if constexpr (VOL) return;  // volumes sum over slices in the item itself
         const int kx = (VOL ? it / npairs / U : (it / npairs) % nkxb) * TPB + team, a = real_pair(it % npairs) / KB;
@@ -498,6 +502,29 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                 const int k = j + M * k2;
                 v[brev(k2, M)] = r == 0 ? v[brev(k2, M)] + tx[NQ + k] : tx[k] - v[brev(k2, M)];
             }
+        } else if constexpr (R > 2 && !is_pow2(R)) {
+            // R = 3, 6: as below, with the team's lanes l = r M + j taking the points
+            // k = l + TEAM t (the outputs stay in wo[] until the exchange reads are done)
+            __syncthreads();  // every group is done with its transpose scratch (aliases xbuf)
+#pragma unroll
+            for (int k2 = 0; k2 < M; ++k2) {
+                const int k = j + M * k2;
+                const cpx<T> e = v[brev(k2, M)];
+                tx[r * NQ + k] = r ? cmul(e, twl<+1>(tw_n, r * k)) : e;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < C::PTS; ++t) {
+                const int k = lt + C::TEAM * t;
+                if (C::PTS * C::TEAM == NQ || k < NQ) {
+                    cpx<T> u[R];
+#pragma unroll
+                    for (int s2 = 0; s2 < R; ++s2) u[s2] = tx[s2 * NQ + k];
+                    dft_nat<R, +1>(u);
+#pragma unroll
+                    for (int q = 0; q < R; ++q) wo[t * R + q] = u[q];
+                }
+            }
         } else if constexpr (R > 2) {
             // X[k + q NQ] = sum_s w_R^{sq} (W^{sk} E_s[k]) (W = W_P, inverse direction): group
             // s twiddles its own values, the team exchanges them through shared memory, and
@@ -524,18 +551,32 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
         }
         __syncthreads();  // exchange reads done: the buffer becomes the tile
         // tile slot (row, team) swizzled by row
+        if constexpr (R > 2 && !is_pow2(R)) {
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-            int row;
-            cpx<T> val;
-            if constexpr (R > 2) {
-                row = j + M * (r * C::PER + i / R) + (i % R) * NQ;
-                val = v[i];
-            } else {
-                row = r * NQ + j + M * i;
-                val = v[brev(i, M)];
+            for (int t = 0; t < C::PTS; ++t) {
+                const int k = lt + C::TEAM * t;
+                if (C::PTS * C::TEAM == NQ || k < NQ) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        const int row = k + q * NQ;
+                        xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = wo[t * R + q];
+                    }
+                }
             }
-            xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = val;
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                int row;
+                cpx<T> val;
+                if constexpr (R > 2) {
+                    row = j + M * (r * C::PER + i / R) + (i % R) * NQ;
+                    val = v[i];
+                } else {
+                    row = r * NQ + j + M * i;
+                    val = v[brev(i, M)];
+                }
+                xbuf[(size_t)row * TPB + (team ^ ((row >> C::SWZ) & (TPB - 1)))] = val;
+            }
         }
         __syncthreads();
         next = s_item;
@@ -661,7 +702,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
     unsigned char* region = smem_raw + (size_t)team * C::REGION;
     const int KA = g.KA, KB = g.KB, npairs = KA * KB, Rout = g.R, Cout = g.C, Qs = g.Qs;
     const size_t RC = (size_t)Rout * Cout;
-    const cpx<T>* twq_c2r = tw.n[ilog2c(Q)];
+    const cpx<T>* twq_c2r = tw_of<Q>(tw);
     float res_max = 0.f;
     int row_max_n = 0;
 
@@ -699,7 +740,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
             };
             cpx<T> v[M];
             team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)],
-                               tw.n[ilog2c(L)]);
+                               tw_of<L>(tw));
             // round to the nearest integer; track the worst residual (the exactness guard)
             float rp = 0.f;
 #pragma unroll
@@ -844,7 +885,7 @@ k_pair_rows_counts(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, const int* __
     unsigned char* region = smem_raw + (size_t)team * C::G::SCRATCH;
     const int nrows = g.r1 - g.r0;
     const long long ntask = (long long)np * nrows;
-    const cpx<T>* twq_c2r = tw.n[ilog2c(Q)];
+    const cpx<T>* twq_c2r = tw_of<Q>(tw);
     float res = 0.f;
     // a uniform trip count per block: every lane of a warp takes part in each transform's warp syncs
     for (long long t0 = (long long)blockIdx.x * NT; t0 < ntask; t0 += (long long)gridDim.x * NT) {
@@ -863,7 +904,7 @@ k_pair_rows_counts(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, const int* __
         };
         cpx<T> v[M];
         team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<T, M>(), tw.sq[ilog2c(M)],
-                           tw.n[ilog2c(L)]);
+                           tw_of<L>(tw));
         if (act) {
             int32_t* o = ov + ((size_t)(lbase + e) * g.R + row) * Q;
 #pragma unroll
@@ -916,7 +957,7 @@ k_pair_rows_w(const cpx<double>* __restrict__ Y, Geom g, Tw<double> tw, double* 
     unsigned char* region = smem_raw + (size_t)team * C::REGION;
     const int KB = g.KB, npairs = g.KA * g.KB, Rout = g.R, Cout = g.C, Qs = g.Qs;
     double* cb = cbw + (size_t)blockIdx.x * KB * Q;
-    const cpx<double>* twq_c2r = tw.n[ilog2c(Q)];
+    const cpx<double>* twq_c2r = tw_of<Q>(tw);
     double row_max_n = 0.0;
     for (int row = g.r0 + blockIdx.x; row < g.r1; row += gridDim.x) {
         double S[U], CA[U], N[U];
@@ -944,7 +985,7 @@ k_pair_rows_w(const cpx<double>* __restrict__ Y, Geom g, Tw<double> tw, double* 
             };
             cpx<double> v[M];
             team_fft<M, R, +1>(v, r, j, load, region + r * grp_scratch_bytes<double, M>(), tw.sq[ilog2c(M)],
-                               tw.n[ilog2c(L)]);
+                               tw_of<L>(tw));
             __syncthreads();  // all transforms done with their scratch
             double2* ob = reinterpret_cast<double2*>(region);
 #pragma unroll

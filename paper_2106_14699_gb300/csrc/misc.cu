@@ -480,7 +480,13 @@ static void host_twiddle(long long k, long long N, double* c, double* s) {
         *s = 0.0;
         return;
     }
-    const long long q4 = N / 4;  // N is a power of two >= 4
+    if (N % 4 != 0) {  // N = 3, 6
+        const double t = 2.0 * M_PI * (double)k / (double)N;
+        *c = std::cos(t);
+        *s = -std::sin(t);
+        return;
+    }
+    const long long q4 = N / 4;  // N = 2^l or 3 2^l, divisible by 4
     const long long qd = k / q4, r = k - qd * q4;
     double cu, su;
     if (2 * r <= q4) {
@@ -503,7 +509,7 @@ static void host_twiddle(long long k, long long N, double* c, double* s) {
     *s = -ss;  // e^{-i t}
 }
 
-void twiddle_table_f32(std::vector<float>& out, size_t off_n[14], size_t off_sq[6]) {
+void twiddle_table_f32(std::vector<float>& out, size_t off_n[14], size_t off_sq[6], size_t off_n3[12]) {
     out.clear();
     size_t n = 0;
     for (int l = 0; l < 14; ++l) {
@@ -527,6 +533,16 @@ void twiddle_table_f32(std::vector<float>& out, size_t off_n[14], size_t off_sq[
                 out.push_back((float)s);
             }
     }
+    for (int l = 0; l < 12; ++l) {
+        off_n3[l] = n;
+        const long long N = 3LL << l;
+        for (long long k = 0; k < N; ++k, ++n) {
+            double c, s;
+            host_twiddle(k, N, &c, &s);
+            out.push_back((float)c);
+            out.push_back((float)s);
+        }
+    }
 }
 
 struct DevTables {
@@ -547,7 +563,7 @@ cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td, Tw<df32>* ts
         // layout: for l = 0..13 the N = 2^l tables, then for l = 0..5 the (2^l)^2 square tables;
         // first all FP64, then all FP32.
         std::vector<double> re, im;
-        std::vector<size_t> off_n(14), off_sq(6);
+        std::vector<size_t> off_n(14), off_sq(6), off_n3(12);
         for (int l = 0; l < 14; ++l) {
             off_n[l] = re.size();
             const long long N = 1LL << l;
@@ -568,6 +584,16 @@ cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td, Tw<df32>* ts
                     re.push_back(c);
                     im.push_back(s);
                 }
+        }
+        for (int l = 0; l < 12; ++l) {
+            off_n3[l] = re.size();
+            const long long N = 3LL << l;
+            for (long long k = 0; k < N; ++k) {
+                double c, s;
+                host_twiddle(k, N, &c, &s);
+                re.push_back(c);
+                im.push_back(s);
+            }
         }
         const size_t n = re.size();
         std::vector<double> hd(2 * n);
@@ -604,6 +630,7 @@ cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td, Tw<df32>* ts
         const cpx<df32>* bs = reinterpret_cast<const cpx<df32>*>((char*)buf + bytes_d + bytes_f);
         for (int l = 0; l < 14; ++l) { t.td.n[l] = bd + off_n[l]; t.tf.n[l] = bf + off_n[l]; t.ts.n[l] = bs + off_n[l]; }
         for (int l = 0; l < 6; ++l) { t.td.sq[l] = bd + off_sq[l]; t.tf.sq[l] = bf + off_sq[l]; t.ts.sq[l] = bs + off_sq[l]; }
+        for (int l = 0; l < 12; ++l) { t.td.n3[l] = bd + off_n3[l]; t.tf.n3[l] = bf + off_n3[l]; t.ts.n3[l] = bs + off_n3[l]; }
     }
     if (tf) *tf = t.tf;
     if (td) *td = t.td;

@@ -54,7 +54,7 @@ cudaError_t launch_entropy_terms(int c0, int n, long long* out, cudaStream_t s);
 cudaError_t launch_fill_labels(int32_t* X, long long n, int K, unsigned seed, cudaStream_t s);
 cudaError_t get_twiddles(int device, Tw<float>* tf, Tw<double>* td, Tw<df32>* ts);
 // Host copy of the FP32 twiddle tables (interleaved re, im) and the entry offsets
-// of each table, in the same layout get_twiddles() uploads.
-void twiddle_table_f32(std::vector<float>& out, size_t off_n[14], size_t off_sq[6]);
+// of each table (lengths 2^l, the (2^l)^2 squares, lengths 3 2^l).
+void twiddle_table_f32(std::vector<float>& out, size_t off_n[14], size_t off_sq[6], size_t off_n3[12]);
 
 }  // namespace cmif

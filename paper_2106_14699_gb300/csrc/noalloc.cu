@@ -51,14 +51,15 @@ cudaError_t setup(int device, NoAllocDevice** out) {
         e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
         std::vector<float> host;
-        size_t off_n[14], off_sq[6];
-        twiddle_table_f32(host, off_n, off_sq);
+        size_t off_n[14], off_sq[6], off_n3[12];
+        twiddle_table_f32(host, off_n, off_sq, off_n3);
         const size_t bytes = host.size() * sizeof(float);
         e = cudaMemcpy(ptr, host.data(), bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
         const cpx<float>* t = reinterpret_cast<const cpx<float>*>(ptr);
         for (int l = 0; l < 14; ++l) d.tw.n[l] = t + off_n[l];
         for (int l = 0; l < 6; ++l) d.tw.sq[l] = t + off_sq[l];
+        for (int l = 0; l < 12; ++l) d.tw.n3[l] = t + off_n3[l];
         d.tw_bytes = up256(bytes);
         d.base = reinterpret_cast<unsigned char*>(ptr);
     }

@@ -21,39 +21,39 @@ cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     constexpr bool split = std::is_same<T, df32>::value;
     const unsigned stg = a.stages ? a.stages : STAGE_ALL;
     if (stg & STAGE_FWD_A) {
-        CMIF_SIZE_SWITCH(g.Q, {
+        CMIF_SIZE_SWITCH_T(T, g.Q, {
             ProfScope ps(a.prof, f32 ? "fwd_rows_A_f32" : split ? "fwd_rows_A_s32" : "fwd_rows_A_f64", s);
             e = Sized<T, SZ>::fwd_rows(g, a, false, s);
         } if (e != cudaSuccess) return e);
-        CMIF_SIZE_SWITCH(g.P, {
+        CMIF_SIZE_SWITCH_T(T, g.P, {
             ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : split ? "fwd_cols_A_s32" : "fwd_cols_A_f64", s);
             e = Sized<T, SZ>::fwd_cols(g, a, false, s);
         } if (e != cudaSuccess) return e);
     }
     if (stg & STAGE_FWD_B) {
-        CMIF_SIZE_SWITCH(g.Q, {
+        CMIF_SIZE_SWITCH_T(T, g.Q, {
             ProfScope ps(a.prof, f32 ? "fwd_rows_B_f32" : split ? "fwd_rows_B_s32" : "fwd_rows_B_f64", s);
             e = Sized<T, SZ>::fwd_rows(g, a, true, s);
         } if (e != cudaSuccess) return e);
-        CMIF_SIZE_SWITCH(g.P, {
+        CMIF_SIZE_SWITCH_T(T, g.P, {
             ProfScope ps(a.prof, f32 ? "fwd_cols_B_f32" : split ? "fwd_cols_B_s32" : "fwd_cols_B_f64", s);
             e = Sized<T, SZ>::fwd_cols(g, a, true, s);
         } if (e != cudaSuccess) return e);
     }
     if (stg & STAGE_COLS) {
-        CMIF_SIZE_SWITCH(g.P, {
+        CMIF_SIZE_SWITCH_T(T, g.P, {
             ProfScope ps(a.prof, f32 ? "pair_cols_f32" : split ? "pair_cols_s32" : "pair_cols_f64", s);
             e = Sized<T, SZ>::pair_cols(g, a, s);
         } if (e != cudaSuccess) return e);
     }
     if (stg & STAGE_ROWS) {
         if (a.weighted) {
-            CMIF_SIZE_SWITCH(g.Q, {
+            CMIF_SIZE_SWITCH_T(T, g.Q, {
                 ProfScope ps(a.prof, "pair_rows_weighted_f64", s);
                 e = Sized<T, SZ>::pair_rows_w(g, a, s);
             } if (e != cudaSuccess) return e);
         } else {
-            CMIF_SIZE_SWITCH(g.Q, {
+            CMIF_SIZE_SWITCH_T(T, g.Q, {
                 ProfScope ps(a.prof, f32 ? "pair_rows_f32" : split ? "pair_rows_s32" : "pair_rows_f64", s);
                 e = Sized<T, SZ>::pair_rows(g, a, s);
             } if (e != cudaSuccess) return e);
@@ -83,7 +83,7 @@ template <typename T>
 size_t rows_smem_bytes(int Q, int KB, bool cb_smem) {
     size_t out = 0;
     auto f = [&]() -> cudaError_t {
-        CMIF_SIZE_SWITCH(Q, out = Sized<T, SZ>::rows_smem(KB, cb_smem));
+        CMIF_SIZE_SWITCH_T(T, Q, out = Sized<T, SZ>::rows_smem(KB, cb_smem));
         return cudaSuccess;
     };
     f();
@@ -94,7 +94,7 @@ template <typename T>
 int rows_threads(int Q) {
     int out = 0;
     auto f = [&]() -> cudaError_t {
-        CMIF_SIZE_SWITCH(Q, out = Sized<T, SZ>::rows_threads());
+        CMIF_SIZE_SWITCH_T(T, Q, out = Sized<T, SZ>::rows_threads());
         return cudaSuccess;
     };
     f();
@@ -103,14 +103,14 @@ int rows_threads(int Q) {
 
 template <typename T>
 cudaError_t rows_max_blocks_per_sm(int Q, int KB, bool cb_smem, int* out) {
-    CMIF_SIZE_SWITCH(Q, return Sized<T, SZ>::rows_max_blocks(KB, cb_smem, out));
+    CMIF_SIZE_SWITCH_T(T, Q, return Sized<T, SZ>::rows_max_blocks(KB, cb_smem, out));
     return cudaSuccess;
 }
 
 int rows_tm_cols(int Q, int KB) {
     int out = 0;
     auto f = [&]() -> cudaError_t {
-        CMIF_SIZE_SWITCH(Q, out = Sized<float, SZ>::tm_cols(KB));
+        CMIF_SIZE_SWITCH_T(float, Q, out = Sized<float, SZ>::tm_cols(KB));
         return cudaSuccess;
     };
     f();
@@ -125,7 +125,7 @@ cudaError_t rows_w_max_blocks_per_sm(int Q, int* out) {
 
 cudaError_t rows_tm_max_blocks_per_sm(int Q, int* out) {
     *out = 0;
-    CMIF_SIZE_SWITCH(Q, return Sized<float, SZ>::tm_max_blocks(out));
+    CMIF_SIZE_SWITCH_T(float, Q, return Sized<float, SZ>::tm_max_blocks(out));
     return cudaSuccess;
 }
 

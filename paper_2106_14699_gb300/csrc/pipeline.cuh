@@ -1,6 +1,7 @@
 // Launch sequence of one CMIF map for one precision (FP32 or FP64 transforms).
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 #include "kernels.cuh"
 #include "profiler.h"
 
@@ -68,7 +69,38 @@ enum : unsigned {
     STAGE_ALL = 15u,
 };
 
-// The transform sizes the kernels are compiled for (P, Q = 16 .. 4096).
+// The transform sizes the kernels are compiled for: P, Q = 2^k (16 .. 4096) in
+// every precision, and 3 * 2^k (96 .. 3072) for FP32 transforms.
+template <typename T>
+constexpr bool kMixedSizes = std::is_same<T, float>::value;
+#define CMIF_MIXED_CASE(TT, V, ...)                                   \
+    case V: {                                                          \
+        constexpr int SZ = V;                                          \
+        if constexpr (kMixedSizes<TT>) { __VA_ARGS__; }                \
+        else { return cudaErrorInvalidValue; }                         \
+    } break;
+// Power-of-two sizes and, for FP32 (TT = float), the 3 * 2^k ones.
+#define CMIF_SIZE_SWITCH_T(TT, N, ...)                                \
+    switch (N) {                                                      \
+        case 16: { constexpr int SZ = 16; __VA_ARGS__; } break;     \
+        case 32: { constexpr int SZ = 32; __VA_ARGS__; } break;     \
+        case 64: { constexpr int SZ = 64; __VA_ARGS__; } break;     \
+        case 128: { constexpr int SZ = 128; __VA_ARGS__; } break;   \
+        case 256: { constexpr int SZ = 256; __VA_ARGS__; } break;   \
+        case 512: { constexpr int SZ = 512; __VA_ARGS__; } break;   \
+        case 1024: { constexpr int SZ = 1024; __VA_ARGS__; } break; \
+        case 2048: { constexpr int SZ = 2048; __VA_ARGS__; } break; \
+        case 4096: { constexpr int SZ = 4096; __VA_ARGS__; } break; \
+        CMIF_MIXED_CASE(TT, 96, __VA_ARGS__)                          \
+        CMIF_MIXED_CASE(TT, 192, __VA_ARGS__)                         \
+        CMIF_MIXED_CASE(TT, 384, __VA_ARGS__)                         \
+        CMIF_MIXED_CASE(TT, 768, __VA_ARGS__)                         \
+        CMIF_MIXED_CASE(TT, 1536, __VA_ARGS__)                        \
+        CMIF_MIXED_CASE(TT, 3072, __VA_ARGS__)                        \
+        default: return cudaErrorInvalidValue;                        \
+    }
+
+// The power-of-two transform sizes (P, Q = 16 .. 4096).
 #define CMIF_SIZE_SWITCH(N, ...)                                     \
     switch (N) {                                                      \
         case 16: { constexpr int SZ = 16; __VA_ARGS__; } break;     \

@@ -11,7 +11,7 @@ namespace cmif {
 
 // Sizes with the 16-lane variant of the column transforms (FP32 only).
 template <typename T, int SZ>
-constexpr bool kHasColVariant = std::is_same<T, float>::value && SZ >= 1024;
+constexpr bool kHasColVariant = std::is_same<T, float>::value && SZ >= 1024 && is_pow2(SZ);
 
 // Opt the kernel in to `bytes` of dynamic shared memory.  Without the attribute,
 // static plus dynamic shared memory must stay within 48 KB, so a kernel with a

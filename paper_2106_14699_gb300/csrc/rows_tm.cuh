@@ -184,8 +184,8 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
     cpx<float>* twq_c2r = tw_sq + C::NQ;
     cpx<float>* tw_pre = twq_c2r + L;
     stage_table(tw_sq, tw.sq[ilog2c(M)], C::NQ);
-    stage_table(twq_c2r, tw.n[ilog2c(Q)], L);
-    if (R > 1) stage_table(tw_pre, tw.n[ilog2c(L)], C::TW_PRE);
+    stage_table(twq_c2r, tw_of<Q>(tw), L);
+    if (R > 1) stage_table(tw_pre, tw_of<L>(tw), C::TW_PRE);
 
     if (tid == 0) s_abort = 0;
     if (lane == 0) mbar_init(bar, 1);

@@ -47,5 +47,5 @@ def test_autotune_keeps_results_and_caches(cm, tmp_path, H, K):
     assert again["from_cache"] == 1 and again["col_lanes"] == t["col_lanes"]
     if t["from_cache"] == 0:
         line = json.loads(cache.read_text().strip().splitlines()[-1])
-        assert line["key"].startswith(f"P{1 << (R - 1).bit_length()}.") and line["col_m"] in (0, 16)
+        assert line["key"].startswith("P") and f".KA{K}.KB{K}." in line["key"] and line["col_m"] in (0, 16)
     plan.close()

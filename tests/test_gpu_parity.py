@@ -331,3 +331,44 @@ def test_max_transform_size_sampled(cm):
     print(f"[mi-error] 2048^2 K=4 AUTO sampled max|dMI|={err:.3e} status={g['status']}")
     assert err <= MI_TOL, err
     assert tuple(g["peak"][1:3]) == (37, -101)
+
+
+# Shapes whose output ranges pick transform lengths 3 * 2^k (96 .. 3072) in FP32 plans:
+# (H_A, W_A, H_B, W_B, K_A, K_B) -> P x Q
+MIXED = [(40, 50, 41, 47, 5, 6),        # 96 x 96
+         (70, 100, 90, 60, 4, 3),       # 192 x 192
+         (150, 20, 140, 30, 3, 4),      # 384 x 64
+         (8, 300, 9, 400, 5, 5),        # 16 x 768
+         (5, 700, 4, 800, 3, 3),        # 16 x 1536
+         (3, 1100, 4, 1200, 2, 2),      # 16 x 3072
+         (1300, 3, 1200, 2, 2, 3)]      # 3072 x 16
+
+
+@pytest.mark.parametrize("shape", MIXED, ids=lambda s: "x".join(map(str, s)))
+def test_mixed_radix_lengths_exact(cm, shape):
+    """FP32 plans take transform lengths 3 * 2^k (radix-3 and radix-6 steps) when
+    they are shorter than the next power of two; counts stay bit-exact."""
+    rng = np.random.default_rng(sum(shape) * 3)
+    A, MA, B, MB = _rand(rng, *shape)
+    check_exact(cm, A, MA, B, MB, shape[4], shape[5], cm.FP32, gamma=0.3)
+
+
+def test_mixed_radix_equals_power_of_two(cm, monkeypatch):
+    """A 768^2 pair (output range 1535: length 1536 instead of 2048): the same N and
+    MI as the power-of-two plan, bit for bit (MI comes from exact integer sums),
+    and the oracle's values at sampled shifts."""
+    rng = np.random.default_rng(768)
+    H, K = 768, 8
+    A, B = synth.planted_pair(rng, H, H, 900, K, K, (31, -17), 0.1, same_labels=True)
+    outs = []
+    for pow2 in (False, True):
+        if pow2:
+            monkeypatch.setenv("CMIF_POW2_ONLY", "1")
+        g = run_gpu(cm, A, None, B, None, K, K, cm.FP32, counts=False, gamma=0.5)
+        assert g["status"][0] == "OK", g["status"]
+        outs.append(g)
+    assert np.array_equal(outs[0]["n"], outs[1]["n"]) and np.array_equal(outs[0]["mi"], outs[1]["mi"])
+    dys, dxs = _sample_shifts(rng, H, H, H, H, 48, extra=[(31, -17)])
+    ref = oracle.cmif_at(A, None, B, None, K, K, dys, dxs)
+    np.testing.assert_array_equal(outs[0]["n"][dys + H - 1, dxs + H - 1], ref["n"])
+    assert float(np.abs(outs[0]["mi"][dys + H - 1, dxs + H - 1] - ref["mi"]).max()) <= MI_TOL
