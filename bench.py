@@ -364,10 +364,13 @@ class TorchFFTPlain:
     """Comparison baseline, not this library: the plain frequency-domain form of
     the same CMIF map with cuFFT through torch.fft and torch elementwise ops (the
     paper's own PyTorch approach): one-hot level sets, rfft2, per-pair product
-    conj(F_a) F_b, irfft2, rounding, c log2 c sums (FP64 accumulation), MI."""
+    conj(F_a) F_b, irfft2, rounding, c log2 c sums (FP64 accumulation), MI.
+    ``dtype`` float64 gives the plain FP64 form (cuFFT Z2D/D2Z): the accuracy of
+    this library's FP32 path with its guard, without the guard."""
 
-    def __init__(self, torch, A, MA, B, MB, KA, KB, dev):
+    def __init__(self, torch, A, MA, B, MB, KA, KB, dev, dtype=None):
         self.t = torch
+        self.dt = torch.float32 if dtype is None else dtype
         HA, WA = A.shape
         HB, WB = B.shape
         self.R, self.C = HA + HB - 1, WA + WB - 1
@@ -378,9 +381,9 @@ class TorchFFTPlain:
         def planes(X, MX, K):
             x = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
             m = torch.ones_like(x, dtype=torch.bool) if MX is None else torch.from_numpy(MX).to(dev).bool()
-            out = torch.zeros((K, self.P, self.Q), dtype=torch.float32, device=dev)
+            out = torch.zeros((K, self.P, self.Q), dtype=self.dt, device=dev)
             for k in range(K):
-                out[k, :x.shape[0], :x.shape[1]] = ((x == k) & m).float()
+                out[k, :x.shape[0], :x.shape[1]] = ((x == k) & m).to(self.dt)
             return out
         self.la, self.lb = planes(A, MA, KA), planes(B, MB, KB)
 
@@ -390,7 +393,7 @@ class TorchFFTPlain:
         FB = t.fft.rfft2(self.lb)
         S = t.zeros((self.P, self.Q), dtype=t.float64, device=FA.device)
         N = t.zeros_like(S)
-        CB = t.zeros((self.KB, self.P, self.Q), dtype=t.float32, device=FA.device)
+        CB = t.zeros((self.KB, self.P, self.Q), dtype=self.dt, device=FA.device)
         for a in range(self.KA):
             c = t.round(t.fft.irfft2(t.conj(FA[a])[None] * FB, s=(self.P, self.Q)))  # c[s] = sum_x a(x) b(x + s)
             ca = c.sum(0)
@@ -430,12 +433,14 @@ def run_secondary(args):
         A, B = d(Av), d(Bv)
         step = lambda: plan.compute(A, None, B, None, mi, n, None, 0.5, pk)
         units, name = plan.R * plan.C, "volume-64^3-K8 FP32"
-    elif args.workload == "torchfft":
+    elif args.workload in ("torchfft", "torchfft64"):
         cfg = synth.make_workload("single-1024x1024-K16")
         H, W = cfg["A"].shape
-        plan = TorchFFTPlain(torch, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 16, 16, dev)
+        f64 = args.workload == "torchfft64"
+        plan = TorchFFTPlain(torch, cfg["A"], cfg["M_A"], cfg["B"], cfg["M_B"], 16, 16, dev,
+                             torch.float64 if f64 else torch.float32)
         step = plan
-        units, name = (2 * H - 1) * (2 * W - 1), cfg["name"] + " torch.fft (cuFFT) plain form FP32"
+        units, name = (2 * H - 1) * (2 * W - 1), cfg["name"] + " torch.fft (cuFFT) plain form " + ("FP64" if f64 else "FP32")
         # sanity: the same map as this library's, at a few shifts
         ref = cm.cmif(d(cfg["A"]), d(cfg["M_A"]), d(cfg["B"]), d(cfg["M_B"]), 16, 16, precision=cm.FP32)["mi"]
         got = plan()
@@ -560,7 +565,7 @@ def run_secondary(args):
                       "clocks": clocks, "cpu_baseline": cpu,
                       "device_status": {"status": st[0], "max_residual": st[1], "escalations": st[2]},
                       **({"impl": "torch.fft (cuFFT) plain form: comparison baseline, not this library"}
-                         if args.workload == "torchfft" else {})}),
+                         if args.workload.startswith("torchfft") else {})}),
           flush=True)
 
 
@@ -574,7 +579,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single1024",
                     choices=["single1024", "rotation", "rotation-window", "two-stage", "batch", "single256",
-                             "plain64", "nmi", "swmi", "torchfft", "volume"],
+                             "plain64", "nmi", "swmi", "torchfft", "torchfft64", "volume"],
                     help="single1024 (default, the headline): 1024^2, K=16; rotation: 512^2, K=16, 64 angles; "
                          "batch: 128 uneven pairs x 4 angles; single256 / plain64: 256^2, K=16 / 64^2, K=8")
     ap.add_argument("--profile-shape", default=None,
