@@ -388,7 +388,7 @@ cmif_status cmif_plan_autotune(cmif_plan plan, const char* cache_path, cmif_tuni
 
 /* Fixed-point scale of the epilogue's per-shift entropy sums (Eq. finalentropy):
  * units of 2^-CMIF_ENTROPY_FIX_BITS. */
-#define CMIF_ENTROPY_FIX_BITS 24
+#define CMIF_ENTROPY_FIX_BITS 23
 
 /* The per-count entropy term T(c) = c log2 c of Eq. finalentropy, exactly as
  * the row epilogue evaluates it (every precision), for the counts
@@ -396,7 +396,7 @@ cmif_status cmif_plan_autotune(cmif_plan plan, const char* cache_path, cmif_tuni
  * 2^-CMIF_ENTROPY_FIX_BITS.  T(c) = c * L(c) with an integer L(c), the
  * fixed-point log2 c; T(0) = T(1) = 0.  The MI of a shift is
  * (sum_joint T - sum_A T - sum_B T + T(N)) / N (Eq. finalentropy rearranged),
- * so its error is at most 4 * max_c |L(c) 2^-24 - log2 c|; this entry point
+ * so its error is at most 4 * max_c |L(c) 2^-23 - log2 c|; this entry point
  * lets a caller measure that maximum over every count a map can hold
  * (c <= 2^22).  out_dev: device int64[n]; 0 <= c0, 0 <= n, c0 + n <= 2^22 + 1
  * (else CMIF_ERR_INVALID_ARG).  Asynchronous on stream. */

@@ -329,7 +329,7 @@ def entropy_terms(c0, n, out, stream=None):
     _check(lib().cmif_entropy_terms(int(c0), int(n), _ptr(out), _stream(stream)), "cmif_entropy_terms")
 
 
-ENTROPY_FIX_BITS = 24
+ENTROPY_FIX_BITS = 23
 
 
 def compute_noalloc(A, M_A, B, M_B, K_A, K_B, mi_map, n_map=None, gamma=0.0, peak=None, status=None,

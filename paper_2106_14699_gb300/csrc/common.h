@@ -46,6 +46,6 @@ struct Geom {
 };
 
 constexpr float kResidualGuard = 0.25f;  // a count whose pre-rounding residual reaches this is not trusted
-constexpr int kFixBits = 24;             // fixed-point scale of sum c*log2(c): units of 2^-24
+constexpr int kFixBits = 23;             // fixed-point scale of sum c*log2(c): units of 2^-23
 
 }  // namespace cmif

@@ -36,10 +36,15 @@ __device__ __forceinline__ long long clog2c_fixed(float c) {
     const int ci = __float_as_int(c + 8388608.0f) - 0x4B000000;
     const int bits = __float_as_int(c);
     const float lm = __log2f(__int_as_float((bits & 0x7FFFFF) | 0x3F800000));
-    // c = 0: ci = 0, so the term is 0 (Sec. 3.2: 0 log 0 = 0) whatever L is.  c = 1:
-    // m = 1 and e = 0, so L = 0.  T stays one fixed function of c, so equal counts
-    // still cancel exactly between joint and marginal sums.
-    const int L = ((bits >> 23) - 127) * (1 << kFixBits) + __float2int_rn(lm * (float)(1 << kFixBits));
+    // 2^23 + log2(m) 2^23 lies in [2^23, 2^24], where floats are spaced 1 apart and
+    // their bit patterns grow by 1 per unit: the FMA rounds log2(m) 2^23 to the
+    // nearest integer and the bits give it back (no float-to-integer conversion).
+    // bits & 0x7F800000 = (e + 127) 2^23.  c = 0: ci = 0, so the term is 0 (Sec. 3.2:
+    // 0 log 0 = 0) whatever L is.  c = 1: m = 1 and e = 0, so L = 0.  T stays one
+    // fixed function of c, so equal counts still cancel exactly between joint and
+    // marginal sums.
+    const int t = __float_as_int(fmaf(lm, 8388608.0f, 8388608.0f));
+    const int L = (bits & 0x7F800000) + t - (0x3F800000 + 0x4B000000);
     return (long long)ci * (long long)L;
 }
 

@@ -122,7 +122,8 @@ struct RowTmCfg {
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
     static constexpr int NT = 16, THREADS = NT * 32;
     static constexpr int QH = Q / 2;             // positions per pass (two passes)
-    static constexpr int UH = QH / THREADS;      // positions per thread per pass
+    static constexpr int UH = QH / THREADS;      // positions per thread per pass: UH t .. UH t + UH - 1 (adjacent,
+                                                 // so that the counts of one thread come in one shared load)
     static constexpr int U = 2 * UH;
     static constexpr int REGION = G::SCRATCH;    // FFT scratch / one pass of rounded counts
     static constexpr int STAGE_BYTES = ((L + 1) * 8 + 15) / 16 * 16;  // one Y row (Qh complex), 16-byte multiple
@@ -349,7 +350,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                         const float* obt = reinterpret_cast<const float*>(smem_raw + (size_t)t * C::REGION);
 #pragma unroll
                         for (int uh = 0; uh < UH; ++uh) {
-                            const int u = hf * UH + uh, pl = tid + BT * uh;
+                            const int u = hf * UH + uh, pl = UH * tid + uh;
                             const float c = obt[pl];
                             S[u].joint(clog2c_fixed(c));
                             CA[u] += c;
@@ -378,7 +379,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                         const float* obt = reinterpret_cast<const float*>(smem_raw + (size_t)t * C::REGION);
 #pragma unroll
                         for (int uh = 0; uh < UH; ++uh) {
-                            const int u = hf * UH + uh, pl = tid + BT * uh;
+                            const int u = hf * UH + uh, pl = UH * tid + uh;
                             const float c = obt[pl];
                             S[u].joint(clog2c_fixed(c));
                             CA[u] += c;
@@ -416,7 +417,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
 #pragma unroll
             for (int uh = 0; uh < UH; ++uh) {
                 const int u = hf * UH + uh;
-                const int cidx = circ_to_out(hf * QH + tid + BT * uh, Q, g.WA, g.WB - 1);
+                const int cidx = circ_to_out(hf * QH + UH * tid + uh, Q, g.WA, g.WB - 1);
                 if (cidx < 0) continue;
                 const size_t o = (size_t)row * Cout + cidx;
                 mi_map[o] = S[u].finish(N[u]);
