@@ -809,10 +809,10 @@ std::string tune_key(const cmif_plan p) {
     const Geom& g = p->g;
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, p->device);
-    char buf[256];
-    std::snprintf(buf, sizeof buf, "P%d.Q%d.KA%d.KB%d.DA%d.DB%d.%s.sm%d.%s", g.P, g.Q, g.KA, g.KB, g.DA, g.DB,
-                  p->prec == CMIF_AUTO ? "auto" : "fp32", p->num_sms, prop.name);
-    return buf;
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "P%d.Q%d.KA%d.KB%d.DA%d.DB%d.%s.sm%d.", g.P, g.Q, g.KA, g.KB, g.DA, g.DB,
+                  p->prec == CMIF_AUTO ? "auto" : "fp32", p->num_sms);
+    return std::string(buf) + std::string(prop.name, strnlen(prop.name, sizeof prop.name));
 }
 
 std::mutex g_tune_mu;

@@ -44,7 +44,7 @@ __device__ __forceinline__ long long clog2c_fixed(float c) {
     // fixed function of c, so equal counts still cancel exactly between joint and
     // marginal sums.
     const int t = __float_as_int(fmaf(lm, 8388608.0f, 8388608.0f));
-    const int L = (bits & 0x7F800000) + t - (0x3F800000 + 0x4B000000);
+    const int L = ((bits & 0x7F800000) - 0x3F800000) + (t - 0x4B000000);  // e 2^23 + round(log2(m) 2^23)
     return (long long)ci * (long long)L;
 }
 
@@ -734,6 +734,18 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
             const bool act = pair < npairs;
             const int ovs = (act && ov_slot) ? ov_slot[pair] : -1;
             const cpx<T>* yr = Y + ((size_t)(act ? pair : 0) * Rout + row) * Qs;
+            if (lt == 0) {
+                // ask L2 for this team's row of the next round (or of the block's next row)
+                int np = pair + NT, nrow = row;
+                if (np >= npairs) {
+                    np = team;
+                    const int nt2 = task + (int)gridDim.x;
+                    nrow = nt2 < ntask ? (nt2 / nr) * g.R2 + g.r0 + nt2 % nr : -1;
+                }
+                if (np < npairs && nrow >= 0)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Y + ((size_t)np * Rout + nrow) * Qs),
+                                 "r"((unsigned)(Qs * sizeof(cpx<T>))) : "memory");
+            }
             // Hermitian split: z = IDFT_L(E + iO), z[m] = x[2m] + i x[2m+1]
             auto load = [&](int k) -> cpx<T> {
                 if (!act) return {T(0), T(0)};

@@ -170,7 +170,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
         wait_polls = kDefaultWaitPolls;
         withhold_row = -1;
     }
-    constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, BT = C::THREADS, QH = C::QH;
+    constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, QH = C::QH;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, team = tid >> 5, lane = tid & 31, r = lane / M, j = lane % M;
     unsigned char* region = smem_raw + (size_t)team * C::REGION;
@@ -310,7 +310,6 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
             for (int hf = 0; hf < 2; ++hf) {
                 __syncthreads();
                 float2* ob = reinterpret_cast<float2*>(region);
-#pragma unroll
                 if (EXT && ovs >= 0) {  // exact counts of positions 2 mf, 2 mf + 1 from the second precision
                     const int32_t* ovr = ov + ((size_t)ovs * Rout + row) * Q;
 #pragma unroll
