@@ -105,6 +105,8 @@ struct cmif_plan_s {
     // call, replayed while the call's arguments are unchanged
     bool use_graph = false;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t aux = nullptr;          // second stream of the forward transforms (plans made by cmif_plan_create*)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
     // diagnostics (cmif_plan_set_wait_test): poll limit of the row kernel's bounded
@@ -254,6 +256,9 @@ void free_plan(cmif_plan p) {
     if (p->stage) cudaFree(p->stage);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     p->prof.destroy();
     if (prev >= 0) cudaSetDevice(prev);
     delete p;
@@ -277,6 +282,9 @@ void fill_io(PipeArgs<T>& a, const int32_t* A, const uint8_t* MA, const int32_t*
              int32_t* n, int32_t* counts, DevStatus* st, const cmif_plan_s* p) {
     a.wait_polls = p->test_wait_polls;
     a.withhold_row = p->test_withhold_row;
+    a.aux = p->aux;
+    a.ev_fork = p->ev_fork;
+    a.ev_join = p->ev_join;
     a.A = A;
     a.MA = MA;
     a.B = B;
@@ -984,6 +992,15 @@ cmif_status plan_create(cmif_plan* out, int D_A, int H_A, int W_A, int D_B, int 
         else {
             p->mem_bytes = bytes;
             st = plan_carve(p, (char*)p->mem);
+        }
+    }
+    if (st == CMIF_OK) {
+        // the forward transforms' second stream (blocking neither way with the legacy stream)
+        if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            st = CMIF_ERR_CUDA;
         }
     }
     if (st == CMIF_OK && (flags & CMIF_FLAG_AUTOTUNE)) st = autotune(p, std::getenv("CMIF_TUNE_CACHE"), nullptr);

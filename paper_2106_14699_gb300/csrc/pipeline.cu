@@ -20,14 +20,23 @@ cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     constexpr bool f32 = sizeof(T) == 4;
     constexpr bool split = std::is_same<T, df32>::value;
     const unsigned stg = a.stages ? a.stages : STAGE_ALL;
+    // A's and B's forward transforms are independent: with a second stream, A's run
+    // on it, forked from s before and joined back into s after B's
+    const bool fork = (stg & STAGE_FWD_A) && (stg & STAGE_FWD_B) && a.aux && a.ev_fork && a.ev_join;
+    const cudaStream_t sa = fork ? a.aux : s;
+    if (fork) {
+        e = cudaEventRecord(a.ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(a.aux, a.ev_fork, 0);
+        if (e != cudaSuccess) return e;
+    }
     if (stg & STAGE_FWD_A) {
         CMIF_SIZE_SWITCH_T(T, g.Q, {
-            ProfScope ps(a.prof, f32 ? "fwd_rows_A_f32" : split ? "fwd_rows_A_s32" : "fwd_rows_A_f64", s);
-            e = Sized<T, SZ>::fwd_rows(g, a, false, s);
+            ProfScope ps(a.prof, f32 ? "fwd_rows_A_f32" : split ? "fwd_rows_A_s32" : "fwd_rows_A_f64", sa);
+            e = Sized<T, SZ>::fwd_rows(g, a, false, sa);
         } if (e != cudaSuccess) return e);
         CMIF_SIZE_SWITCH_T(T, g.P, {
-            ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : split ? "fwd_cols_A_s32" : "fwd_cols_A_f64", s);
-            e = Sized<T, SZ>::fwd_cols(g, a, false, s);
+            ProfScope ps(a.prof, f32 ? "fwd_cols_A_f32" : split ? "fwd_cols_A_s32" : "fwd_cols_A_f64", sa);
+            e = Sized<T, SZ>::fwd_cols(g, a, false, sa);
         } if (e != cudaSuccess) return e);
     }
     if (stg & STAGE_FWD_B) {
@@ -39,6 +48,11 @@ cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
             ProfScope ps(a.prof, f32 ? "fwd_cols_B_f32" : split ? "fwd_cols_B_s32" : "fwd_cols_B_f64", s);
             e = Sized<T, SZ>::fwd_cols(g, a, true, s);
         } if (e != cudaSuccess) return e);
+    }
+    if (fork) {
+        e = cudaEventRecord(a.ev_join, a.aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, a.ev_join, 0);
+        if (e != cudaSuccess) return e;
     }
     if (stg & STAGE_COLS) {
         CMIF_SIZE_SWITCH_T(T, g.P, {

@@ -47,6 +47,10 @@ struct PipeArgs {
     int wait_polls;   // poll limit of the TMEM row kernel's bounded waits (0: the default)
     int withhold_row; // diagnostics: output row whose first bulk copy is withheld (-1: none)
     unsigned stages;  // STAGE_* bits: which parts of the sequence to launch
+    // optional second stream and events: A's and B's forward transforms run side by side
+    // (fork from and join back into the call's stream; graph capture records the branch)
+    cudaStream_t aux;
+    cudaEvent_t ev_fork, ev_join;
     // per-pair precision (CMIF_AUTO): all nullable / 0 when unused
     int* popA;                  // [K_A] label pixel counts of A, added by the forward row kernel
     int* popB;                  // [K_B]
