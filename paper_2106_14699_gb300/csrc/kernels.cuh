@@ -273,7 +273,7 @@ struct ColCfg {
 };
 
 template <typename T, int P, int MMAX>
-__global__ void __launch_bounds__(ColCfg<T, P, MMAX>::THREADS)
+__global__ void __launch_bounds__(ColCfg<T, P, MMAX>::THREADS, sizeof(T) == 4 && ColCfg<T, P, MMAX>::THREADS <= 256 ? 3 : 1)
 k_fwd_cols(const cpx<T>* __restrict__ T1, int H, int nplanes, int Qh, int Qs, cpx<T>* __restrict__ F, Tw<T> tw,
            const DevStatus* __restrict__ st, int conditional, T out_scale,
            const unsigned char* __restrict__ plane_need, int slices) {
