@@ -297,11 +297,30 @@ __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, c
     dft_reg<M, DIR, PACK>(v);  // v[brev(k2)] = X_r[j + M k2]
 }
 
-template <int M, int R, int DIR, bool PACK = true, typename T, typename Load>
+template <int M, int R, int DIR, bool PACK = true, bool ONCE = false, typename T, typename Load>
 __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
                                          const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
+    // ONCE (R = 2, teams of one warp): the radix-2 step loads every input once and
+    // passes the groups' halves through the team's buffer (2 M^2 complex values in
+    // front of the groups' scratch), instead of each group loading all inputs.
     constexpr int NQ = M * M;
-    if constexpr (R > 2 && !is_pow2(R)) {
+    if constexpr (ONCE) {
+        static_assert(R == 2 && R * M == 32, "load-once radix-2 step: one-warp teams");
+        constexpr int H2 = M / 2;
+        cpx<T>* xs = reinterpret_cast<cpx<T>*>(reinterpret_cast<char*>(sm) - r * grp_scratch_bytes<T, M>());
+        __syncwarp();  // earlier users of the team's scratch are done
+#pragma unroll
+        for (int t = 0; t < H2; ++t) {
+            const int m = j + M * (r * H2 + t);  // the lanes of both groups cover m < NQ once
+            const cpx<T> x0 = load(m), x1 = load(m + NQ);
+            xs[m] = x0 + x1;
+            xs[NQ + m] = cmul(x0 - x1, twl<DIR>(twn, m));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = xs[r * NQ + j + M * i];
+        __syncwarp();  // the groups' transposes below reuse this buffer
+    } else if constexpr (R > 2 && !is_pow2(R)) {
         // Radix-R decimation in frequency (R = 3, 6) with every input loaded once: the
         // team's lanes l = r M + j take the points m = l + TEAM t, form the R-point DFT
         // of x[m + s NQ], s < R, twiddle frequency q by w_N^{m q} and hand it to group q

@@ -125,7 +125,10 @@ struct RowTmCfg {
     static constexpr int UH = QH / THREADS;      // positions per thread per pass: UH t .. UH t + UH - 1 (adjacent,
                                                  // so that the counts of one thread come in one shared load)
     static constexpr int U = 2 * UH;
-    static constexpr int REGION = G::SCRATCH;    // FFT scratch / one pass of rounded counts
+    // radix-2 teams (Q = 1024) load every input once through a buffer of 2 M^2 complex
+    static constexpr bool ONCE = R == 2;
+    static constexpr int XS = ONCE ? R * M * M * 8 : 0;
+    static constexpr int REGION = G::SCRATCH > XS ? G::SCRATCH : XS;  // FFT scratch / one pass of rounded counts
     static constexpr int STAGE_BYTES = ((L + 1) * 8 + 15) / 16 * 16;  // one Y row (Qh complex), 16-byte multiple
     static constexpr size_t OFF_STAGE = (size_t)NT * REGION;
     static constexpr size_t OFF_BAR = OFF_STAGE + (size_t)NT * STAGE_BYTES;
@@ -264,7 +267,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 return {z.x, z.y};
             };
             cpx<float> v[M];
-            team_fft<M, R, +1, false>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw_sq, tw_pre);
+            team_fft<M, R, +1, false, C::ONCE>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw_sq, tw_pre);
             // the staging buffer is free again: prefetch this team's next active item
             // (the next round of this row, else round 0 of its next row)
             __syncwarp();
