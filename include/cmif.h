@@ -407,7 +407,7 @@ cmif_status cmif_entropy_terms(int c0, int n, int64_t* out_dev, void* stream);
  * gives up after a poll limit, records CMIF_ERR_TIMEOUT in the status word and
  * ends the kernel's work cleanly).  poll_limit > 0 sets the limit of the
  * plan's later calls (0 restores the default of 2^24 polls); withhold_row >= 0
- * makes the Tensor-Memory row kernel (FP32, transform widths 1024 and 2048)
+ * makes the Tensor-Memory row kernel (FP32, transform widths 512, 1024 and 2048)
  * skip the bulk copy of that output row's first label pair, so that the wait
  * for it runs out: the call then reports CMIF_ERR_TIMEOUT from cmif_get_status
  * and that map row is not written.  -1 turns it off.  Used by the tests to

@@ -134,7 +134,7 @@ cmif_status from_cuda(cudaError_t e) {
 }
 
 // Row-kernel choice for precision T: the TMEM / TMA variant where it applies
-// (FP32, Q = 1024 or 2048), else B-marginals in shared memory when they fit,
+// (FP32, Q = 512, 1024 or 2048), else B-marginals in shared memory when they fit,
 // else in global memory.  Fills tm_cols, cb_smem and rows_grid.
 template <typename T>
 cmif_status choose_rows(cmif_plan p, Workspace<T>& w) {

@@ -1,5 +1,5 @@
 // FP32 Tensor-Memory row / entropy-epilogue kernel over several units (rotation
-// angles) for transform sizes 1024 and 2048.
+// angles) for transform sizes 512, 1024 and 2048.
 #include "pipeline_impl.cuh"
 namespace cmif {
 template <int Q, bool NMI>
@@ -12,6 +12,8 @@ cudaError_t launch_rows_tm_units(const Geom& g, const PipeArgs<float>& a, cudaSt
                                                                      nullptr);
     return cudaGetLastError();
 }
+template cudaError_t launch_rows_tm_units<512, false>(const Geom&, const PipeArgs<float>&, cudaStream_t);
+template cudaError_t launch_rows_tm_units<512, true>(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template cudaError_t launch_rows_tm_units<1024, false>(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template cudaError_t launch_rows_tm_units<1024, true>(const Geom&, const PipeArgs<float>&, cudaStream_t);
 template cudaError_t launch_rows_tm_units<2048, false>(const Geom&, const PipeArgs<float>&, cudaStream_t);

@@ -133,7 +133,7 @@ struct Sized {
     static size_t rows_smem(int KB, bool cb_smem);
     static int rows_threads();
     static cudaError_t rows_max_blocks(int KB, bool cb_smem, int* out);
-    static int tm_cols(int KB);                 // 0 unless the TMEM row kernel applies (FP32, Q = 1024 / 2048)
+    static int tm_cols(int KB);                 // 0 unless the TMEM row kernel applies (FP32, Q = 512 / 1024 / 2048)
     static cudaError_t tm_max_blocks(int* out);
     static cudaError_t pair_rows_w(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);  // FP64 only
     static size_t rows_w_smem();
@@ -142,7 +142,7 @@ struct Sized {
 
 template <typename T>
 cudaError_t run_pipeline(const Geom& g, const PipeArgs<T>& a, cudaStream_t s);
-// The Tensor-Memory row kernel over several units (FP32, Q = 1024 or 2048).
+// The Tensor-Memory row kernel over several units (FP32, Q = 512, 1024 or 2048).
 template <int Q, bool NMI>
 cudaError_t launch_rows_tm_units(const Geom& g, const PipeArgs<float>& a, cudaStream_t s);
 // List mode of the second precision: pair products and inverse column transforms of

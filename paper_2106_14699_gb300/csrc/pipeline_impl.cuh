@@ -81,7 +81,7 @@ static cudaError_t launch_pair_cols(const Geom& g, const PipeArgs<T>& a, cudaStr
 template <typename T, int Q, bool NMI>
 static cudaError_t launch_pair_rows_v(const Geom& g, const PipeArgs<T>& a, cudaStream_t s) {
     using C = RowCfg<T, Q>;
-    if constexpr (sizeof(T) == 4 && (Q == 1024 || Q == 2048)) {
+    if constexpr (sizeof(T) == 4 && (Q == 512 || Q == 1024 || Q == 2048)) {
         if (a.tm_cols > 0 && !a.counts) {  // debug count maps: the generic kernel below
             const bool ext = a.ov_slot || a.pair_res || a.conditional || a.wait_polls > 0 || a.withhold_row >= 0;
             // the multi-unit kernel lives in its own translation unit (kernels_f32_rows_units.cu):
@@ -242,7 +242,7 @@ cudaError_t Sized<T, SZ>::rows_w_max_blocks(int* out) {
 
 template <typename T, int SZ>
 int Sized<T, SZ>::tm_cols(int KB) {
-    if constexpr (sizeof(T) == 4 && (SZ == 1024 || SZ == 2048)) {
+    if constexpr (sizeof(T) == 4 && (SZ == 512 || SZ == 1024 || SZ == 2048)) {
         const int need = tm_cols_needed(KB, RowTmCfg<SZ>::U);
         return need <= 512 ? tm_alloc_cols(need) : 0;
     } else {
@@ -253,7 +253,7 @@ int Sized<T, SZ>::tm_cols(int KB) {
 
 template <typename T, int SZ>
 cudaError_t Sized<T, SZ>::tm_max_blocks(int* out) {
-    if constexpr (sizeof(T) == 4 && (SZ == 1024 || SZ == 2048)) {
+    if constexpr (sizeof(T) == 4 && (SZ == 512 || SZ == 1024 || SZ == 2048)) {
         cudaError_t e = ensure_smem(k_pair_rows_tm<SZ, false, 0>, RowTmCfg<SZ>::SMEM);
         if (e != cudaSuccess) return e;
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pair_rows_tm<SZ, false, 0>, RowTmCfg<SZ>::THREADS,

@@ -1,5 +1,5 @@
 // Inverse row transform + fused entropy epilogue, FP32, one warp per pair
-// transform (Q = 1024 or 2048), with
+// transform (Q = 512, 1024 or 2048), with
 //   * the B-marginal accumulators C_B^b(p) held in Tensor Memory (TMEM,
 //     tcgen05.ld / tcgen05.st), one 32-bit column per (b, position) of the
 //     owning thread, and
@@ -118,13 +118,17 @@ __device__ __forceinline__ void tmem_st<32>(uint32_t t, const uint32_t (&r)[32])
 template <int Q>
 struct RowTmCfg {
     static constexpr int L = Q / 2;
-    using G = TeamGeom<float, L>;
+    // Q = 512: a one-warp team needs M = 8, R = 4 (256 = 4 * 8^2), and one pass
+    // holds the whole row (512 positions, one per thread)
+    static constexpr int MMAX = Q <= 512 ? 8 : 32;
+    static constexpr int HALVES = Q <= 512 ? 1 : 2;
+    using G = TeamGeom<float, L, MMAX>;
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
     static constexpr int NT = 16, THREADS = NT * 32;
-    static constexpr int QH = Q / 2;             // positions per pass (two passes)
+    static constexpr int QH = Q / HALVES;        // positions per pass
     static constexpr int UH = QH / THREADS;      // positions per thread per pass: UH t .. UH t + UH - 1 (adjacent,
                                                  // so that the counts of one thread come in one shared load)
-    static constexpr int U = 2 * UH;
+    static constexpr int U = HALVES * UH;
     // radix-2 teams (Q = 1024) load every input once through a buffer of 2 M^2 complex
     static constexpr bool ONCE = R == 2;
     static constexpr int XS = ONCE ? R * M * M * 8 : 0;
@@ -173,7 +177,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
         wait_polls = kDefaultWaitPolls;
         withhold_row = -1;
     }
-    constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, QH = C::QH;
+    constexpr int M = C::M, R = C::R, L = C::L, NT = C::NT, U = C::U, UH = C::UH, QH = C::QH, HALVES = C::HALVES;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, team = tid >> 5, lane = tid & 31, r = lane / M, j = lane % M;
     unsigned char* region = smem_raw + (size_t)team * C::REGION;
@@ -310,21 +314,21 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
             const int a0 = base / KB, b0 = base - a0 * KB;
             const bool fast = (KB == NT) && (b0 == 0);  // the round is exactly (a0, b = 0..15)
 #pragma unroll
-            for (int hf = 0; hf < 2; ++hf) {
+            for (int hf = 0; hf < HALVES; ++hf) {
                 __syncthreads();
                 float2* ob = reinterpret_cast<float2*>(region);
                 if (EXT && ovs >= 0) {  // exact counts of positions 2 mf, 2 mf + 1 from the second precision
                     const int32_t* ovr = ov + ((size_t)ovs * Rout + row) * Q;
 #pragma unroll
-                    for (int k2 = hf * (M / 2); k2 < (hf + 1) * (M / 2); ++k2) {
+                    for (int k2 = hf * (M / HALVES); k2 < (hf + 1) * (M / HALVES); ++k2) {
                         const int mf = R * (j + M * k2) + r;
                         const int2 q = *reinterpret_cast<const int2*>(ovr + 2 * mf);
-                        ob[mf - hf * (L / 2)] = make_float2((float)q.x, (float)q.y);
+                        ob[mf - hf * (L / HALVES)] = make_float2((float)q.x, (float)q.y);
                     }
                 } else {
 #pragma unroll
-                    for (int k2 = hf * (M / 2); k2 < (hf + 1) * (M / 2); ++k2) {
-                        const int m = R * (j + M * k2) + r - hf * (L / 2);
+                    for (int k2 = hf * (M / HALVES); k2 < (hf + 1) * (M / HALVES); ++k2) {
+                        const int m = R * (j + M * k2) + r - hf * (L / HALVES);
                         const cpx<float> z = v[brev(k2, M)];
                         ob[m] = make_float2(z.x, z.y);
                     }
@@ -399,7 +403,7 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
         if (aborted) break;
         // finish the row: last A-marginal, the B-marginals, MI
 #pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
+        for (int hf = 0; hf < HALVES; ++hf) {
 #pragma unroll
             for (int uh = 0; uh < UH; ++uh) {
                 const int u = hf * UH + uh;

@@ -88,10 +88,10 @@ def test_ragged_random(cm, prec_name, shape):
 # Wide maps (Q = 1024 / 2048) run the row kernel that keeps the B-marginals in
 # Tensor Memory and prefetches Y rows with TMA: K_B = 16 takes its fast path,
 # other K_B the general one.  Also check it against the shared-memory kernel.
-# Row widths C = W_A + W_B - 1 whose transform width Q is 1024 or 2048 (the smallest
-# 2^k or 3 * 2^k >= C), the widths of the Tensor-Memory row kernel.
-WIDE = [((20, 450, 30, 500), (16, 16)), ((16, 300, 12, 480), (5, 7)), ((9, 900, 11, 800), (16, 16)),
-        ((12, 880, 10, 900), (24, 3))]
+# Row widths C = W_A + W_B - 1 whose transform width Q is 512, 1024 or 2048 (the
+# smallest 2^k or 3 * 2^k >= C), the widths of the Tensor-Memory row kernel.
+WIDE = [((20, 450, 30, 500), (16, 16)), ((16, 300, 12, 480), (5, 7)), ((20, 200, 30, 250), (16, 16)),
+        ((9, 900, 11, 800), (16, 16)), ((12, 880, 10, 900), (24, 3)), ((16, 240, 12, 260), (5, 7))]
 
 
 def _transform_width(c):
@@ -100,13 +100,14 @@ def _transform_width(c):
 
 @pytest.mark.parametrize("shape,K", WIDE, ids=lambda x: "x".join(map(str, x)))
 def test_wide_rows_tmem_path(cm, shape, K, monkeypatch):
-    """Q = 1024 and 2048 with no count maps requested run the Tensor-Memory row
+    """Q = 512, 1024 and 2048 with no count maps requested run the Tensor-Memory row
     kernel (TMA-staged rows, B-marginals in TMEM; at Q = 1024 the load-once radix-2
-    step): N and MI against the oracle over the whole map.  The generic kernel
+    step, at Q = 512 radix-4 teams and one pass per row): N and MI against the
+    oracle over the whole map.  The generic kernel
     (CMIF_DISABLE_TMEM=1, with count maps, every count against the oracle) gives
     the same N and bit-identical MI."""
     HA, WA, HB, WB = shape
-    assert _transform_width(WA + WB - 1) in (1024, 2048)
+    assert _transform_width(WA + WB - 1) in (512, 1024, 2048)
     rng = np.random.default_rng(sum(shape) * 7 + K[0])
     A, MA, B, MB = _rand(rng, *shape, *K)
     g = run_gpu(cm, A, MA, B, MB, K[0], K[1], cm.FP32, counts=False, gamma=0.5)
@@ -119,7 +120,7 @@ def test_wide_rows_tmem_path(cm, shape, K, monkeypatch):
     assert np.array_equal(g2["n"], g["n"]) and np.array_equal(g2["mi"], g["mi"])
 
 
-@pytest.mark.parametrize("shape,K", WIDE[:2], ids=lambda x: "x".join(map(str, x)))
+@pytest.mark.parametrize("shape,K", WIDE[:3], ids=lambda x: "x".join(map(str, x)))
 def test_wide_rows_tmem_auto(cm, shape, K, monkeypatch):
     """CMIF_AUTO at the Tensor-Memory widths: the row kernel's AUTO form (exact
     counts of listed pairs, per-pair residuals) with every pair listed and with the
