@@ -118,10 +118,11 @@ __device__ __forceinline__ void tmem_st<32>(uint32_t t, const uint32_t (&r)[32])
 template <int Q>
 struct RowTmCfg {
     static constexpr int L = Q / 2;
-    // Q = 512: a one-warp team needs M = 8, R = 4 (256 = 4 * 8^2), and one pass
-    // holds the whole row (512 positions, one per thread)
+    // Q = 512: a one-warp team needs M = 8, R = 4 (256 = 4 * 8^2).  Q <= 1024: one
+    // pass holds the whole row (the team's scratch has room for it: at 1024 the
+    // load-once radix-2 buffer), fewer barriers and TMEM round trips per round
     static constexpr int MMAX = Q <= 512 ? 8 : 32;
-    static constexpr int HALVES = Q <= 512 ? 1 : 2;
+    static constexpr int HALVES = Q <= 1024 ? 1 : 2;
     using G = TeamGeom<float, L, MMAX>;
     static constexpr int M = G::M, R = G::R, TEAM = G::TEAM;
     static constexpr int NT = 16, THREADS = NT * 32;
