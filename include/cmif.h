@@ -137,7 +137,10 @@ cmif_status cmif_plan_create(cmif_plan* out, int H, int W, int K_A, int K_B, cmi
  *   4096 (else CMIF_ERR_UNSUPPORTED).  They are the smallest powers of two
  *   (at least 16) or, for CMIF_FP32 plans, the smallest 3 * 2^k (96 .. 3072)
  *   when that is smaller (CMIF_POW2_ONLY=1 in the environment at creation
- *   keeps powers of two); the counts and MI do not depend on the choice.
+ *   keeps powers of two).  Q keeps the power of two 512, 1024 or 2048 when the
+ *   Tensor-Memory row kernel runs it (plans without count maps; faster than a
+ *   shorter 3 * 2^k width; CMIF_ROWS_POW2=0 keeps the shortest width).  The
+ *   counts and MI do not depend on the choice.
  *   prec: see cmif_precision.  flags: CMIF_FLAG_*.
  * Allocates the workspace on the current CUDA device, which becomes the
  * plan's device.  On error *out is NULL.  The environment variable

@@ -481,6 +481,19 @@ cmif_status plan_init(cmif_plan p, int H_A, int W_A, int H_B, int W_B, int K_A, 
     const bool mixed = prec == CMIF_FP32 && !(p2e && p2e[0] == '1');
     g.P = transform_size(g.R2, mixed);
     g.Q = transform_size(g.C, mixed);
+    {
+        // The row transform prefers the widths of the Tensor-Memory row kernel (512,
+        // 1024, 2048) to a shorter 3 * 2^k: that kernel turns out counts about twice as
+        // fast as the generic one, which outweighs the 4/3 more points of the longer
+        // rows (and of the pair-column transforms over their columns).  Plans that ask
+        // for the count maps run the generic kernel and keep the shorter width.
+        const char* tq = std::getenv("CMIF_ROWS_POW2");  // "0": keep the shortest width
+        const char* no_tm = std::getenv("CMIF_DISABLE_TMEM");
+        const int q2 = transform_size(g.C, false);
+        if (mixed && q2 != g.Q && (q2 == 512 || q2 == 1024 || q2 == 2048) && !(tq && tq[0] == '0') &&
+            !(no_tm && no_tm[0] == '1') && !(flags & CMIF_FLAG_DEBUG_COUNTS) && rows_tm_cols(q2, K_B) > 0)
+            g.Q = q2;
+    }
     if (g.P > 4096 || g.Q > 4096) return CMIF_ERR_UNSUPPORTED;
     g.Qh = g.Q / 2 + 1;
     g.Qs = (int)align_up((size_t)g.Qh, 4);

@@ -396,6 +396,7 @@ def test_mixed_radix_equals_power_of_two(cm, monkeypatch):
     rng = np.random.default_rng(768)
     H, K = 768, 8
     A, B = synth.planted_pair(rng, H, H, 900, K, K, (31, -17), 0.1, same_labels=True)
+    monkeypatch.setenv("CMIF_ROWS_POW2", "0")  # rows of width 1536 too, not only the columns
     outs = []
     for pow2 in (False, True):
         if pow2:
