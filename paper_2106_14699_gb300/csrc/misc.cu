@@ -37,15 +37,18 @@ __global__ void k_peak_partial(const double* __restrict__ mi, const NT* __restri
     n += blockIdx.y * unit_rc;
     parts += (size_t)blockIdx.y * gridDim.x;
     const double thr = gamma * (maxn_u ? (double)maxn_u[blockIdx.y] : max_n_of(st, n));
-    const int wc = c1 - c0;
-    const long long cnt = (long long)(r1 - r0) * wc;
     double bm = -INFINITY;
     long long bi = -1;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x) {
-        const long long i = (long long)(r0 + t / wc) * Cout + c0 + t % wc;
-        if ((double)n[i] >= thr) {
-            const double m = mi[i];
-            if (bi < 0 || better(m, i, bm, bi)) { bm = m; bi = i; }
+    // rows of the window over the blocks, columns over the threads (no index division;
+    // the result does not depend on the visiting order: ties go to the lowest index)
+    for (int r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        const long long base = (long long)r * Cout;
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            const long long i = base + c;
+            if ((double)n[i] >= thr) {
+                const double m = mi[i];
+                if (bi < 0 || better(m, i, bm, bi)) { bm = m; bi = i; }
+            }
         }
     }
     __shared__ double sm_m[32];
@@ -257,11 +260,9 @@ __global__ void k_finalize(DevStatus* st, int slot_if_escalated, int slot_defaul
 __global__ void k_unit_max_n(const int32_t* __restrict__ n, int Cout, int r0, int r1, int c0, int c1,
                              long long unit_rc, int* __restrict__ maxn_u) {
     n += blockIdx.y * unit_rc;
-    const int wc = c1 - c0;
-    const long long cnt = (long long)(r1 - r0) * wc;
     int m = 0;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x)
-        m = max(m, n[(long long)(r0 + t / wc) * Cout + c0 + t % wc]);
+    for (int r = r0 + blockIdx.x; r < r1; r += gridDim.x)
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) m = max(m, n[(long long)r * Cout + c]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&maxn_u[blockIdx.y], m);
