@@ -674,7 +674,14 @@ struct RowCfg {
     // FP32: one thread per position of a pass (Q / 2), between one warp and 512
     // threads, so that no thread idles in the epilogue; smaller blocks share an SM.
     static constexpr int BT_TARGET = sizeof(T) == 4 ? (Q / 2 >= 512 ? 512 : (Q / 2 >= 32 ? Q / 2 : 32)) : 256;
-    static constexpr int NT = TEAM >= BT_TARGET ? 1 : BT_TARGET / TEAM;
+    // FP32: as many teams as the target allows, fewer when that lets the threads divide
+    // a pass's positions exactly (no idle lanes in the epilogue) at no more than a
+    // quarter fewer teams (3072: 4 teams of 96 lanes, 1536: 8 of 48)
+    static constexpr int NT0 = TEAM >= BT_TARGET ? 1 : BT_TARGET / TEAM;
+    static constexpr int nt_exact(int nt) {
+        return nt <= 1 ? 1 : ((Q / (sizeof(T) == 4 ? 2 : 1)) % (nt * TEAM) == 0 ? nt : nt_exact(nt - 1));
+    }
+    static constexpr int NT = (sizeof(T) == 4 && nt_exact(NT0) * 4 >= NT0 * 3) ? nt_exact(NT0) : NT0;
     static constexpr int THREADS = NT * TEAM;
     static constexpr int HALVES = sizeof(T) == 4 ? 2 : 1;
     static constexpr int QH = Q / HALVES;                      // positions per pass
