@@ -189,9 +189,12 @@ cmif_status cmif_compute(cmif_plan plan, const int32_t* A, const uint8_t* M_A, c
                          const uint8_t* M_B, double* mi_map, int32_t* n_map, int32_t* counts, double gamma,
                          cmif_peak* peak_dev, void* stream);
 
-/* cmif_compute with HOST buffers: copies the images in, computes, copies
- * mi_map (and n_map, peak when non-NULL) out, and synchronises the stream.
- * Host pointers (pinned memory makes the copies asynchronous DMA).  The device
+/* cmif_compute with HOST buffers: copies the images in, computes, delivers
+ * mi_map (and n_map, peak when non-NULL), and synchronises the stream.
+ * Host pointers.  Output maps in page-locked (pinned) host memory are written
+ * by the kernels directly as their rows are finished; other host memory
+ * receives a copy after the map (pinned inputs make the copies in asynchronous
+ * DMA).  The device
  * staging buffer belongs to the plan: it is allocated by the first host call
  * (the one exception to "compute calls allocate nothing"; CMIF_ERR_OOM when
  * that fails), reused by later ones and freed by cmif_plan_destroy. */

@@ -1170,13 +1170,26 @@ cmif_status cmif_compute_host(cmif_plan plan, const int32_t* A, const uint8_t* M
     if (e == cudaSuccess && M_B) e = cudaMemcpyAsync(b + oMB, M_B, nB, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return from_cuda(e);
     const bool want_n = n_map || peak_host;
+    // Output maps in page-locked host memory are written by the kernels themselves
+    // (the device reaches that memory directly: NVLink-C2C on Grace hosts, PCIe
+    // elsewhere), as the rows are finished, instead of a copy after the map; other
+    // host memory takes a copy from the staging buffer.
+    auto direct = [](void* host) -> void* {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, host) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        return pa.type == cudaMemoryTypeHost ? pa.devicePointer : nullptr;
+    };
+    double* mi_out = static_cast<double*>(direct(mi_map));
+    int32_t* n_out = n_map ? static_cast<int32_t*>(direct(n_map)) : nullptr;
+    const bool mi_copy = mi_out == nullptr, n_copy = n_map && n_out == nullptr;
+    if (mi_copy) mi_out = (double*)(b + oMI);
+    if (!n_out && want_n) n_out = (int32_t*)(b + oN);
     cmif_status st = cmif_compute(plan, (int32_t*)(b + oA), M_A ? (uint8_t*)(b + oMA) : nullptr, (int32_t*)(b + oB),
-                                  M_B ? (uint8_t*)(b + oMB) : nullptr, (double*)(b + oMI),
-                                  want_n ? (int32_t*)(b + oN) : nullptr, nullptr, gamma,
-                                  peak_host ? (cmif_peak*)(b + oPk) : nullptr, stream);
+                                  M_B ? (uint8_t*)(b + oMB) : nullptr, mi_out, want_n ? n_out : nullptr, nullptr,
+                                  gamma, peak_host ? (cmif_peak*)(b + oPk) : nullptr, stream);
     if (st != CMIF_OK) return st;
-    e = cudaMemcpyAsync(mi_map, b + oMI, RC * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && n_map) e = cudaMemcpyAsync(n_map, b + oN, RC * 4, cudaMemcpyDeviceToHost, s);
+    if (mi_copy) e = cudaMemcpyAsync(mi_map, b + oMI, RC * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && n_copy) e = cudaMemcpyAsync(n_map, b + oN, RC * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && peak_host) e = cudaMemcpyAsync(peak_host, b + oPk, sizeof(cmif_peak), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return from_cuda(e);

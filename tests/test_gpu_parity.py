@@ -318,6 +318,34 @@ def test_host_buffer_entry_point(cm):
     plan.close()
 
 
+@pytest.mark.parametrize("shape,K,prec", [((40, 70, 50, 60), 5, "FP32"), ((100, 300, 90, 260), 6, "FP32"),
+                                          ((33, 41, 29, 37), 4, "FP64")])
+def test_host_entry_pinned_outputs(cm, shape, K, prec):
+    """Output maps in pinned host memory are written by the kernels directly (no copy
+    after the map), pageable ones by a copy: both equal the oracle (N exactly, MI within
+    the tolerance) and each other bit for bit, and so does the peak."""
+    rng = np.random.default_rng(sum(shape) + K)
+    A, MA, B, MB = _rand(rng, *shape, K, K)
+    HA, WA, HB, WB = shape
+    R, C = HA + HB - 1, WA + WB - 1
+    ref = oracle.cmif(A, MA, B, MB, K, K)
+    plan = cm.Plan(*shape, K, K, getattr(cm, prec))
+    mi_p = torch.full((R, C), float("nan"), dtype=torch.float64).pin_memory()
+    n_p = torch.full((R, C), -1, dtype=torch.int32).pin_memory()
+    pk_p = cm.Peak()
+    plan.compute_host(A, MA, B, MB, mi_p, n_p, 0.5, pk_p)
+    mi_h = np.full((R, C), np.nan)
+    n_h = np.full((R, C), -1, np.int32)
+    pk_h = cm.Peak()
+    plan.compute_host(A, MA, B, MB, mi_h, n_h, 0.5, pk_h)
+    assert plan.status()[0] == "OK"
+    plan.close()
+    np.testing.assert_array_equal(n_p.numpy(), ref["n"])
+    assert float(np.abs(mi_p.numpy() - ref["mi"]).max()) <= MI_TOL
+    assert np.array_equal(mi_p.numpy(), mi_h) and np.array_equal(n_p.numpy(), n_h)
+    assert (pk_p.dy, pk_p.dx, pk_p.n, pk_p.mi) == (pk_h.dy, pk_h.dx, pk_h.n, pk_h.mi)
+
+
 def test_max_label_count_exact(cm):
     """K_A = K_B = 64 (the largest accepted): 4096 label pairs; exact counts on the
     whole map, FP32 and FP64."""
