@@ -242,12 +242,34 @@ __host__ __device__ constexpr int team_scratch_bytes() {
 // Every lane of every warp taking part must call this (it uses __syncwarp).
 // The four-step core on values already in registers: v[i] = y[j + M*i] for the
 // group's M*M-point sequence y.  Result: v[brev(k2, M)] = Y[j + M*k2].
-template <int M, int DIR, bool PACK = true, typename T>
+template <int M, int DIR, bool PACK = true, bool WIDE = false, typename T>
 __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, const cpx<T>* __restrict__ twq) {
     dft_reg<M, DIR, PACK>(v);  // v[brev(k1)] = A[j][k1]
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) v[brev(k1, M)] = cmul(v[brev(k1, M)], twl<DIR>(twq, k1 * M + j));
-    if constexpr (sizeof(T) == 4 && M == 32) {
+    if constexpr (WIDE) {
+        // WIDE (FP32, M = 32, a group scratch of M*M complex): one pass of complex
+        // values.  Row k1 holds 16 blocks of two complex; element (k1, col) sits in
+        // block (col / 2) ^ (k1 % 8).  A row write by the 32 lanes is a permutation of
+        // the row; the 16-byte row reads of 8 lanes (rows j .. j + 7) hit 8 different
+        // 16-byte bank groups: conflict-free.
+        static_assert(sizeof(T) == 4 && M == 32, "wide transpose: FP32, 32-lane groups");
+        float2* sc = reinterpret_cast<float2*>(sm);
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) {
+            const cpx<T> z = v[brev(k1, M)];
+            sc[k1 * M + ((((j >> 1) ^ (k1 & 7)) << 1) | (j & 1))] = make_float2(z.x, z.y);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < M / 2; ++b) {
+            const float4 q = *reinterpret_cast<const float4*>(sc + j * M + ((b ^ (j & 7)) << 1));
+            v[2 * b] = {q.x, q.y};
+            v[2 * b + 1] = {q.z, q.w};
+        }
+        __syncwarp();
+    } else if constexpr (sizeof(T) == 4 && M == 32) {
         // Rows of 32 floats in 8 blocks of 4; element (row, col) sits in block
         // (col/4) ^ (row % 8).  Column writes (one float per lane) are a
         // permutation of the row's 32 banks; row reads take 16-byte loads and the

@@ -368,6 +368,7 @@ struct PairColsCfg {
     static constexpr size_t XBUF = (size_t)TPB * P * sizeof(cpx<T>);
     static constexpr size_t FFT = (size_t)TPB * G::SCRATCH;
     static constexpr size_t MAIN = (XBUF > FFT ? XBUF : FFT);
+    static constexpr size_t FFT_WIDE = (size_t)TPB * R * M * M * sizeof(cpx<T>);  // complex transposes
     static constexpr int TW_N = R == 2 ? P / 2 : (R > 2 ? P : 0);  // combine twiddles W_P^k
     static constexpr size_t SMEM = MAIN + (size_t)(NQ + TW_N) * sizeof(cpx<T>);
     // FP32: two blocks per SM (M = 32 needs 128 registers a thread, so 256 threads)
@@ -486,7 +487,10 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                              : "memory");
             }
         }
-        team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
+        if constexpr (sizeof(T) == 4 && M == 32 && !VOL && C::FFT_WIDE <= C::MAIN)  // scratch of M*M complex per group
+            team_fft_core<M, +1, true, true>(v, j, smem_raw + (size_t)(team * R + r) * (M * M * sizeof(cpx<T>)), tw_sq);
+        else
+            team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
         if (threadIdx.x == 0) s_item = next;  // read by all after the tile barrier below
         cpx<T>* tx = xbuf + (size_t)team * P;  // this team's R sub-transforms
         if constexpr (R == 2) {
