@@ -272,7 +272,15 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 return {z.x, z.y};
             };
             cpx<float> v[M];
-            team_fft<M, R, +1, false, C::ONCE>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw_sq, tw_pre);
+            if constexpr (R == 1 && M == 32 && C::STAGE_BYTES >= M * M * 8) {
+                // the staged row is consumed by the loads: its buffer takes the one-pass
+                // complex transpose (the next copy into it is issued after the transform)
+#pragma unroll
+                for (int i = 0; i < M; ++i) v[i] = load(j + M * i);
+                team_fft_core<M, +1, false, true>(v, j, const_cast<cpx<float>*>(stage), tw_sq);
+            } else {
+                team_fft<M, R, +1, false, C::ONCE>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(), tw_sq, tw_pre);
+            }
             // the staging buffer is free again: prefetch this team's next active item
             // (the next round of this row, else round 0 of its next row)
             __syncwarp();
