@@ -248,12 +248,12 @@ __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, c
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) v[brev(k1, M)] = cmul(v[brev(k1, M)], twl<DIR>(twq, k1 * M + j));
     if constexpr (WIDE) {
-        // WIDE (FP32, M = 32, a group scratch of M*M complex): one pass of complex
-        // values.  Row k1 holds 16 blocks of two complex; element (k1, col) sits in
+        // WIDE (FP32, M = 16 or 32, a group scratch of M*M complex): one pass of complex
+        // values.  Row k1 holds M/2 blocks of two complex; element (k1, col) sits in
         // block (col / 2) ^ (k1 % 8).  A row write by the 32 lanes is a permutation of
         // the row; the 16-byte row reads of 8 lanes (rows j .. j + 7) hit 8 different
         // 16-byte bank groups: conflict-free.
-        static_assert(sizeof(T) == 4 && M == 32, "wide transpose: FP32, 32-lane groups");
+        static_assert(sizeof(T) == 4 && (M == 32 || M == 16), "wide transpose: FP32, 16- or 32-lane groups");
         float2* sc = reinterpret_cast<float2*>(sm);
         __syncwarp();
 #pragma unroll
@@ -319,9 +319,11 @@ __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, c
     dft_reg<M, DIR, PACK>(v);  // v[brev(k2)] = X_r[j + M k2]
 }
 
-template <int M, int R, int DIR, bool PACK = true, bool ONCE = false, typename T, typename Load>
+template <int M, int R, int DIR, bool PACK = true, bool ONCE = false, bool WIDE = false, typename T, typename Load>
 __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
                                          const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
+    // WIDE: the groups' scratch are M*M complex each (one-pass complex transposes);
+    // sm is then this group's slice at r * M*M complex from the team's base
     // ONCE (R = 2, teams of one warp): the radix-2 step loads every input once and
     // passes the groups' halves through the team's buffer (2 M^2 complex values in
     // front of the groups' scratch), instead of each group loading all inputs.
@@ -329,7 +331,8 @@ __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& lo
     if constexpr (ONCE) {
         static_assert(R == 2 && R * M == 32, "load-once radix-2 step: one-warp teams");
         constexpr int H2 = M / 2;
-        cpx<T>* xs = reinterpret_cast<cpx<T>*>(reinterpret_cast<char*>(sm) - r * grp_scratch_bytes<T, M>());
+        constexpr int GS = WIDE ? M * M * (int)sizeof(cpx<T>) : grp_scratch_bytes<T, M>();
+        cpx<T>* xs = reinterpret_cast<cpx<T>*>(reinterpret_cast<char*>(sm) - r * GS);
         __syncwarp();  // earlier users of the team's scratch are done
 #pragma unroll
         for (int t = 0; t < H2; ++t) {
@@ -409,7 +412,7 @@ __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& lo
             }
         }
     }
-    team_fft_core<M, DIR, PACK>(v, j, sm, twq);
+    team_fft_core<M, DIR, PACK, WIDE>(v, j, sm, twq);
 }
 
 }  // namespace cmif
