@@ -41,8 +41,8 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # by the units processed (2047/511 output rows; 1025/257 kx columns).  Set to
 # None when a kernel changes after its capture.
 NCU_TRAFFIC = {
-    "pair_rows_f32": 4.37e9,  # (1.076 GB read + 0.014 GB written) at 511 rows x 2047/511
-    "pair_cols_f32": 5.24e9,  # 0.205 GB read x 1025/257 + 1.118 GB written x 1028/260
+    "pair_rows_f32": 4.36e9,  # (1.076 GB read + 0.013 GB written) at 511 rows x 2047/511
+    "pair_cols_f32": 5.01e9,  # 0.198 GB read x 1025/257 + 1.067 GB written x 1028/260
 }
 
 
