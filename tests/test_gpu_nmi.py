@@ -40,8 +40,9 @@ def _check(got, ref):
 
 
 @pytest.mark.parametrize("shape,K,prec", [
-    ((150, 200), 8, "FP32"),     # generic FP32 row kernel (Q = 512)
+    ((150, 200), 8, "FP32"),     # TMEM row kernel (Q = 512)
     ((96, 520), 8, "FP32"),      # TMEM row kernel (Q = 2048)
+    ((40, 1100), 6, "FP32"),     # generic FP32 row kernel (Q = 3072)
     ((70, 66), 6, "FP64"),
     ((70, 66), 6, "SPLIT32"),
 ])
