@@ -382,7 +382,8 @@ struct PairColsCfg {
 // transforms the M*M samples ky = R*m + r (every input is loaded and
 // multiplied once per team), the groups exchange their sub-transforms through
 // shared memory, and group r forms the outputs [r*M*M, (r+1)*M*M) by the
-// radix-R butterfly.  The exchange buffer then serves as a P x TPB tile
+// radix-R butterfly (FP32 groups of 16 or 32 lanes transpose complex values in
+// one pass through their M*M slice of the same buffer).  The exchange buffer then serves as a P x TPB tile
 // (column slots XOR-swizzled by row, conflict-free writes) whose rows leave
 // as chunks of TPB adjacent kx.  While the tile leaves, the F_a loads of the
 // block's next item are already in flight, and items at the head of a kx
