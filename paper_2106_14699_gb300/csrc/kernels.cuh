@@ -488,7 +488,7 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
                              : "memory");
             }
         }
-        if constexpr (sizeof(T) == 4 && M >= 16 && !VOL && C::FFT_WIDE <= C::MAIN)  // scratch of M*M complex per group
+        if constexpr (sizeof(T) == 4 && M >= 16 && C::FFT_WIDE <= C::MAIN)  // scratch of M*M complex per group
             team_fft_core<M, +1, true, true>(v, j, smem_raw + (size_t)(team * R + r) * (M * M * sizeof(cpx<T>)), tw_sq);
         else
             team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
