@@ -6,7 +6,8 @@
 //
 //  * dft_reg<M>     : an M-point DFT (M = 2..32) held in one thread's
 //                     registers, radix-2 decimation in frequency, twiddles
-//                     folded to compile-time constants.  Output in
+//                     folded to compile-time constants (optionally in the
+//                     radix-2^2 order, fewer general rotations).  Output in
 //                     bit-reversed register order.
 //  * team_fft<M,R>  : a length N = R*M*M DFT done by a "team" of R groups of
 //                     M lanes (M points per lane).  The four-step split
@@ -101,8 +102,51 @@ __device__ __forceinline__ cpx<T> twc(cpx<T> d, int k) {
 // after the call v[brev(k, M)] = sum_n v_in[n] e^{DIR 2 pi i n k / M}.
 // PACK = false keeps the butterflies' adds in scalar form (the +-i twiddles then
 // stay free operand negations), for kernels where that issues fewer instructions.
-template <int M, int DIR, bool PACK = true, typename T>
+template <int M, int DIR, bool PACK, typename T>
+__device__ __forceinline__ void dft_reg_r22(cpx<T> (&v)[M]) {
+    // Radix-2^2 ordering of the radix-2 network: the stages go in pairs; on the first
+    // stage of a pair a lower output keeps only the quarter-turn part of its twiddle
+    // (a free swap / negation) and defers the rest, which is the same for the two
+    // inputs of its next butterfly and so moves past it; the second stage applies
+    // everything pending.  N = 32: 28 general rotations instead of 34 (16: 8 vs 10).
+    // pend[i]: rotation still owed by v[i], in units of 2 pi / 32 (all compile-time).
+    int pend[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) pend[i] = 0;
+#pragma unroll
+    for (int span = M / 2, stage = 0; span >= 1; span >>= 1, ++stage) {
+        const bool first = (stage % 2 == 0) && span >= 2;
+#pragma unroll
+        for (int start = 0; start < M; start += 2 * span) {
+#pragma unroll
+            for (int j = 0; j < span; ++j) {
+                const cpx<T> a = v[start + j], b = v[start + j + span];
+                if constexpr (PACK) {
+                    v[start + j] = a + b;
+                    v[start + j + span] = a - b;
+                } else {
+                    v[start + j] = cpx<T>{a.x + b.x, a.y + b.y};
+                    v[start + j + span] = cpx<T>{a.x - b.x, a.y - b.y};
+                }
+                pend[start + j + span] = (pend[start + j] + j * (32 / (2 * span))) & 31;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int e = pend[i];
+            const int q = first ? (e & ~7) : e;
+            if (q) v[i] = twc<32, DIR>(v[i], q);
+            pend[i] = e - q;
+        }
+    }
+}
+
+template <int M, int DIR, bool PACK = true, bool R22 = false, typename T>
 __device__ __forceinline__ void dft_reg(cpx<T> (&v)[M]) {
+    if constexpr (R22) {
+        dft_reg_r22<M, DIR, PACK>(v);
+        return;
+    }
 #pragma unroll
     for (int span = M / 2; span >= 1; span >>= 1) {
 #pragma unroll
@@ -242,9 +286,9 @@ __host__ __device__ constexpr int team_scratch_bytes() {
 // Every lane of every warp taking part must call this (it uses __syncwarp).
 // The four-step core on values already in registers: v[i] = y[j + M*i] for the
 // group's M*M-point sequence y.  Result: v[brev(k2, M)] = Y[j + M*k2].
-template <int M, int DIR, bool PACK = true, bool WIDE = false, typename T>
+template <int M, int DIR, bool PACK = true, bool WIDE = false, bool R22 = false, typename T>
 __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, const cpx<T>* __restrict__ twq) {
-    dft_reg<M, DIR, PACK>(v);  // v[brev(k1)] = A[j][k1]
+    dft_reg<M, DIR, PACK, R22>(v);  // v[brev(k1)] = A[j][k1]
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) v[brev(k1, M)] = cmul(v[brev(k1, M)], twl<DIR>(twq, k1 * M + j));
     if constexpr (WIDE) {
@@ -316,10 +360,11 @@ __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, c
         for (int n2 = 0; n2 < M; ++n2) v[n2] = sc[j * M + (n2 ^ j)];
         __syncwarp();
     }
-    dft_reg<M, DIR, PACK>(v);  // v[brev(k2)] = X_r[j + M k2]
+    dft_reg<M, DIR, PACK, R22>(v);  // v[brev(k2)] = X_r[j + M k2]
 }
 
-template <int M, int R, int DIR, bool PACK = true, bool ONCE = false, bool WIDE = false, typename T, typename Load>
+template <int M, int R, int DIR, bool PACK = true, bool ONCE = false, bool WIDE = false, bool R22 = false,
+          typename T, typename Load>
 __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
                                          const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {
     // WIDE: the groups' scratch are M*M complex each (one-pass complex transposes);
@@ -412,7 +457,7 @@ __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& lo
             }
         }
     }
-    team_fft_core<M, DIR, PACK, WIDE>(v, j, sm, twq);
+    team_fft_core<M, DIR, PACK, WIDE, R22>(v, j, sm, twq);
 }
 
 }  // namespace cmif
