@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # None when a kernel changes after its capture.
 NCU_TRAFFIC = {
     "pair_rows_f32": 4.36e9,  # (1.076 GB read + 0.013 GB written) at 511 rows x 2047/511
-    "pair_cols_f32": 5.01e9,  # 0.198 GB read x 1025/257 + 1.067 GB written x 1028/260
+    "pair_cols_f32": 5.03e9,  # 0.202 GB read x 1025/257 + 1.067 GB written x 1028/260
 }
 
 
