@@ -286,9 +286,10 @@ __host__ __device__ constexpr int team_scratch_bytes() {
 // Every lane of every warp taking part must call this (it uses __syncwarp).
 // The four-step core on values already in registers: v[i] = y[j + M*i] for the
 // group's M*M-point sequence y.  Result: v[brev(k2, M)] = Y[j + M*k2].
-template <int M, int DIR, bool PACK = true, bool WIDE = false, bool R22 = false, typename T>
+// R22: bit 0 / bit 1 put the first / second register DFT in the radix-2^2 order.
+template <int M, int DIR, bool PACK = true, bool WIDE = false, int R22 = 0, typename T>
 __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, const cpx<T>* __restrict__ twq) {
-    dft_reg<M, DIR, PACK, R22>(v);  // v[brev(k1)] = A[j][k1]
+    dft_reg<M, DIR, PACK, (R22 & 1) != 0>(v);  // v[brev(k1)] = A[j][k1]
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) v[brev(k1, M)] = cmul(v[brev(k1, M)], twl<DIR>(twq, k1 * M + j));
     if constexpr (WIDE) {
@@ -360,10 +361,10 @@ __device__ __forceinline__ void team_fft_core(cpx<T> (&v)[M], int j, void* sm, c
         for (int n2 = 0; n2 < M; ++n2) v[n2] = sc[j * M + (n2 ^ j)];
         __syncwarp();
     }
-    dft_reg<M, DIR, PACK, R22>(v);  // v[brev(k2)] = X_r[j + M k2]
+    dft_reg<M, DIR, PACK, (R22 & 2) != 0>(v);  // v[brev(k2)] = X_r[j + M k2]
 }
 
-template <int M, int R, int DIR, bool PACK = true, bool ONCE = false, bool WIDE = false, bool R22 = false,
+template <int M, int R, int DIR, bool PACK = true, bool ONCE = false, bool WIDE = false, int R22 = 0,
           typename T, typename Load>
 __device__ __forceinline__ void team_fft(cpx<T> (&v)[M], int r, int j, Load&& load, void* sm,
                                          const cpx<T>* __restrict__ twq, const cpx<T>* __restrict__ twn) {

@@ -489,8 +489,9 @@ k_pair_cols(const cpx<T>* __restrict__ FA, const cpx<T>* __restrict__ FB, int KA
             }
         }
         if constexpr (sizeof(T) == 4 && M >= 16 && C::FFT_WIDE <= C::MAIN)  // scratch of M*M complex per group
-            // radix-2^2 register DFTs where they do not push the kernel into spills (R = 1)
-            team_fft_core<M, +1, true, true, R == 1>(v, j, smem_raw + (size_t)(team * R + r) * (M * M * sizeof(cpx<T>)), tw_sq);
+            // radix-2^2 register DFTs at R = 1 (at R = 2 both made the kernel spill, the
+            // second alone measured no faster)
+            team_fft_core<M, +1, true, true, R == 1 ? 3 : 0>(v, j, smem_raw + (size_t)(team * R + r) * (M * M * sizeof(cpx<T>)), tw_sq);
         else
             team_fft_core<M, +1>(v, j, smem_raw + (size_t)team * C::G::SCRATCH + r * grp_scratch_bytes<T, M>(), tw_sq);
         if (threadIdx.x == 0) s_item = next;  // read by all after the tile barrier below

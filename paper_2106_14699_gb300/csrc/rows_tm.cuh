@@ -277,9 +277,9 @@ k_pair_rows_tm(const cpx<float>* __restrict__ Y, Geom g, Tw<float> tw, double* _
                 // complex transpose (the next copy into it is issued after the transform)
 #pragma unroll
                 for (int i = 0; i < M; ++i) v[i] = load(j + M * i);
-                team_fft_core<M, +1, false, true, true>(v, j, const_cast<cpx<float>*>(stage), tw_sq);
+                team_fft_core<M, +1, false, true, 3>(v, j, const_cast<cpx<float>*>(stage), tw_sq);
             } else {
-                team_fft<M, R, +1, false, C::ONCE, false, true>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(),
+                team_fft<M, R, +1, false, C::ONCE, false, 3>(v, r, j, load, region + r * grp_scratch_bytes<float, M>(),
                                                                  tw_sq, tw_pre);
             }
             // the staging buffer is free again: prefetch this team's next active item
