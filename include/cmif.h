@@ -145,7 +145,9 @@ cmif_status cmif_plan_create(cmif_plan* out, int H, int W, int K_A, int K_B, cmi
  * Allocates the workspace on the current CUDA device, which becomes the
  * plan's device.  On error *out is NULL.  The environment variable
  * CMIF_DISABLE_TMEM=1 at creation makes FP32 plans use the shared-memory row
- * kernel instead of the Tensor-Memory one (same results; for comparison). */
+ * kernel instead of the Tensor-Memory one, and CMIF_COL_M=16 the 16-lane
+ * column-team variant of the FP32 column transforms (P >= 1024; one of the
+ * autotuner's candidates); same results, for comparison. */
 cmif_status cmif_plan_create_ex(cmif_plan* out, int H_A, int W_A, int H_B, int W_B, int K_A, int K_B,
                                 cmif_precision prec, unsigned flags);
 
