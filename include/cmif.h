@@ -184,7 +184,9 @@ cmif_status cmif_plan_workspace_bytes(cmif_plan plan, size_t* bytes);
  *   gamma   : overlap fraction in [0, 1] of Alg. 1 for the peak
  *   peak_dev: device cmif_peak* or NULL: the gamma-gated argmax of Alg. 1
  *             (ties: lowest map index), angle_idx = 0
- *   stream  : cudaStream_t
+ *   stream  : cudaStream_t.  The call is ordered on it: A's forward transforms
+ *             may run on a second stream of the plan, forked from and joined
+ *             back into stream (a branch when the call is captured in a graph).
  * Returns CMIF_ERR_INVALID_ARG for NULL A/B/mi_map, a counts pointer
  * without the debug flag, or gamma outside [0, 1]. */
 cmif_status cmif_compute(cmif_plan plan, const int32_t* A, const uint8_t* M_A, const int32_t* B,
