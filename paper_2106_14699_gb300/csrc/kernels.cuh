@@ -696,9 +696,27 @@ struct RowCfg {
     static constexpr int U = HALVES * UH;
     static constexpr int REGION = G::SCRATCH;                  // >= QH floats
     static constexpr size_t TEAM_SMEM = (size_t)NT * REGION;
+    // FP32: each team's next Y row (L + 1 complex, 16-byte chunks) is copied into a
+    // shared-memory buffer by asynchronous copies (cp.async) while the current round
+    // computes; the transform then loads its inputs from shared memory
+    static constexpr bool STAGE = sizeof(T) == 4;
+    static constexpr int STAGE_BYTES = STAGE ? ((L + 1) * 8 + 15) / 16 * 16 : 0;
+    static constexpr size_t OFF_STAGE = (TEAM_SMEM + 15) / 16 * 16;
+    static constexpr size_t OFF_CB = OFF_STAGE + (size_t)NT * STAGE_BYTES;  // B-marginals (shared-memory variant)
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 && THREADS < 512 ? 512 / THREADS : 1;  // <= 128 registers
     static_assert(REGION >= QH * 4, "team scratch must hold one pass of rounded counts");
 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// 16-byte asynchronous global-to-shared copy (L2 only), its group commit and the
+// wait for all of this thread's copies
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename T, int Q, bool CB_SMEM, bool NMI>
 __global__ void __launch_bounds__(RowCfg<T, Q>::THREADS, RowCfg<T, Q>::MIN_BLOCKS)
@@ -715,7 +733,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
     constexpr int HALVES = C::HALVES, QH = C::QH;
     if (conditional && !(st->flags & STATUS_ESCALATE)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float* cb = CB_SMEM ? reinterpret_cast<float*>(smem_raw + C::TEAM_SMEM)
+    float* cb = CB_SMEM ? reinterpret_cast<float*>(smem_raw + C::OFF_CB)
                         : cb_global + (size_t)blockIdx.x * g.KB * Q;
     const int tid = threadIdx.x, team = tid / C::TEAM, lt = tid % C::TEAM, r = lt / M, j = lt % M;
     unsigned char* region = smem_raw + (size_t)team * C::REGION;
@@ -727,8 +745,26 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
 
     // tasks: the window's rows of every unit (units > 1: several maps, R2 rows apart)
     const int nr = g.r1 - g.r0, ntask = g.units * nr;
+    auto task_row = [&](int tk) { return (tk / nr) * g.R2 + g.r0 + tk % nr; };
+    // STAGE: the team's buffer for the Y row of its current pair; the team's lanes
+    // copy a row in 16-byte chunks (the rows start on 32-byte boundaries: Qs is a
+    // multiple of 4 complex)
+    const cpx<T>* stage = reinterpret_cast<const cpx<T>*>(smem_raw + C::OFF_STAGE + (size_t)team * C::STAGE_BYTES);
+    auto stage_issue = [&](int pair_i, int row_i) {
+        if constexpr (C::STAGE) {
+            const char* src = reinterpret_cast<const char*>(Y + ((size_t)pair_i * Rout + row_i) * Qs);
+            const uint32_t dst = smem_u32(stage);
+            for (int c = lt; c < C::STAGE_BYTES / 16; c += C::TEAM) cp_async16(dst + 16u * c, src + 16 * c);
+            cp_async_commit();
+        }
+    };
+    if constexpr (C::STAGE) {
+        if ((int)blockIdx.x < ntask && team < npairs) stage_issue(team, task_row(blockIdx.x));
+        cp_async_wait_all();
+        __syncthreads();
+    }
     for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
-        const int row = (task / nr) * g.R2 + g.r0 + task % nr;
+        const int row = task_row(task);
         EntAcc<NMI> S[U];
         float CA[U];
         int N[U];
@@ -747,8 +783,8 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
             const int pair = base + team;
             const bool act = pair < npairs;
             const int ovs = (act && ov_slot) ? ov_slot[pair] : -1;
-            const cpx<T>* yr = Y + ((size_t)(act ? pair : 0) * Rout + row) * Qs;
-            if (lt == 0) {
+            const cpx<T>* yr = C::STAGE ? stage : Y + ((size_t)(act ? pair : 0) * Rout + row) * Qs;
+            if (!C::STAGE && lt == 0) {
                 // ask L2 for this team's row of the next round (or of the block's next row)
                 int np = pair + NT, nrow = row;
                 if (np >= npairs) {
@@ -794,6 +830,13 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
 #pragma unroll
             for (int hf = 0; hf < HALVES; ++hf) {
                 __syncthreads();  // all scratch reads (FFT or previous pass) done
+                if (C::STAGE && hf == 0) {
+                    // the staged rows are consumed: copy this team's next row (the next
+                    // round of this task, else round 0 of the block's next task)
+                    int np = pair + NT, ntk = task;
+                    if (np >= npairs) { np = team; ntk = task + (int)gridDim.x; }
+                    if (np < npairs && ntk < ntask) stage_issue(np, task_row(ntk));
+                }
                 float2* ob = reinterpret_cast<float2*>(region);
 #pragma unroll
                 for (int k2 = hf * (M / HALVES); k2 < (hf + 1) * (M / HALVES); ++k2) {
@@ -812,6 +855,52 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
                 auto accumulate = [&](auto dbg) {
                     constexpr bool DBG = decltype(dbg)::value;
                     int a = a0, b = b0;
+                    if constexpr (!CB_SMEM && !DBG && NT * UH <= 16 && C::THREADS <= 384) {  // registers to spare
+                        if (nt == NT && NT <= KB) {
+                            // the round's pairs have distinct labels b: load their B-marginal
+                            // slots (global memory) together, one memory latency per pass
+                            // instead of one per pair
+                            float cbv[NT][UH];
+#pragma unroll
+                            for (int t = 0; t < NT; ++t) {
+                                const float* cbb = cb + (size_t)b * Q + hf * QH;
+#pragma unroll
+                                for (int uh = 0; uh < UH; ++uh) {
+                                    const int pl = tid + BT * uh;
+                                    cbv[t][uh] = pl < QH ? cbb[pl] : 0.f;
+                                }
+                                if (++b == KB) b = 0;
+                            }
+                            b = b0;
+#pragma unroll
+                            for (int t = 0; t < NT; ++t) {
+                                if (a != cur_a[hf]) {
+#pragma unroll
+                                    for (int uh = 0; uh < UH; ++uh) {
+                                        const int u = hf * UH + uh, pl = tid + BT * uh;
+                                        if (pl >= QH) continue;
+                                        S[u].marg(clog2c_fixed(CA[u]));
+                                        N[u] += (int)CA[u];
+                                        CA[u] = 0.f;
+                                    }
+                                    cur_a[hf] = a;
+                                }
+                                const float* obt = reinterpret_cast<const float*>(smem_raw + (size_t)t * C::REGION);
+                                float* cbb = cb + (size_t)b * Q + hf * QH;
+#pragma unroll
+                                for (int uh = 0; uh < UH; ++uh) {
+                                    const int u = hf * UH + uh, pl = tid + BT * uh;
+                                    if (pl >= QH) continue;
+                                    const float c = obt[pl];
+                                    S[u].joint(clog2c_fixed(c));
+                                    CA[u] += c;
+                                    cbb[pl] = cbv[t][uh] + c;
+                                }
+                                if (++b == KB) { b = 0; ++a; }
+                            }
+                            return;
+                        }
+                    }
                     for (int t = 0; t < nt; ++t) {
                         if (a != cur_a[hf]) {  // uniform: the A-marginal of label cur_a is complete
 #pragma unroll
@@ -850,6 +939,7 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
                 if (counts) accumulate(std::true_type{});
                 else accumulate(std::false_type{});
             }
+            if constexpr (C::STAGE) cp_async_wait_all();  // the next round's rows, visible after the barrier
             __syncthreads();  // the next round's transforms overwrite the scratch read above
         }
 #pragma unroll
@@ -1074,7 +1164,7 @@ k_pair_rows_w(const cpx<double>* __restrict__ Y, Geom g, Tw<double> tw, double* 
 
 template <typename T, int Q>
 constexpr size_t pair_rows_smem(int KB, bool cb_smem) {
-    return RowCfg<T, Q>::TEAM_SMEM + (cb_smem ? (size_t)KB * Q * sizeof(float) : 0);
+    return RowCfg<T, Q>::OFF_CB + (cb_smem ? (size_t)KB * Q * sizeof(float) : 0);
 }
 
 // ---------------------------------------------------------------------------

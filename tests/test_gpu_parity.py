@@ -367,6 +367,22 @@ def test_max_k_wide_rows_global_b_marginals(cm):
     assert float(np.abs(g["mi"] - ref["mi"]).max()) <= MI_TOL
 
 
+@pytest.mark.parametrize("KA,KB", [(3, 17), (5, 24)])
+def test_wide_3x_rows_global_b_marginals(cm, KA, KB):
+    """Q = 3072 rows (output width 2299) with the B-marginals in the row kernel's
+    global slice (K_B x 3072 floats do not fit in shared memory): every round of
+    four pairs loads its slots together.  K_B = 17: A's label changes inside
+    rounds and the last round is shorter (one pair at a time); K_B = 24: whole
+    rounds throughout."""
+    rng = np.random.default_rng(68 + KB)
+    A, MA, B, MB = _rand(rng, 4, 1100, 5, 1200, KA, KB, p0=0.05)
+    g = run_gpu(cm, A, MA, B, MB, KA, KB, cm.FP32, counts=False, gamma=0.2)
+    ref = oracle.cmif(A, MA, B, MB, KA, KB)
+    assert g["status"][0] == "OK", g["status"]
+    np.testing.assert_array_equal(g["n"], ref["n"])
+    assert float(np.abs(g["mi"] - ref["mi"]).max()) <= MI_TOL
+
+
 def test_extreme_aspect_max_row_transform(cm):
     """1 x 2048 rows: P = 16 (the smallest transform), Q = 4096 (the largest)."""
     rng = np.random.default_rng(66)
