@@ -942,6 +942,25 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
             if constexpr (C::STAGE) cp_async_wait_all();  // the next round's rows, visible after the barrier
             __syncthreads();  // the next round's transforms overwrite the scratch read above
         }
+        // the B-marginals: all of this thread's positions of one label loaded together
+        for (int b = 0; b < KB; ++b) {
+            float cbv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int pl = tid + BT * (u % UH), p = (u / UH) * QH + pl;
+                cbv[u] = pl < QH ? cb[(size_t)b * Q + p] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int pl = tid + BT * (u % UH), p = (u / UH) * QH + pl;
+                if (pl >= QH) continue;
+                S[u].marg(clog2c_fixed(cbv[u]));
+                if (counts) {
+                    const int cidx = circ_to_out(p, Q, g.WA, g.WB - 1);
+                    if (cidx >= 0) counts[((size_t)npairs + KA + b) * RC + (size_t)row * Cout + cidx] = (int)cbv[u];
+                }
+            }
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int pl = tid + BT * (u % UH), p = (u / UH) * QH + pl;
@@ -950,11 +969,6 @@ k_pair_rows(const cpx<T>* __restrict__ Y, Geom g, Tw<T> tw, float* __restrict__ 
             S[u].marg(clog2c_fixed(CA[u]));
             N[u] += (int)CA[u];
             if (counts && cidx >= 0) counts[((size_t)npairs + cur_a[u / UH]) * RC + (size_t)row * Cout + cidx] = (int)CA[u];
-            for (int b = 0; b < KB; ++b) {
-                const float cbv = cb[(size_t)b * Q + p];
-                S[u].marg(clog2c_fixed(cbv));
-                if (counts && cidx >= 0) counts[((size_t)npairs + KA + b) * RC + (size_t)row * Cout + cidx] = (int)cbv;
-            }
             if (cidx < 0) continue;
             const size_t o = (size_t)row * Cout + cidx;
             mi_map[o] = S[u].finish(N[u]);
