@@ -246,7 +246,7 @@ cudaError_t launch_status_code(const DevStatus* st, int32_t* out, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Final verdict on the authoritative precision's residual (slot 2: per-pair
+// Final decision on the authoritative precision's residual (slot 2: per-pair
 // precision, where both the FP32 pairs' and the second-precision pairs' count).
 __global__ void k_finalize(DevStatus* st, int slot_if_escalated, int slot_default) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
